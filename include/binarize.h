@@ -1,0 +1,179 @@
+/*
+ * binarize.h — C ABI of the GB300 local adaptive binarization library.
+ *
+ * The library computes, for every pixel (i, j) of an 8-bit gray image, the
+ * statistics of the h x w window around it and compares the pixel with a
+ * local threshold, as in Chan, "Memory-efficient and fast implementation of
+ * local adaptive binarization methods" (arXiv 1905.13038):
+ *
+ *   window     rows (i-o, i+u], columns (j-l, j+r] with l = floor((w+1)/2),
+ *              r = floor(w/2), o = floor((h+1)/2), u = floor(h/2)
+ *              (Algorithm 1, Sec. 1 definitions of m and s);
+ *   border     pixels outside the image count as 0 and n is the number of
+ *              in-image window pixels (Sec. 3.2 assumptions, Algorithm 1);
+ *   sums       S1 = sum I, S2 = sum I^2, exact integers (Sec. 3.1, Sec. 3.3);
+ *   threshold  Sauvola t = m (1 + k (s/R - 1)) (Sec. 1, Table 1),
+ *              Niblack t = m + k s (Table 1), with m = S1/n and
+ *              s = sqrt(V)/n, V = n S2 - S1^2 (exact 64-bit integer);
+ *              local quantile t = Q - offset (Sec. 3.4);
+ *   output     bit 0 where I <= t (dark, foreground), 1 elsewhere
+ *              (Algorithm 1), packed LSB first: bit (j & 7) of byte (j >> 3)
+ *              of each output row; padding bits of the last byte are 0.
+ *
+ * Floating point.  The reference threshold is the "canonical" FP64
+ * evaluation, every operation IEEE binary64 round-to-nearest without FMA
+ * contraction, in exactly this order:
+ *     nd = n; m = S1/nd; s = sqrt(V/(nd*nd));
+ *     Sauvola t = m*(1 + k*(s/R - 1));  Niblack t = m + k*s.
+ * BZ_FP64 reproduces its decisions bit for bit; BZ_FP32 evaluates the same
+ * formula in FP32 and may differ on pixels within ~1e-4 gray levels of t.
+ *
+ * Memory.  Every image/output pointer is a DEVICE pointer owned by the
+ * caller (for instance a torch tensor); the library neither frees nor keeps
+ * it past the completion of the work on `stream` (a cudaStream_t passed as
+ * void*, NULL = legacy default stream).  The image has H rows of in_pitch
+ * >= W bytes; out has H rows of out_pitch >= ceil(W/8) bytes.  Only the
+ * first ceil(W/8) bytes of each output row are written.  Image and output
+ * must not overlap (Sec. 3.2 assumptions): overlap -> BZ_EOVERLAP.
+ *
+ * Errors.  Argument errors are reported synchronously and nothing is
+ * launched.  Launch failures return BZ_ECUDA.  Work is asynchronous with
+ * respect to the host; kernel-side faults surface at the caller's next
+ * synchronisation.  No entry point aborts the process.
+ *
+ * Limits: 1 <= H, W <= 2^31 - 1; 1 <= h, w <= 511 (keeps V < 2^53 so the
+ * FP64 threshold sees it exactly).
+ */
+#ifndef BINARIZE_H
+#define BINARIZE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BZ_OK = 0,
+    BZ_EINVAL = 1,          /* bad argument (size, pitch, window, parameter) */
+    BZ_EOVERLAP = 2,        /* image and output buffers overlap              */
+    BZ_ENOMEM = 3,          /* the library could not allocate its scratch    */
+    BZ_EBUDGET = 4,         /* server: request larger than the HBM budget    */
+    BZ_ECUDA = 5,           /* a CUDA call or kernel launch failed           */
+    BZ_ETIMEOUT = 6,        /* server: wait timed out (request cancelled)    */
+    BZ_EDEVICE_TIMEOUT = 7, /* a bounded device-side wait gave up            */
+    BZ_ECANCELLED = 8       /* server: request cancelled                     */
+} bz_status;
+
+typedef enum {
+    BZ_FP64 = 0,        /* decisions identical to the canonical FP64 threshold:
+                           certified FP32 filter + FP64 for near-ties         */
+    BZ_FP32 = 1,        /* FP32 threshold only (fast, may flip near-ties)    */
+    BZ_FP64_DIRECT = 2  /* canonical FP64 threshold evaluated for every pixel */
+} bz_precision;
+
+typedef enum { BZ_SAUVOLA = 0, BZ_NIBLACK = 1, BZ_QUANTILE = 2 } bz_method;
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char *bz_status_string(bz_status s);
+
+/* Sauvola binarization (Sec. 1 formula; Algorithm 1; sqrt-free identity of
+ * Sec. 3.2 for k >= 0).  k: any finite value (the paper requires k >= 0 for
+ * its square-root-free form; the library accepts any k); R > 0 finite. */
+bz_status binarize_sauvola(const uint8_t *image, int64_t H, int64_t W,
+                           int64_t in_pitch, int32_t h, int32_t w, double k,
+                           double R, uint8_t *out, int64_t out_pitch,
+                           bz_precision precision, void *stream);
+
+/* Niblack binarization, t = m + k s (Table 1).  k: any finite value. */
+bz_status binarize_niblack(const uint8_t *image, int64_t H, int64_t W,
+                           int64_t in_pitch, int32_t h, int32_t w, double k,
+                           uint8_t *out, int64_t out_pitch,
+                           bz_precision precision, void *stream);
+
+/* Local-quantile binarization (Sec. 3.4, sliding histograms).
+ * Q = rho-th smallest gray level of the clipped window with
+ * rho = max(1, ceil(n * q_num / q_den)) computed in integers
+ * (q = 1/2 gives the lower median); bit = 0 iff I <= Q - offset.
+ * 0 <= q_num <= q_den, q_den >= 1, |offset| <= 255. */
+bz_status binarize_quantile(const uint8_t *image, int64_t H, int64_t W,
+                            int64_t in_pitch, int32_t h, int32_t w,
+                            int32_t q_num, int32_t q_den, int32_t offset,
+                            uint8_t *out, int64_t out_pitch, void *stream);
+
+/* Parity export of the exact window statistics (Sec. 1 definitions computed
+ * with the Sec. 3.1 recursive identities): S1, S2 and n as dense H x W
+ * row-major device arrays (uint32, uint64, uint32).  Any of the three may
+ * be NULL to skip it. */
+bz_status window_sums(const uint8_t *image, int64_t H, int64_t W,
+                      int64_t in_pitch, int32_t h, int32_t w, uint32_t *S1,
+                      uint64_t *S2, uint32_t *n, void *stream);
+
+/* Parity export of the window quantile Q (Sec. 3.4): dense H x W uint8. */
+bz_status window_quantile(const uint8_t *image, int64_t H, int64_t W,
+                          int64_t in_pitch, int32_t h, int32_t w,
+                          int32_t q_num, int32_t q_den, uint8_t *Q,
+                          void *stream);
+
+/* FP32-versus-FP64 report for a Sauvola (method 0) or Niblack (method 1)
+ * configuration: adds to *flips_dev the number of pixels whose BZ_FP32
+ * decision differs from the canonical FP64 decision, and raises
+ * *max_abs_dt_dev to the largest |t32 - t64| seen.  Both are caller-owned
+ * device scalars (initialise them to 0).  R is ignored for Niblack. */
+bz_status binarize_precision_report(int32_t method, const uint8_t *image,
+                                    int64_t H, int64_t W, int64_t in_pitch,
+                                    int32_t h, int32_t w, double k, double R,
+                                    uint64_t *flips_dev,
+                                    double *max_abs_dt_dev, void *stream);
+
+/* Number of pixels the most recent BZ_FP64 call on this device could not
+ * decide in FP32 and evaluated in FP64, read back synchronously after the
+ * stream finishes.  Diagnostic only; returns -1 when unknown. */
+int64_t bz_last_fp64_fallbacks(void *stream);
+
+/* ---------------------------------------------------------------------- */
+/* Batched execution: many images of uneven sizes in one launch.          */
+/* ---------------------------------------------------------------------- */
+typedef struct {
+    const uint8_t *image; /* device */
+    uint8_t *out;         /* device */
+    int64_t H, W, in_pitch, out_pitch;
+    int32_t h, w;
+    int32_t method;       /* bz_method */
+    double k, R;          /* Sauvola / Niblack parameters */
+    int32_t q_num, q_den, offset; /* quantile parameters */
+} bz_job;
+
+/* Runs n jobs (host array, copied before return) as one persistent launch
+ * over a device work list.  precision applies to Sauvola/Niblack jobs.
+ * Every job is validated first; on any invalid job nothing is launched and
+ * BZ_EINVAL/BZ_EOVERLAP is returned. */
+bz_status binarize_batch(const bz_job *jobs_host, int32_t n,
+                         bz_precision precision, void *stream);
+
+/* ---------------------------------------------------------------------- */
+/* Served execution: continuous batching of requests on the device.       */
+/* ---------------------------------------------------------------------- */
+typedef struct bz_server bz_server;
+
+/* hbm_budget_bytes: upper bound on the summed image+output bytes of the
+ * requests in flight on the device; max_slots: requests in flight at most. */
+bz_status bz_server_create(int64_t hbm_budget_bytes, int32_t max_slots,
+                           bz_server **out);
+/* Queues a job; its buffers must stay valid until bz_server_wait returns
+ * BZ_OK, BZ_ECANCELLED or BZ_ETIMEOUT for the ticket. */
+bz_status bz_server_submit(bz_server *srv, const bz_job *job,
+                           bz_precision precision, uint64_t *ticket);
+/* Waits for a ticket; timeout_ms < 0 waits forever.  On timeout the
+ * request is cancelled (or has completed) and BZ_ETIMEOUT is returned. */
+bz_status bz_server_wait(bz_server *srv, uint64_t ticket, int32_t timeout_ms);
+bz_status bz_server_cancel(bz_server *srv, uint64_t ticket);
+/* Cancels queued requests, waits for the in-flight ones, frees the server. */
+bz_status bz_server_destroy(bz_server *srv);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BINARIZE_H */

@@ -1,0 +1,250 @@
+"""GB300 local adaptive binarization (Sauvola, Niblack, local quantile).
+
+Thin ctypes binding over the C ABI declared in ``include/binarize.h``: every
+function here only marshals torch tensors (device memory) and the current CUDA
+stream into the C call of the same name; all arithmetic runs in the library's
+CUDA kernels.  There is no CPU fallback: if ``libbinarize.so`` is missing,
+every call raises.
+
+Image tensors are uint8 CUDA tensors of shape (H, pitch) whose first W columns
+hold the image (W defaults to the pitch).  Outputs are packed bits, shape
+(H, out_pitch), bit (j & 7) of byte (j >> 3) = pixel j, 0 = foreground (I <= t).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import _build
+
+__all__ = [
+    "build", "library_path", "FP64", "FP32", "FP64_DIRECT", "SAUVOLA", "NIBLACK", "QUANTILE",
+    "BinarizeError", "binarize_sauvola", "binarize_niblack", "binarize_quantile", "window_sums",
+    "window_quantile", "binarize_precision_report", "last_fp64_fallbacks", "Job", "binarize_batch",
+    "Server", "status_string",
+]
+
+FP64, FP32, FP64_DIRECT = 0, 1, 2
+SAUVOLA, NIBLACK, QUANTILE = 0, 1, 2
+_PREC = {"fp64": FP64, "fp32": FP32, "fp64_direct": FP64_DIRECT, FP64: FP64, FP32: FP32,
+         FP64_DIRECT: FP64_DIRECT}
+
+_lib = None
+
+
+class BinarizeError(RuntimeError):
+    def __init__(self, fn: str, status: int):
+        super().__init__(f"{fn}: {status_string(status)} (status {status})")
+        self.status = status
+
+
+def build(force: bool = False) -> str:
+    """Compile the CUDA library in place (nvcc, sm_103a)."""
+    global _lib
+    path = _build.build(force=force)
+    _lib = None
+    return path
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+class _JobC(ctypes.Structure):
+    _fields_ = [("image", ctypes.c_void_p), ("out", ctypes.c_void_p), ("H", ctypes.c_int64),
+                ("W", ctypes.c_int64), ("in_pitch", ctypes.c_int64), ("out_pitch", ctypes.c_int64),
+                ("h", ctypes.c_int32), ("w", ctypes.c_int32), ("method", ctypes.c_int32),
+                ("k", ctypes.c_double), ("R", ctypes.c_double), ("q_num", ctypes.c_int32),
+                ("q_den", ctypes.c_int32), ("offset", ctypes.c_int32)]
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"{_build.LIB} is missing: build the CUDA library first "
+                           "(paper_1905_13038_gb300.build() or __graft_entry__.build())")
+    lib = ctypes.CDLL(_build.LIB)
+    P, i64, i32, f64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
+    st = ctypes.c_int
+    sig = {
+        "bz_status_string": ([st], ctypes.c_char_p),
+        "binarize_sauvola": ([P, i64, i64, i64, i32, i32, f64, f64, P, i64, st, P], st),
+        "binarize_niblack": ([P, i64, i64, i64, i32, i32, f64, P, i64, st, P], st),
+        "binarize_quantile": ([P, i64, i64, i64, i32, i32, i32, i32, i32, P, i64, P], st),
+        "window_sums": ([P, i64, i64, i64, i32, i32, P, P, P, P], st),
+        "window_quantile": ([P, i64, i64, i64, i32, i32, i32, i32, P, P], st),
+        "binarize_precision_report": ([i32, P, i64, i64, i64, i32, i32, f64, f64, P, P, P], st),
+        "bz_last_fp64_fallbacks": ([P], i64),
+        "binarize_batch": ([ctypes.POINTER(_JobC), i32, st, P], st),
+        "bz_server_create": ([i64, i32, ctypes.POINTER(P)], st),
+        "bz_server_submit": ([P, ctypes.POINTER(_JobC), st, ctypes.POINTER(ctypes.c_uint64)], st),
+        "bz_server_wait": ([P, ctypes.c_uint64, i32], st),
+        "bz_server_cancel": ([P, ctypes.c_uint64], st),
+        "bz_server_destroy": ([P], st),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def status_string(status: int) -> str:
+    return _load().bz_status_string(status).decode()
+
+
+def _check(fn: str, status: int):
+    if status != 0:
+        raise BinarizeError(fn, status)
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _image(t, W):
+    if t.dtype.itemsize != 1 or not t.is_cuda or t.dim() != 2 or t.stride(1) != 1:
+        raise ValueError("image must be a 2-D uint8 CUDA tensor with unit column stride")
+    H = t.shape[0]
+    pitch = t.stride(0) if H > 1 else t.shape[1]
+    W = t.shape[1] if W is None else W
+    return t.data_ptr(), H, W, pitch
+
+
+def _out(out, H, W, device):
+    import torch
+    if out is None:
+        out = torch.empty((H, (W + 7) // 8), dtype=torch.uint8, device=device)
+    if out.dtype.itemsize != 1 or not out.is_cuda or out.dim() != 2 or out.stride(1) != 1:
+        raise ValueError("out must be a 2-D uint8 CUDA tensor with unit column stride")
+    pitch = out.stride(0) if out.shape[0] > 1 else out.shape[1]
+    return out, pitch
+
+
+def binarize_sauvola(image, h: int, w: int, k: float = 0.5, R: float = 128.0, out=None,
+                     precision="fp64", W: int | None = None, stream=None):
+    ptr, H, W, pitch = _image(image, W)
+    out, op = _out(out, H, W, image.device)
+    _check("binarize_sauvola", _load().binarize_sauvola(ptr, H, W, pitch, h, w, k, R, out.data_ptr(), op,
+                                                        _PREC[precision], _stream(stream)))
+    return out
+
+
+def binarize_niblack(image, h: int, w: int, k: float = -0.2, out=None, precision="fp64",
+                     W: int | None = None, stream=None):
+    ptr, H, W, pitch = _image(image, W)
+    out, op = _out(out, H, W, image.device)
+    _check("binarize_niblack", _load().binarize_niblack(ptr, H, W, pitch, h, w, k, out.data_ptr(), op,
+                                                        _PREC[precision], _stream(stream)))
+    return out
+
+
+def binarize_quantile(image, h: int, w: int, q_num: int = 1, q_den: int = 2, offset: int = 8,
+                      out=None, W: int | None = None, stream=None):
+    ptr, H, W, pitch = _image(image, W)
+    out, op = _out(out, H, W, image.device)
+    _check("binarize_quantile", _load().binarize_quantile(ptr, H, W, pitch, h, w, q_num, q_den, offset,
+                                                          out.data_ptr(), op, _stream(stream)))
+    return out
+
+
+def window_sums(image, h: int, w: int, W: int | None = None, stream=None):
+    """(S1 int32-view of uint32, S2 int64-view of uint64, n) CUDA tensors (H, W)."""
+    import torch
+    ptr, H, W, pitch = _image(image, W)
+    S1 = torch.empty((H, W), dtype=torch.int32, device=image.device)
+    S2 = torch.empty((H, W), dtype=torch.int64, device=image.device)
+    n = torch.empty((H, W), dtype=torch.int32, device=image.device)
+    _check("window_sums", _load().window_sums(ptr, H, W, pitch, h, w, S1.data_ptr(), S2.data_ptr(),
+                                              n.data_ptr(), _stream(stream)))
+    return S1, S2, n
+
+
+def window_quantile(image, h: int, w: int, q_num: int = 1, q_den: int = 2, W: int | None = None,
+                    stream=None):
+    import torch
+    ptr, H, W, pitch = _image(image, W)
+    Q = torch.empty((H, W), dtype=torch.uint8, device=image.device)
+    _check("window_quantile", _load().window_quantile(ptr, H, W, pitch, h, w, q_num, q_den, Q.data_ptr(),
+                                                      _stream(stream)))
+    return Q
+
+
+def binarize_precision_report(method: int, image, h: int, w: int, k: float, R: float = 128.0,
+                              W: int | None = None, stream=None):
+    """(flips, max |t32 - t64|) as Python numbers (synchronises the stream)."""
+    import torch
+    ptr, H, W, pitch = _image(image, W)
+    flips = torch.zeros(1, dtype=torch.int64, device=image.device)
+    maxdt = torch.zeros(1, dtype=torch.float64, device=image.device)
+    _check("binarize_precision_report",
+           _load().binarize_precision_report(method, ptr, H, W, pitch, h, w, k, R, flips.data_ptr(),
+                                             maxdt.data_ptr(), _stream(stream)))
+    return int(flips.item()), float(maxdt.item())
+
+
+def last_fp64_fallbacks(stream=None) -> int:
+    return int(_load().bz_last_fp64_fallbacks(_stream(stream)))
+
+
+class Job:
+    """One image of a batch or a served request (tensors stay owned by the caller)."""
+
+    def __init__(self, image, method: int, h: int, w: int, k: float = 0.5, R: float = 128.0,
+                 q_num: int = 1, q_den: int = 2, offset: int = 8, out=None, W: int | None = None):
+        ptr, H, W, pitch = _image(image, W)
+        self.image = image
+        self.out, self.out_pitch = _out(out, H, W, image.device)
+        self.c = _JobC(ptr, self.out.data_ptr(), H, W, pitch, self.out_pitch, h, w, method, k, R,
+                       q_num, q_den, offset)
+
+
+def binarize_batch(jobs, precision="fp64", stream=None):
+    arr = (_JobC * len(jobs))(*[j.c for j in jobs])
+    _check("binarize_batch", _load().binarize_batch(arr, len(jobs), _PREC[precision], _stream(stream)))
+    return [j.out for j in jobs]
+
+
+class Server:
+    """Continuous-batching server (bz_server_*)."""
+
+    def __init__(self, hbm_budget_bytes: int, max_slots: int = 64):
+        self._h = ctypes.c_void_p()
+        _check("bz_server_create", _load().bz_server_create(hbm_budget_bytes, max_slots,
+                                                            ctypes.byref(self._h)))
+        self._jobs = {}
+
+    def submit(self, job: Job, precision="fp64") -> int:
+        t = ctypes.c_uint64()
+        _check("bz_server_submit", _load().bz_server_submit(self._h, ctypes.byref(job.c),
+                                                            _PREC[precision], ctypes.byref(t)))
+        self._jobs[t.value] = job
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: int = -1) -> int:
+        st = _load().bz_server_wait(self._h, ticket, timeout_ms)
+        self._jobs.pop(ticket, None)
+        return st
+
+    def cancel(self, ticket: int) -> int:
+        return _load().bz_server_cancel(self._h, ticket)
+
+    def close(self):
+        if self._h:
+            _check("bz_server_destroy", _load().bz_server_destroy(self._h))
+            self._h = ctypes.c_void_p()
+            self._jobs.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

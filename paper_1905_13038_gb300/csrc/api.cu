@@ -1,0 +1,249 @@
+// C ABI entry points: argument validation, overlap checks, dispatch.
+#include <math.h>
+#include <mutex>
+
+#include "bz_internal.h"
+
+namespace bz {
+
+bool ranges_overlap(const void *a, size_t na, const void *b, size_t nb)
+{
+    const uintptr_t a0 = (uintptr_t)a, b0 = (uintptr_t)b;
+    return a0 < b0 + nb && b0 < a0 + na;
+}
+
+static size_t span_bytes(int64_t rows, int64_t pitch, int64_t last_row_bytes)
+{
+    return (size_t)((rows - 1) * pitch + last_row_bytes);
+}
+
+bz_status check_image(const uint8_t *image, int64_t H, int64_t W, int64_t in_pitch, int32_t h,
+                      int32_t w)
+{
+    if (!image || H < 1 || W < 1 || H > 2147483647LL || W > 2147483647LL || in_pitch < W)
+        return BZ_EINVAL;
+    if (h < 1 || w < 1 || h > 511 || w > 511)
+        return BZ_EINVAL;
+    // H * pitch must stay addressable
+    if (in_pitch > (INT64_MAX / H))
+        return BZ_EINVAL;
+    return BZ_OK;
+}
+
+bz_status check_out(const uint8_t *image, int64_t H, int64_t W, int64_t in_pitch,
+                    const uint8_t *out, int64_t out_pitch)
+{
+    const int64_t wb = (W + 7) / 8;
+    if (!out || out_pitch < wb || out_pitch > (INT64_MAX / H))
+        return BZ_EINVAL;
+    if (ranges_overlap(image, span_bytes(H, in_pitch, W), out, span_bytes(H, out_pitch, wb)))
+        return BZ_EOVERLAP;
+    return BZ_OK;
+}
+
+// One 8-byte FP64-fallback counter per device, allocated on first use.
+unsigned long long *fallback_counter(int device)
+{
+    static std::mutex mu;
+    static unsigned long long *ptrs[64] = {nullptr};
+    if (device < 0 || device >= 64)
+        return nullptr;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!ptrs[device]) {
+        void *p = nullptr;
+        if (cudaMalloc(&p, sizeof(unsigned long long)) != cudaSuccess)
+            return nullptr;
+        if (cudaMemset(p, 0, sizeof(unsigned long long)) != cudaSuccess) {
+            cudaFree(p);
+            return nullptr;
+        }
+        ptrs[device] = (unsigned long long *)p;
+    }
+    return ptrs[device];
+}
+
+static bool finite_params(int method, double k, double R)
+{
+    if (!isfinite(k) || fabs(k) > 1e6)
+        return false;
+    if (method == 0 && (!isfinite(R) || R < 1e-6 || R > 1e9))
+        return false;
+    return true;
+}
+
+static bz_status run_threshold(int method, const uint8_t *image, int64_t H, int64_t W,
+                               int64_t in_pitch, int32_t h, int32_t w, double k, double R,
+                               uint8_t *out, int64_t out_pitch, bz_precision precision,
+                               void *stream)
+{
+    bz_status st = check_image(image, H, W, in_pitch, h, w);
+    if (st != BZ_OK)
+        return st;
+    st = check_out(image, H, W, in_pitch, out, out_pitch);
+    if (st != BZ_OK)
+        return st;
+    if (!finite_params(method, k, R))
+        return BZ_EINVAL;
+    int mode;
+    switch (precision) {
+    case BZ_FP64: mode = MODE_FP64; break;
+    case BZ_FP32: mode = MODE_FP32; break;
+    case BZ_FP64_DIRECT: mode = MODE_FP64_DIRECT; break;
+    default: return BZ_EINVAL;
+    }
+    Image g{image, H, W, in_pitch};
+    Window win = make_window(h, w);
+    Thresh T = make_thresh(method, k, method == 0 ? R : 128.0);
+    Outputs o{};
+    o.bits = out;
+    o.out_pitch = out_pitch;
+    if (mode == MODE_FP64) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess)
+            return BZ_ECUDA;
+        o.fallbacks = fallback_counter(dev);
+        if (o.fallbacks &&
+            cudaMemsetAsync(o.fallbacks, 0, sizeof(unsigned long long), (cudaStream_t)stream) !=
+                cudaSuccess)
+            return BZ_ECUDA;
+    }
+    return launch_window(mode, g, win, T, o, (cudaStream_t)stream) == cudaSuccess ? BZ_OK
+                                                                                  : BZ_ECUDA;
+}
+
+}  // namespace bz
+
+using namespace bz;
+
+extern "C" {
+
+const char *bz_status_string(bz_status s)
+{
+    switch (s) {
+    case BZ_OK: return "ok";
+    case BZ_EINVAL: return "invalid argument";
+    case BZ_EOVERLAP: return "image and output overlap";
+    case BZ_ENOMEM: return "out of memory";
+    case BZ_EBUDGET: return "request exceeds the HBM budget";
+    case BZ_ECUDA: return "CUDA error";
+    case BZ_ETIMEOUT: return "timed out";
+    case BZ_EDEVICE_TIMEOUT: return "device-side wait timed out";
+    case BZ_ECANCELLED: return "cancelled";
+    }
+    return "unknown status";
+}
+
+bz_status binarize_sauvola(const uint8_t *image, int64_t H, int64_t W, int64_t in_pitch,
+                           int32_t h, int32_t w, double k, double R, uint8_t *out,
+                           int64_t out_pitch, bz_precision precision, void *stream)
+{
+    return run_threshold(0, image, H, W, in_pitch, h, w, k, R, out, out_pitch, precision, stream);
+}
+
+bz_status binarize_niblack(const uint8_t *image, int64_t H, int64_t W, int64_t in_pitch,
+                           int32_t h, int32_t w, double k, uint8_t *out, int64_t out_pitch,
+                           bz_precision precision, void *stream)
+{
+    return run_threshold(1, image, H, W, in_pitch, h, w, k, 128.0, out, out_pitch, precision,
+                         stream);
+}
+
+bz_status binarize_quantile(const uint8_t *image, int64_t H, int64_t W, int64_t in_pitch,
+                            int32_t h, int32_t w, int32_t q_num, int32_t q_den, int32_t offset,
+                            uint8_t *out, int64_t out_pitch, void *stream)
+{
+    bz_status st = check_image(image, H, W, in_pitch, h, w);
+    if (st != BZ_OK)
+        return st;
+    st = check_out(image, H, W, in_pitch, out, out_pitch);
+    if (st != BZ_OK)
+        return st;
+    if (q_den < 1 || q_num < 0 || q_num > q_den || offset < -255 || offset > 255)
+        return BZ_EINVAL;
+    Image g{image, H, W, in_pitch};
+    return launch_quantile(g, make_window(h, w), q_num, q_den, offset, out, out_pitch, nullptr,
+                           (cudaStream_t)stream) == cudaSuccess
+               ? BZ_OK
+               : BZ_ECUDA;
+}
+
+bz_status window_sums(const uint8_t *image, int64_t H, int64_t W, int64_t in_pitch, int32_t h,
+                      int32_t w, uint32_t *S1, uint64_t *S2, uint32_t *n, void *stream)
+{
+    bz_status st = check_image(image, H, W, in_pitch, h, w);
+    if (st != BZ_OK)
+        return st;
+    const size_t img_bytes = (size_t)((H - 1) * in_pitch + W);
+    const size_t HW = (size_t)(H * W);
+    if ((S1 && ranges_overlap(image, img_bytes, S1, HW * 4)) ||
+        (S2 && ranges_overlap(image, img_bytes, S2, HW * 8)) ||
+        (n && ranges_overlap(image, img_bytes, n, HW * 4)))
+        return BZ_EOVERLAP;
+    Image g{image, H, W, in_pitch};
+    Outputs o{};
+    o.S1 = S1;
+    o.S2 = S2;
+    o.n = n;
+    Thresh T = make_thresh(0, 0.5, 128.0);
+    return launch_window(MODE_SUMS, g, make_window(h, w), T, o, (cudaStream_t)stream) ==
+                   cudaSuccess
+               ? BZ_OK
+               : BZ_ECUDA;
+}
+
+bz_status window_quantile(const uint8_t *image, int64_t H, int64_t W, int64_t in_pitch, int32_t h,
+                          int32_t w, int32_t q_num, int32_t q_den, uint8_t *Q, void *stream)
+{
+    bz_status st = check_image(image, H, W, in_pitch, h, w);
+    if (st != BZ_OK)
+        return st;
+    if (!Q || q_den < 1 || q_num < 0 || q_num > q_den)
+        return BZ_EINVAL;
+    if (ranges_overlap(image, (size_t)((H - 1) * in_pitch + W), Q, (size_t)(H * W)))
+        return BZ_EOVERLAP;
+    Image g{image, H, W, in_pitch};
+    return launch_quantile(g, make_window(h, w), q_num, q_den, 0, nullptr, 0, Q,
+                           (cudaStream_t)stream) == cudaSuccess
+               ? BZ_OK
+               : BZ_ECUDA;
+}
+
+bz_status binarize_precision_report(int32_t method, const uint8_t *image, int64_t H, int64_t W,
+                                    int64_t in_pitch, int32_t h, int32_t w, double k, double R,
+                                    uint64_t *flips_dev, double *max_abs_dt_dev, void *stream)
+{
+    bz_status st = check_image(image, H, W, in_pitch, h, w);
+    if (st != BZ_OK)
+        return st;
+    if ((method != 0 && method != 1) || !flips_dev || !max_abs_dt_dev)
+        return BZ_EINVAL;
+    if (!finite_params(method, k, R))
+        return BZ_EINVAL;
+    Image g{image, H, W, in_pitch};
+    Outputs o{};
+    o.flips = (unsigned long long *)flips_dev;
+    o.maxdt_bits = (unsigned long long *)max_abs_dt_dev;
+    Thresh T = make_thresh(method, k, method == 0 ? R : 128.0);
+    return launch_window(MODE_REPORT, g, make_window(h, w), T, o, (cudaStream_t)stream) ==
+                   cudaSuccess
+               ? BZ_OK
+               : BZ_ECUDA;
+}
+
+int64_t bz_last_fp64_fallbacks(void *stream)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess)
+        return -1;
+    unsigned long long *p = fallback_counter(dev);
+    if (!p)
+        return -1;
+    unsigned long long v = 0;
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess)
+        return -1;
+    if (cudaMemcpy(&v, p, sizeof v, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return -1;
+    return (int64_t)v;
+}
+
+}  // extern "C"

@@ -1,0 +1,398 @@
+// Batched execution: many images of uneven sizes and windows in one launch.
+//
+// The host turns the jobs into a device work list (a header plus one
+// descriptor per job with the first global tile index of the job) and runs a
+// CUDA graph [H2D copy of the list -> reset of the FP64-fallback counter ->
+// persistent window kernel -> persistent quantile kernel] on the caller's
+// stream.  Persistent warps (window path) and blocks (quantile path) pop
+// global tile indices from atomic counters in the list header, find the job
+// by binary search over the tile offsets, and run the same tile routines as
+// the single-image kernels, so every result is bit-identical to the
+// single-image call.  The graph topology is fixed per precision; only the
+// list contents change between launches.
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+#include "batch_internal.h"
+#include "bz_quantile.cuh"
+
+namespace bz {
+
+constexpr int kBatchWarps = 4;   // warps per block, window kernel
+constexpr int kQuantNT = 64;     // threads per block, quantile kernel
+
+template <int MODE>
+__global__ void __launch_bounds__(32 * kBatchWarps)
+    k_batch_window(BatchHeader *hdr, const WinJobDev *jobs, unsigned long long *fallbacks)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t total = hdr->win_tiles;
+    const int nj = hdr->n_win;
+    for (;;) {
+        unsigned long long t = 0;
+        if (lane == 0)
+            t = atomicAdd(&hdr->win_next, 1ull);
+        t = __shfl_sync(0xFFFFFFFFu, t, 0);
+        if ((int64_t)t >= total)
+            break;
+        int lo = 0, hi = nj - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (jobs[mid].tile_begin <= (int64_t)t)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        const WinJobDev &J = jobs[lo];
+        const int64_t local = (int64_t)t - J.tile_begin;
+        const int64_t tx = local % J.tiles_x, ty = local / J.tiles_x;
+        const int64_t x0 = tx * kTileCols, y0 = ty * J.tile_h;
+        const int64_t y1 = y0 + J.tile_h < J.g.H ? y0 + J.tile_h : J.g.H;
+        Outputs o{};
+        o.bits = J.out;
+        o.out_pitch = J.out_pitch;
+        o.fallbacks = fallbacks;
+        if (J.vec) {
+            if (J.wide)
+                window_tile<MODE, true, unsigned long long>(J.g, J.win, J.T, o, x0, y0, y1, lane);
+            else
+                window_tile<MODE, true, uint32_t>(J.g, J.win, J.T, o, x0, y0, y1, lane);
+        } else {
+            if (J.wide)
+                window_tile<MODE, false, unsigned long long>(J.g, J.win, J.T, o, x0, y0, y1, lane);
+            else
+                window_tile<MODE, false, uint32_t>(J.g, J.win, J.T, o, x0, y0, y1, lane);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kQuantNT) k_batch_quantile(BatchHeader *hdr, const QJobDev *jobs)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ unsigned long long t_sh;
+    const int64_t total = hdr->q_tiles;
+    const int nj = hdr->n_q;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0)
+            t_sh = atomicAdd(&hdr->q_next, 1ull);
+        __syncthreads();
+        const unsigned long long t = t_sh;
+        if ((int64_t)t >= total)
+            break;
+        int lo = 0, hi = nj - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (jobs[mid].tile_begin <= (int64_t)t)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        const QJobDev &J = jobs[lo];
+        const int64_t local = (int64_t)t - J.tile_begin;
+        const int64_t tx = local % J.tiles_x, ty = local / J.tiles_x;
+        const int64_t x0 = tx * kQuantNT, y0 = ty * J.tile_h;
+        const int64_t y1 = y0 + J.tile_h < J.g.H ? y0 + J.tile_h : J.g.H;
+        if (J.ct32)
+            quantile_tile<uint32_t, kQuantNT>(J.g, J.win, J.q_num, J.q_den, J.offset, J.out,
+                                              J.out_pitch, nullptr, x0, y0, y1, smem);
+        else
+            quantile_tile<uint16_t, kQuantNT>(J.g, J.win, J.q_num, J.q_den, J.offset, J.out,
+                                              J.out_pitch, nullptr, x0, y0, y1, smem);
+    }
+}
+
+static size_t batch_quant_smem() { return quantile_smem_bytes<kQuantNT>(4, 511); }
+
+// ------------------------------------------------------------------ host --
+bz_status validate_job(const bz_job &j)
+{
+    bz_status st = check_image(j.image, j.H, j.W, j.in_pitch, j.h, j.w);
+    if (st != BZ_OK)
+        return st;
+    st = check_out(j.image, j.H, j.W, j.in_pitch, j.out, j.out_pitch);
+    if (st != BZ_OK)
+        return st;
+    if (j.method == BZ_QUANTILE) {
+        if (j.q_den < 1 || j.q_num < 0 || j.q_num > j.q_den || j.offset < -255 || j.offset > 255)
+            return BZ_EINVAL;
+    } else if (j.method == BZ_SAUVOLA || j.method == BZ_NIBLACK) {
+        if (!isfinite(j.k) || fabs(j.k) > 1e6)
+            return BZ_EINVAL;
+        if (j.method == BZ_SAUVOLA && (!isfinite(j.R) || j.R < 1e-6 || j.R > 1e9))
+            return BZ_EINVAL;
+    } else {
+        return BZ_EINVAL;
+    }
+    return BZ_OK;
+}
+
+static int64_t batch_tile_rows(int64_t H, int h)
+{
+    // in a batch the parallelism comes from many images: favour tall tiles
+    int64_t th = 3 * (int64_t)h;
+    if (th < 48)
+        th = 48;
+    if (th > H)
+        th = H;
+    return th;
+}
+
+static int64_t quant_tile_rows(int64_t H, int h)
+{
+    int64_t th = 2 * (int64_t)h;
+    if (th < 64)
+        th = 64;
+    if (th > H)
+        th = H;
+    return th;
+}
+
+BatchSlot::~BatchSlot()
+{
+    release();
+}
+
+void BatchSlot::release()
+{
+    for (int m = 0; m < 3; m++)
+        if (exec[m]) {
+            cudaGraphExecDestroy(exec[m]);
+            exec[m] = nullptr;
+        }
+    if (d_table)
+        cudaFree(d_table);
+    if (h_table)
+        cudaFreeHost(h_table);
+    if (cap_stream)
+        cudaStreamDestroy(cap_stream);
+    if (done)
+        cudaEventDestroy(done);
+    d_table = nullptr;
+    h_table = nullptr;
+    cap_stream = nullptr;
+    done = nullptr;
+    cap_win = cap_q = 0;
+}
+
+static size_t table_bytes(int cap_win, int cap_q)
+{
+    return sizeof(BatchHeader) + sizeof(WinJobDev) * (size_t)cap_win +
+           sizeof(QJobDev) * (size_t)cap_q;
+}
+
+static bz_status ensure_capacity(BatchSlot &s, int n_win, int n_q)
+{
+    if (!s.cap_stream) {
+        if (cudaGetDevice(&s.device) != cudaSuccess)
+            return BZ_ECUDA;
+        if (cudaStreamCreateWithFlags(&s.cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+            return BZ_ECUDA;
+        if (cudaEventCreateWithFlags(&s.done, cudaEventDisableTiming) != cudaSuccess)
+            return BZ_ECUDA;
+        s.fallbacks = fallback_counter(s.device);
+        int nsm = 0;
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, s.device);
+        s.num_sms = nsm > 0 ? nsm : 1;
+    }
+    if (n_win <= s.cap_win && n_q <= s.cap_q && s.d_table)
+        return BZ_OK;
+    // grow (power of two) and drop the graphs, which embed the buffer addresses
+    int cw = s.cap_win > 0 ? s.cap_win : 64, cq = s.cap_q > 0 ? s.cap_q : 16;
+    while (cw < n_win)
+        cw *= 2;
+    while (cq < n_q)
+        cq *= 2;
+    if (s.d_table) {
+        cudaStreamSynchronize(s.cap_stream);
+        cudaEventSynchronize(s.done);
+        cudaFree(s.d_table);
+        cudaFreeHost(s.h_table);
+        s.d_table = nullptr;
+        s.h_table = nullptr;
+    }
+    for (int m = 0; m < 3; m++)
+        if (s.exec[m]) {
+            cudaGraphExecDestroy(s.exec[m]);
+            s.exec[m] = nullptr;
+        }
+    const size_t bytes = table_bytes(cw, cq);
+    if (cudaMalloc(&s.d_table, bytes) != cudaSuccess)
+        return BZ_ENOMEM;
+    if (cudaMallocHost(&s.h_table, bytes) != cudaSuccess) {
+        cudaFree(s.d_table);
+        s.d_table = nullptr;
+        return BZ_ENOMEM;
+    }
+    s.cap_win = cw;
+    s.cap_q = cq;
+    return BZ_OK;
+}
+
+template <int MODE>
+static cudaError_t capture_graph(BatchSlot &s, cudaGraphExec_t *out)
+{
+    cudaStream_t cs = s.cap_stream;
+    BatchHeader *hdr = (BatchHeader *)s.d_table;
+    WinJobDev *wj = (WinJobDev *)(hdr + 1);
+    QJobDev *qj = (QJobDev *)(wj + s.cap_win);
+    const size_t bytes = table_bytes(s.cap_win, s.cap_q);
+    const size_t qsmem = batch_quant_smem();
+    cudaError_t e = cudaFuncSetAttribute(k_batch_quantile,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qsmem);
+    if (e != cudaSuccess)
+        return e;
+    int occ_w = 0, occ_q = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_w, k_batch_window<MODE>, 32 * kBatchWarps, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_q, k_batch_quantile, kQuantNT, qsmem);
+    if (occ_w < 1)
+        occ_w = 1;
+    if (occ_q < 1)
+        occ_q = 1;
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess)
+        return e;
+    cudaMemcpyAsync(s.d_table, s.h_table, bytes, cudaMemcpyHostToDevice, cs);
+    if (s.fallbacks)
+        cudaMemsetAsync(s.fallbacks, 0, sizeof(unsigned long long), cs);
+    k_batch_window<MODE><<<s.num_sms * occ_w, 32 * kBatchWarps, 0, cs>>>(hdr, wj, s.fallbacks);
+    k_batch_quantile<<<s.num_sms * occ_q, kQuantNT, qsmem, cs>>>(hdr, qj);
+    e = cudaStreamEndCapture(cs, &graph);
+    if (e != cudaSuccess)
+        return e;
+    e = cudaGraphInstantiate(out, graph, 0);
+    cudaGraphDestroy(graph);
+    return e;
+}
+
+bz_status run_batch(BatchSlot &s, const bz_job *jobs, int32_t n, bz_precision precision,
+                    cudaStream_t stream)
+{
+    if (n < 0 || (n > 0 && !jobs))
+        return BZ_EINVAL;
+    int mode;
+    switch (precision) {
+    case BZ_FP64: mode = 0; break;
+    case BZ_FP32: mode = 1; break;
+    case BZ_FP64_DIRECT: mode = 2; break;
+    default: return BZ_EINVAL;
+    }
+    int n_win = 0, n_q = 0;
+    for (int32_t i = 0; i < n; i++) {
+        const bz_status st = validate_job(jobs[i]);
+        if (st != BZ_OK)
+            return st;
+        if (jobs[i].method == BZ_QUANTILE)
+            n_q++;
+        else
+            n_win++;
+    }
+    if (n == 0)
+        return BZ_OK;
+    std::lock_guard<std::mutex> lk(s.mu);
+    bz_status st = ensure_capacity(s, n_win, n_q);
+    if (st != BZ_OK)
+        return st;
+    // the previous launch of this slot must have consumed the pinned table
+    if (cudaEventSynchronize(s.done) != cudaSuccess)
+        return BZ_ECUDA;
+
+    BatchHeader *hdr = (BatchHeader *)s.h_table;
+    WinJobDev *wj = (WinJobDev *)(hdr + 1);
+    QJobDev *qj = (QJobDev *)(wj + s.cap_win);
+    // order: most expensive tiles first (longest warm-up + tile), then by size
+    std::vector<int> wi, qi;
+    for (int32_t i = 0; i < n; i++)
+        (jobs[i].method == BZ_QUANTILE ? qi : wi).push_back(i);
+    std::stable_sort(wi.begin(), wi.end(), [&](int a, int b) {
+        return batch_tile_rows(jobs[a].H, jobs[a].h) + jobs[a].h >
+               batch_tile_rows(jobs[b].H, jobs[b].h) + jobs[b].h;
+    });
+    std::stable_sort(qi.begin(), qi.end(), [&](int a, int b) {
+        return (int64_t)jobs[a].w * (quant_tile_rows(jobs[a].H, jobs[a].h) + jobs[a].h) >
+               (int64_t)jobs[b].w * (quant_tile_rows(jobs[b].H, jobs[b].h) + jobs[b].h);
+    });
+    int64_t tb = 0;
+    for (size_t a = 0; a < wi.size(); a++) {
+        const bz_job &j = jobs[wi[a]];
+        WinJobDev &d = wj[a];
+        d.g = Image{j.image, j.H, j.W, j.in_pitch};
+        d.win = make_window(j.h, j.w);
+        d.T = make_thresh(j.method == BZ_SAUVOLA ? 0 : 1, j.k, j.method == BZ_SAUVOLA ? j.R : 128.0);
+        d.out = j.out;
+        d.out_pitch = j.out_pitch;
+        d.tile_h = batch_tile_rows(j.H, j.h);
+        d.tiles_x = (j.W + kTileCols - 1) / kTileCols;
+        d.tile_begin = tb;
+        d.vec = ((uintptr_t)j.image % 8 == 0) && (j.in_pitch % 8 == 0);
+        d.wide = (int64_t)j.h * j.w > 66051;
+        tb += d.tiles_x * ((j.H + d.tile_h - 1) / d.tile_h);
+    }
+    hdr->win_tiles = tb;
+    tb = 0;
+    for (size_t a = 0; a < qi.size(); a++) {
+        const bz_job &j = jobs[qi[a]];
+        QJobDev &d = qj[a];
+        d.g = Image{j.image, j.H, j.W, j.in_pitch};
+        d.win = make_window(j.h, j.w);
+        d.q_num = j.q_num;
+        d.q_den = j.q_den;
+        d.offset = j.offset;
+        d.ct32 = (int64_t)j.h * j.w > 65535;
+        d.out = j.out;
+        d.out_pitch = j.out_pitch;
+        d.tile_h = quant_tile_rows(j.H, j.h);
+        d.tiles_x = (j.W + kQuantNT - 1) / kQuantNT;
+        d.tile_begin = tb;
+        tb += d.tiles_x * ((j.H + d.tile_h - 1) / d.tile_h);
+    }
+    hdr->q_tiles = tb;
+    hdr->n_win = n_win;
+    hdr->n_q = n_q;
+    hdr->win_next = 0;
+    hdr->q_next = 0;
+
+    if (!s.exec[mode]) {
+        cudaError_t e = mode == 0   ? capture_graph<MODE_FP64>(s, &s.exec[mode])
+                        : mode == 1 ? capture_graph<MODE_FP32>(s, &s.exec[mode])
+                                    : capture_graph<MODE_FP64_DIRECT>(s, &s.exec[mode]);
+        if (e != cudaSuccess) {
+            s.exec[mode] = nullptr;
+            cudaGetLastError();
+            return BZ_ECUDA;
+        }
+    }
+    if (cudaGraphLaunch(s.exec[mode], stream) != cudaSuccess)
+        return BZ_ECUDA;
+    if (cudaEventRecord(s.done, stream) != cudaSuccess)
+        return BZ_ECUDA;
+    return BZ_OK;
+}
+
+static BatchSlot *default_slot(int device)
+{
+    static std::mutex mu;
+    static BatchSlot *slots[64] = {nullptr};
+    if (device < 0 || device >= 64)
+        return nullptr;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!slots[device])
+        slots[device] = new BatchSlot();
+    return slots[device];
+}
+
+}  // namespace bz
+
+extern "C" bz_status binarize_batch(const bz_job *jobs_host, int32_t n, bz_precision precision,
+                                    void *stream)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess)
+        return BZ_ECUDA;
+    bz::BatchSlot *s = bz::default_slot(dev);
+    if (!s)
+        return BZ_ECUDA;
+    return bz::run_batch(*s, jobs_host, n, precision, (cudaStream_t)stream);
+}

@@ -1,0 +1,58 @@
+// Batched-execution internals shared by batch.cu and server.cu.
+#pragma once
+#include <math.h>
+#include <mutex>
+
+#include "bz_internal.h"
+
+namespace bz {
+
+struct BatchHeader {
+    int32_t n_win, n_q;
+    int64_t win_tiles, q_tiles;
+    unsigned long long win_next, q_next;  // work-list cursors (reset by the host copy)
+    int64_t pad;
+};
+
+struct WinJobDev {
+    Image g;
+    Window win;
+    Thresh T;
+    uint8_t *out;
+    int64_t out_pitch;
+    int64_t tiles_x, tile_h, tile_begin;
+    int32_t vec, wide;
+};
+
+struct QJobDev {
+    Image g;
+    Window win;
+    int32_t q_num, q_den, offset, ct32;
+    uint8_t *out;
+    int64_t out_pitch;
+    int64_t tiles_x, tile_h, tile_begin;
+};
+
+// A reusable launch context: device work list, pinned host staging copy and
+// one instantiated graph per precision.  Launches through one slot are
+// serialised on its `done` event; independent slots run concurrently.
+struct BatchSlot {
+    std::mutex mu;
+    int device = 0;
+    int num_sms = 1;
+    int cap_win = 0, cap_q = 0;
+    void *d_table = nullptr;
+    void *h_table = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    cudaEvent_t done = nullptr;
+    cudaGraphExec_t exec[3] = {nullptr, nullptr, nullptr};
+    unsigned long long *fallbacks = nullptr;
+    ~BatchSlot();
+    void release();
+};
+
+bz_status validate_job(const bz_job &j);
+bz_status run_batch(BatchSlot &s, const bz_job *jobs, int32_t n, bz_precision precision,
+                    cudaStream_t stream);
+
+}  // namespace bz

@@ -1,0 +1,47 @@
+// Host-side internals shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/binarize.h"
+#include "bz_window.cuh"
+
+namespace bz {
+
+// Window parameters of Algorithm 1.
+inline Window make_window(int h, int w)
+{
+    Window win;
+    win.h = h;
+    win.w = w;
+    win.l = (w + 1) / 2;
+    win.r = w / 2;
+    win.o = (h + 1) / 2;
+    win.u = h / 2;
+    return win;
+}
+
+Thresh make_thresh(int method, double k, double R);
+
+// Rows of a warp tile for the window path (autotuned heuristics).
+int64_t window_tile_rows(int64_t H, int64_t W, int h, int w);
+
+// Launches of the window path; mode is a bz::Mode.
+cudaError_t launch_window(int mode, const Image &g, const Window &win, const Thresh &T,
+                          const Outputs &o, cudaStream_t stream);
+
+cudaError_t launch_quantile(const Image &g, const Window &win, int32_t q_num, int32_t q_den,
+                            int32_t offset, uint8_t *out, int64_t out_pitch, uint8_t *Q,
+                            cudaStream_t stream);
+
+// Library-owned per-device scratch: FP64-fallback counter.
+unsigned long long *fallback_counter(int device);
+
+// Validation helpers (return BZ_OK or an error status).
+bz_status check_image(const uint8_t *image, int64_t H, int64_t W, int64_t in_pitch, int32_t h,
+                      int32_t w);
+bz_status check_out(const uint8_t *image, int64_t H, int64_t W, int64_t in_pitch,
+                    const uint8_t *out, int64_t out_pitch);
+bool ranges_overlap(const void *a, size_t na, const void *b, size_t nb);
+
+}  // namespace bz

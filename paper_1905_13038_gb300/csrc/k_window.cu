@@ -1,0 +1,125 @@
+// Window-statistics kernels: Sauvola / Niblack binarization (FP64-exact,
+// FP32, FP64-direct), the exact window-sum export and the FP32-vs-FP64
+// report.  The per-tile arithmetic lives in bz_window.cuh.
+#include <math.h>
+
+#include "bz_internal.h"
+
+namespace bz {
+
+constexpr int kWarpsPerBlock = 4;
+
+template <int MODE, bool VEC, typename S2T>
+__global__ void __launch_bounds__(32 * kWarpsPerBlock)
+    k_window(Image g, Window win, Thresh T, Outputs o, int64_t tiles_x, int64_t tiles_total,
+             int64_t tile_h)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
+    const int64_t stride = (int64_t)gridDim.x * kWarpsPerBlock;
+    for (int64_t t = wid; t < tiles_total; t += stride) {
+        const int64_t tx = t % tiles_x, ty = t / tiles_x;
+        const int64_t x0 = tx * kTileCols, y0 = ty * tile_h;
+        const int64_t y1 = y0 + tile_h < g.H ? y0 + tile_h : g.H;
+        window_tile<MODE, VEC, S2T>(g, win, T, o, x0, y0, y1, lane);
+    }
+}
+
+// Relative error bound of the FP32 evaluation in decide_f32 (units of
+// 2^-24): inputs rounded once each, 1/n from two correctly rounded
+// reciprocals and a product, sqrt.approx within 2^-22, one fused
+// multiply-add per term and the rounding of the comparison operands; the
+// derivation sums to < 18 units, 24 leaves a margin.
+constexpr float kEpsF32 = 24.0f / 16777216.0f;
+
+Thresh make_thresh(int method, double k, double R)
+{
+    Thresh T;
+    T.method = method;
+    T.k = k;
+    T.R = R;
+    double alpha, beta, gamma, mag;
+    const double u64 = 1.1102230246251565e-16;  // 2^-53
+    if (method == 0) {  // Sauvola: t = m(1-k) + (k/R) m s
+        alpha = 1.0 - k;
+        beta = k / R;
+        gamma = 0.0;
+        // |t64 - t| <= 8 u64 m (1 + |k|(s/R + 1)), m <= 255, s <= 127.5
+        mag = 16.0 * u64 * 255.0 * (1.0 + fabs(k) * (127.5 / R + 1.0));
+    } else {  // Niblack: t = m + k s
+        alpha = 1.0;
+        beta = 0.0;
+        gamma = k;
+        mag = 8.0 * u64 * (255.0 + fabs(k) * 127.5);
+    }
+    T.alpha = (float)alpha;
+    T.beta = (float)beta;
+    T.gamma = (float)gamma;
+    T.aalpha = fabsf(T.alpha);
+    T.abeta = fabsf(T.beta);
+    T.agamma = fabsf(T.gamma);
+    T.eps = kEpsF32;
+    T.delta64 = (float)(mag * 1.01) + 1e-30f;
+    return T;
+}
+
+int64_t window_tile_rows(int64_t H, int64_t W, int h, int w)
+{
+    (void)w;
+    // Enough warps to fill the GPU (~16 per SM on 152 SMs) while keeping the
+    // warm-up (h rows, half the cost of a sliding row) a modest fraction.
+    const int64_t strips = (W + kTileCols - 1) / kTileCols;
+    const int64_t want_warps = 152 * 16;
+    int64_t by_par = (H * strips + want_warps - 1) / want_warps;
+    int64_t by_warm = 2 * (int64_t)h;
+    int64_t th = by_par > by_warm ? by_par : by_warm;
+    if (th < 16)
+        th = 16;
+    if (th > H)
+        th = H;
+    return th;
+}
+
+template <int MODE, bool VEC, typename S2T>
+static cudaError_t launch_t(const Image &g, const Window &win, const Thresh &T, const Outputs &o,
+                            cudaStream_t stream)
+{
+    const int64_t tile_h = window_tile_rows(g.H, g.W, win.h, win.w);
+    const int64_t tiles_x = (g.W + kTileCols - 1) / kTileCols;
+    const int64_t tiles_y = (g.H + tile_h - 1) / tile_h;
+    const int64_t tiles = tiles_x * tiles_y;
+    int64_t blocks = (tiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    if (blocks > 2147483647LL)
+        blocks = 2147483647LL;
+    k_window<MODE, VEC, S2T><<<(unsigned)blocks, 32 * kWarpsPerBlock, 0, stream>>>(
+        g, win, T, o, tiles_x, tiles, tile_h);
+    return cudaGetLastError();
+}
+
+template <int MODE>
+static cudaError_t launch_m(const Image &g, const Window &win, const Thresh &T, const Outputs &o,
+                            cudaStream_t stream)
+{
+    const bool vec = ((uintptr_t)g.img % 8 == 0) && (g.pitch % 8 == 0);
+    const bool wide = (int64_t)win.h * win.w > 66051;  // S2 may reach 2^32
+    if (vec)
+        return wide ? launch_t<MODE, true, unsigned long long>(g, win, T, o, stream)
+                    : launch_t<MODE, true, uint32_t>(g, win, T, o, stream);
+    return wide ? launch_t<MODE, false, unsigned long long>(g, win, T, o, stream)
+                : launch_t<MODE, false, uint32_t>(g, win, T, o, stream);
+}
+
+cudaError_t launch_window(int mode, const Image &g, const Window &win, const Thresh &T,
+                          const Outputs &o, cudaStream_t stream)
+{
+    switch (mode) {
+    case MODE_FP64: return launch_m<MODE_FP64>(g, win, T, o, stream);
+    case MODE_FP32: return launch_m<MODE_FP32>(g, win, T, o, stream);
+    case MODE_FP64_DIRECT: return launch_m<MODE_FP64_DIRECT>(g, win, T, o, stream);
+    case MODE_SUMS: return launch_m<MODE_SUMS>(g, win, T, o, stream);
+    case MODE_REPORT: return launch_m<MODE_REPORT>(g, win, T, o, stream);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace bz

@@ -1,0 +1,347 @@
+// Served execution: continuous batching of binarization requests.
+//
+// Requests (device-resident images) are queued by bz_server_submit.  A
+// scheduler thread admits queued requests in FIFO order while the summed
+// image+output bytes of the requests on the device stay within the HBM
+// budget and fewer than max_slots requests are in flight, groups the
+// admitted requests of one precision into a batch and launches it through an
+// idle batch slot on that slot's own stream (the batched persistent kernels
+// of batch.cu).  Several batches are in flight at once on different streams,
+// so requests that arrive while others run are admitted as soon as budget and
+// a slot free up, and their work overlaps on the device.  Completion is
+// detected with CUDA events; bz_server_wait blocks on a condition variable.
+//
+// Host-side fault injection for tests (environment variable BZ_FAULT):
+//   "launch"     every batch launch reports BZ_ECUDA without touching the GPU
+//   "slow:<ms>"  completions are reported <ms> milliseconds late
+#include <stdlib.h>
+#include <string.h>
+
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "batch_internal.h"
+
+namespace bz {
+
+enum ReqState { RS_QUEUED, RS_RUNNING, RS_DONE };
+
+struct Request {
+    bz_job job;
+    bz_precision prec;
+    int64_t bytes;
+    ReqState state;
+    bz_status result;
+    bool cancelled;
+};
+
+struct ExecLane {
+    BatchSlot slot;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev = nullptr;
+    bool busy = false;
+    bool failed = false;
+    std::vector<uint64_t> tickets;
+    std::chrono::steady_clock::time_point ready_at;
+};
+
+}  // namespace bz
+
+struct bz_server {
+    int64_t budget = 0;
+    int32_t max_slots = 0;
+    int device = 0;
+    std::mutex mu;
+    std::condition_variable cv_done;
+    std::condition_variable cv_work;
+    std::deque<uint64_t> queue;
+    std::unordered_map<uint64_t, bz::Request> reqs;
+    uint64_t next_ticket = 1;
+    int64_t inflight_bytes = 0;
+    int32_t inflight = 0;
+    std::vector<bz::ExecLane *> lanes;
+    std::thread sched;
+    bool stop = false;
+    bool fault_launch = false;
+    int fault_slow_ms = 0;
+};
+
+namespace bz {
+
+static int64_t job_bytes(const bz_job &j)
+{
+    return j.H * j.in_pitch + j.H * j.out_pitch;
+}
+
+// Completes the lanes whose event fired; called with srv->mu held.
+static void reap(bz_server *srv)
+{
+    const auto now = std::chrono::steady_clock::now();
+    for (ExecLane *L : srv->lanes) {
+        if (!L->busy)
+            continue;
+        bz_status result = BZ_OK;
+        if (!L->failed) {
+            const cudaError_t q = cudaEventQuery(L->ev);
+            if (q == cudaErrorNotReady)
+                continue;
+            if (q != cudaSuccess)
+                result = BZ_ECUDA;
+        } else {
+            result = BZ_ECUDA;
+        }
+        if (srv->fault_slow_ms > 0) {
+            if (L->ready_at.time_since_epoch().count() == 0)
+                L->ready_at = now + std::chrono::milliseconds(srv->fault_slow_ms);
+            if (now < L->ready_at)
+                continue;
+        }
+        for (uint64_t t : L->tickets) {
+            auto it = srv->reqs.find(t);
+            if (it == srv->reqs.end())
+                continue;
+            it->second.state = RS_DONE;
+            it->second.result = it->second.cancelled ? BZ_ECANCELLED : result;
+            srv->inflight_bytes -= it->second.bytes;
+            srv->inflight -= 1;
+        }
+        L->tickets.clear();
+        L->busy = false;
+        L->failed = false;
+        L->ready_at = {};
+    }
+}
+
+// Admits queued requests into idle lanes; called with srv->mu held.
+static void admit(bz_server *srv)
+{
+    for (ExecLane *L : srv->lanes) {
+        if (L->busy)
+            continue;
+        if (srv->queue.empty())
+            return;
+        std::vector<bz_job> batch;
+        std::vector<uint64_t> tickets;
+        bz_precision prec = BZ_FP64;
+        bool have_prec = false;
+        // FIFO admission; requests of another precision wait for a later batch
+        for (auto it = srv->queue.begin(); it != srv->queue.end();) {
+            Request &r = srv->reqs[*it];
+            if (have_prec && r.prec != prec) {
+                ++it;
+                continue;
+            }
+            if (srv->inflight >= srv->max_slots || srv->inflight_bytes + r.bytes > srv->budget)
+                break;  // head-of-line: keep FIFO order under the budget
+            prec = r.prec;
+            have_prec = true;
+            r.state = RS_RUNNING;
+            srv->inflight_bytes += r.bytes;
+            srv->inflight += 1;
+            batch.push_back(r.job);
+            tickets.push_back(*it);
+            it = srv->queue.erase(it);
+        }
+        if (batch.empty())
+            return;
+        L->tickets = tickets;
+        L->busy = true;
+        L->failed = false;
+        if (srv->fault_launch) {
+            L->failed = true;
+            continue;
+        }
+        const bz_status st = run_batch(L->slot, batch.data(), (int32_t)batch.size(), prec,
+                                       L->stream);
+        if (st != BZ_OK || cudaEventRecord(L->ev, L->stream) != cudaSuccess)
+            L->failed = true;
+    }
+}
+
+static void scheduler(bz_server *srv)
+{
+    cudaSetDevice(srv->device);
+    std::unique_lock<std::mutex> lk(srv->mu);
+    for (;;) {
+        reap(srv);
+        admit(srv);
+        srv->cv_done.notify_all();
+        bool any_busy = false;
+        for (ExecLane *L : srv->lanes)
+            any_busy |= L->busy;
+        if (srv->stop && srv->queue.empty() && !any_busy)
+            break;
+        if (any_busy)
+            srv->cv_work.wait_for(lk, std::chrono::microseconds(20));
+        else
+            srv->cv_work.wait_for(lk, std::chrono::milliseconds(5));
+    }
+    srv->cv_done.notify_all();
+}
+
+}  // namespace bz
+
+using namespace bz;
+
+extern "C" {
+
+bz_status bz_server_create(int64_t hbm_budget_bytes, int32_t max_slots, bz_server **out)
+{
+    if (!out || hbm_budget_bytes <= 0 || max_slots < 1)
+        return BZ_EINVAL;
+    *out = nullptr;
+    bz_server *srv = new (std::nothrow) bz_server();
+    if (!srv)
+        return BZ_ENOMEM;
+    srv->budget = hbm_budget_bytes;
+    srv->max_slots = max_slots;
+    if (cudaGetDevice(&srv->device) != cudaSuccess) {
+        delete srv;
+        return BZ_ECUDA;
+    }
+    const char *f = getenv("BZ_FAULT");
+    if (f) {
+        if (strcmp(f, "launch") == 0)
+            srv->fault_launch = true;
+        else if (strncmp(f, "slow:", 5) == 0)
+            srv->fault_slow_ms = atoi(f + 5);
+    }
+    const int nlanes = 4;  // batches in flight at once (independent streams)
+    for (int i = 0; i < nlanes; i++) {
+        ExecLane *L = new ExecLane();
+        if (cudaStreamCreateWithFlags(&L->stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&L->ev, cudaEventDisableTiming) != cudaSuccess) {
+            delete L;
+            bz_server_destroy(srv);
+            return BZ_ECUDA;
+        }
+        srv->lanes.push_back(L);
+    }
+    srv->sched = std::thread(scheduler, srv);
+    *out = srv;
+    return BZ_OK;
+}
+
+bz_status bz_server_submit(bz_server *srv, const bz_job *job, bz_precision precision,
+                           uint64_t *ticket)
+{
+    if (!srv || !job || !ticket)
+        return BZ_EINVAL;
+    if (precision != BZ_FP64 && precision != BZ_FP32 && precision != BZ_FP64_DIRECT)
+        return BZ_EINVAL;
+    const bz_status st = validate_job(*job);
+    if (st != BZ_OK)
+        return st;
+    const int64_t bytes = job_bytes(*job);
+    if (bytes > srv->budget)
+        return BZ_EBUDGET;
+    std::lock_guard<std::mutex> lk(srv->mu);
+    if (srv->stop)
+        return BZ_EINVAL;
+    const uint64_t t = srv->next_ticket++;
+    srv->reqs[t] = Request{*job, precision, bytes, RS_QUEUED, BZ_OK, false};
+    srv->queue.push_back(t);
+    *ticket = t;
+    srv->cv_work.notify_one();
+    return BZ_OK;
+}
+
+bz_status bz_server_cancel(bz_server *srv, uint64_t ticket)
+{
+    if (!srv)
+        return BZ_EINVAL;
+    std::lock_guard<std::mutex> lk(srv->mu);
+    auto it = srv->reqs.find(ticket);
+    if (it == srv->reqs.end())
+        return BZ_EINVAL;
+    if (it->second.state == RS_QUEUED) {
+        for (auto q = srv->queue.begin(); q != srv->queue.end(); ++q)
+            if (*q == ticket) {
+                srv->queue.erase(q);
+                break;
+            }
+        it->second.state = RS_DONE;
+        it->second.result = BZ_ECANCELLED;
+        srv->cv_done.notify_all();
+        return BZ_OK;
+    }
+    // in flight: the GPU work cannot be recalled; it completes and the
+    // request reports BZ_ECANCELLED
+    if (it->second.state == RS_RUNNING) {
+        it->second.cancelled = true;
+        return BZ_OK;
+    }
+    return BZ_EINVAL;  // already finished
+}
+
+bz_status bz_server_wait(bz_server *srv, uint64_t ticket, int32_t timeout_ms)
+{
+    if (!srv)
+        return BZ_EINVAL;
+    std::unique_lock<std::mutex> lk(srv->mu);
+    auto it = srv->reqs.find(ticket);
+    if (it == srv->reqs.end())
+        return BZ_EINVAL;
+    auto done = [&] { return srv->reqs[ticket].state == RS_DONE; };
+    bool timed_out = false;
+    if (timeout_ms < 0) {
+        srv->cv_done.wait(lk, done);
+    } else if (!srv->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), done)) {
+        timed_out = true;
+        Request &r = srv->reqs[ticket];
+        if (r.state == RS_QUEUED) {
+            for (auto q = srv->queue.begin(); q != srv->queue.end(); ++q)
+                if (*q == ticket) {
+                    srv->queue.erase(q);
+                    break;
+                }
+            r.state = RS_DONE;
+            r.result = BZ_ECANCELLED;
+        } else {
+            // running: its buffers are in use until the GPU finishes
+            r.cancelled = true;
+            srv->cv_done.wait(lk, done);
+        }
+    }
+    const bz_status result = srv->reqs[ticket].result;
+    srv->reqs.erase(ticket);
+    if (timed_out)
+        return BZ_ETIMEOUT;
+    return result;
+}
+
+bz_status bz_server_destroy(bz_server *srv)
+{
+    if (!srv)
+        return BZ_EINVAL;
+    {
+        std::lock_guard<std::mutex> lk(srv->mu);
+        srv->stop = true;
+        for (uint64_t t : srv->queue) {
+            srv->reqs[t].state = RS_DONE;
+            srv->reqs[t].result = BZ_ECANCELLED;
+        }
+        srv->queue.clear();
+        srv->cv_work.notify_all();
+        srv->cv_done.notify_all();
+    }
+    if (srv->sched.joinable())
+        srv->sched.join();
+    for (ExecLane *L : srv->lanes) {
+        if (L->stream)
+            cudaStreamSynchronize(L->stream);
+        if (L->ev)
+            cudaEventDestroy(L->ev);
+        if (L->stream)
+            cudaStreamDestroy(L->stream);
+        delete L;
+    }
+    delete srv;
+    return BZ_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,68 @@
+"""GPU parity of the local-quantile path (Sec. 3.4) against the oracle:
+quantile plane and binary output bit-exact."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_helpers import check_packed, out_buffer, to_device
+
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    # H, W, h, w, q_num, q_den
+    (70, 300, 9, 9, 1, 2),
+    (70, 300, 8, 12, 1, 10),
+    (129, 200, 31, 31, 1, 2),
+    (40, 33, 2, 3, 3, 4),
+    (1, 200, 5, 7, 1, 2),
+    (200, 1, 7, 5, 1, 2),
+    (15, 19, 60, 50, 1, 2),
+    (90, 140, 101, 101, 1, 10),
+    (300, 300, 257, 257, 1, 2),  # h*w > 65535: 32-bit histogram counters
+    (50, 70, 5, 5, 0, 1),
+    (50, 70, 5, 5, 1, 1),
+]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built(cuda_device):
+    import paper_1905_13038_gb300 as bz
+    bz.build()
+
+
+@pytest.mark.parametrize("H,W,h,w,qn,qd", CASES)
+def test_window_quantile_exact(H, W, h, w, qn, qd):
+    import paper_1905_13038_gb300 as bz
+    img = synth.document(H, W, 400 + H, stains=1 if min(H, W) > 20 else 0, salt_pepper=0.02,
+                         pitch=W + 3)
+    t, _ = to_device(img, W, misalign=2)
+    Q = bz.window_quantile(t, h, w, qn, qd, W=W).cpu().numpy()
+    np.testing.assert_array_equal(Q, oracle.window_quantile(img, h, w, qn, qd, W=W))
+
+
+@pytest.mark.parametrize("H,W,h,w,qn,qd", CASES)
+@pytest.mark.parametrize("offset", [8, 0, -5])
+def test_binarize_quantile_exact(H, W, h, w, qn, qd, offset):
+    import paper_1905_13038_gb300 as bz
+    img = synth.document(H, W, 500 + W, salt_pepper=0.02)
+    t, _ = to_device(img)
+    out = out_buffer(H, W, extra=1)
+    bz.binarize_quantile(t, h, w, qn, qd, offset, out=out)
+    _, ref = oracle.binarize_quantile(img, h, w, qn, qd, offset)
+    check_packed(out, ref, W)
+
+
+@pytest.mark.parametrize("h,w,qn,qd", [(31, 31, 1, 2), (31, 31, 1, 10), (101, 101, 1, 2), (101, 101, 1, 10)])
+def test_quantile_page_full(h, w, qn, qd):
+    """2048 x 2048 page with 2% salt-and-pepper: the full quantile plane and
+    binary output against the (parallel) sliding-histogram oracle."""
+    import paper_1905_13038_gb300 as bz
+    img = synth.quantile_page()
+    t, W = to_device(img)
+    nt = oracle.max_threads()
+    Q = bz.window_quantile(t, h, w, qn, qd).cpu().numpy()
+    np.testing.assert_array_equal(Q, oracle.window_quantile(img, h, w, qn, qd, threads=nt))
+    out = bz.binarize_quantile(t, h, w, qn, qd, 8)
+    _, ref = oracle.binarize_quantile(img, h, w, qn, qd, 8, threads=nt)
+    check_packed(out, ref, W)
