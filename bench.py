@@ -223,7 +223,8 @@ def main():
         for s in range(args.steps):
             step(s)
     torch.cuda.synchronize(dev)
-    graph.replay()  # untimed replay: page in the graph
+    with torch.cuda.stream(stream):
+        graph.replay()  # untimed replay: page in the graph
     torch.cuda.synchronize(dev)
 
     def barrier():
@@ -236,9 +237,10 @@ def main():
     e1 = torch.cuda.Event(enable_timing=True)
     with ClockSampler(local if world > 1 else 0) as clk:
         barrier()
-        e0.record(stream)
-        graph.replay()
-        e1.record(stream)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            graph.replay()  # replays on the current stream: `stream`
+            e1.record(stream)
         barrier()
     ms = e0.elapsed_time(e1)
     if world > 1:

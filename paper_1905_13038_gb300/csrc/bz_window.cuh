@@ -62,103 +62,6 @@ struct Outputs {
     unsigned long long *maxdt_bits; // MODE_REPORT (double bits, >= 0)
 };
 
-// ---------------------------------------------------------------- loads --
-// 8 gray levels of row `row`, columns col0 .. col0+7; 0 outside the image.
-// VEC: image base and pitch are multiples of 8, so aligned 8-byte loads of
-// the row never leave [row start, row start + pitch).
-template <bool VEC>
-__device__ __forceinline__ uint2 load8(const Image &g, int64_t row, int64_t col0)
-{
-    if (row < 0 || row >= g.H)
-        return make_uint2(0u, 0u);
-    const uint8_t *rp = g.img + row * g.pitch;
-    if (VEC && col0 >= 0 && col0 + 8 <= g.W) {
-        const int64_t a8 = col0 & ~(int64_t)7;
-        const int k = (int)(col0 - a8);
-        const uint2 p = __ldg(reinterpret_cast<const uint2 *>(rp + a8));
-        if (k == 0)
-            return p;
-        const uint2 q = __ldg(reinterpret_cast<const uint2 *>(rp + a8 + 8));
-        const unsigned sel = (unsigned)(k & 3) * 0x1111u + 0x3210u;
-        uint2 v;
-        if (k < 4) {
-            v.x = __byte_perm(p.x, p.y, sel);
-            v.y = __byte_perm(p.y, q.x, sel);
-        } else {
-            v.x = __byte_perm(p.y, q.x, sel);
-            v.y = __byte_perm(q.x, q.y, sel);
-        }
-        return v;
-    }
-    uint32_t lo = 0, hi = 0;
-#pragma unroll
-    for (int m = 0; m < 8; m++) {
-        const int64_t c = col0 + m;
-        const uint32_t b = (c >= 0 && c < g.W) ? (uint32_t)rp[c] : 0u;
-        if (m < 4)
-            lo |= b << (8 * m);
-        else
-            hi |= b << (8 * (m - 4));
-    }
-    return make_uint2(lo, hi);
-}
-
-// 4 gray levels at columns c4 .. c4+3 (c4 a multiple of 4), 0 outside.
-template <bool VEC>
-__device__ __forceinline__ uint32_t load4_aligned(const Image &g, int64_t row, int64_t c4)
-{
-    if (row < 0 || row >= g.H)
-        return 0u;
-    const uint8_t *rp = g.img + row * g.pitch;
-    if (VEC && c4 >= 0 && c4 + 4 <= g.W)
-        return __ldg(reinterpret_cast<const uint32_t *>(rp + c4));
-    uint32_t v = 0;
-#pragma unroll
-    for (int m = 0; m < 4; m++) {
-        const int64_t c = c4 + m;
-        if (c >= 0 && c < g.W)
-            v |= (uint32_t)rp[c] << (8 * m);
-    }
-    return v;
-}
-
-__device__ __forceinline__ uint32_t byte_of(uint2 v, int m)
-{
-    return ((m < 4 ? v.x : v.y) >> (8 * (m & 3))) & 0xFFu;
-}
-
-// Sum and sum of squares of row `row` over columns [c0, c0 + cnt), spread
-// over the warp (each lane returns its partial; caller reduces).
-template <bool VEC>
-__device__ __forceinline__ void row_partial(const Image &g, int64_t row, int64_t c0, int cnt,
-                                            int lane, uint32_t &s1, uint32_t &s2)
-{
-    if (row < 0 || row >= g.H || cnt <= 0)
-        return;
-    const int64_t a4 = c0 >= 0 ? (c0 & ~(int64_t)3) : -((-c0 + 3) & ~(int64_t)3);
-    const int64_t end = c0 + cnt;  // exclusive
-    for (int64_t c4 = a4 + 4 * lane; c4 < end; c4 += 128) {
-        uint32_t wd = load4_aligned<VEC>(g, row, c4);
-        // keep only the bytes whose column lies in [c0, end)
-        uint32_t keep = 0xFFFFFFFFu;
-        if (c4 < c0)
-            keep &= 0xFFFFFFFFu << (8 * (int)(c0 - c4));
-        if (c4 + 4 > end)
-            keep &= 0xFFFFFFFFu >> (8 * (int)(c4 + 4 - end));
-        wd &= keep;
-        s1 = __dp4a(wd, 0x01010101u, s1);
-        s2 = __dp4a(wd, wd, s2);
-    }
-}
-
-__device__ __forceinline__ int32_t warp_allsum(int32_t v)
-{
-#pragma unroll
-    for (int d = 16; d >= 1; d >>= 1)
-        v += __shfl_xor_sync(0xFFFFFFFFu, v, d);
-    return v;
-}
-
 template <typename T>
 __device__ __forceinline__ T warp_incl_scan(T v, int lane)
 {
@@ -193,87 +96,146 @@ __device__ __forceinline__ float sqrt_approx(float x)
     return y;
 }
 
-struct Decision {
-    uint32_t bit;       // 0/1 decision
-    bool certain;       // decision certified equal to the canonical FP64 one
-    float t32;          // FP32 threshold (report mode)
-};
-
-// FP32 evaluation of the threshold from the exact integers, with the
-// certified margin.
-__device__ __forceinline__ Decision decide_f32(const Thresh &T, uint32_t I, uint32_t S1, long long V,
-                                               float inv_n)
+// ------------------------------------------------------------ the tile --
+// Byte m (0..7) of an 8-byte group, zero-extended.
+__device__ __forceinline__ int32_t byte_at(uint2 v, int m)
 {
-    const float S1f = __uint2float_rn(S1);
-    const float Vf = __ll2float_rn(V);
-    const float m = S1f * inv_n;
-    const float var = (Vf * inv_n) * inv_n;
-    const float s = sqrt_approx(var);
-    const float g = fmaf(T.beta, m, T.gamma);
-    const float t = fmaf(g, s, T.alpha * m);
-    const float mag = fmaf(fmaf(T.abeta, m, T.agamma), s, T.aalpha * m);
-    const float E = fmaf(T.eps, mag, T.delta64);
-    const float If = __uint2float_rn(I);
-    Decision d;
-    d.t32 = t;
-    d.bit = If > t ? 1u : 0u;
-    d.certain = (If > t + E) || (If < t - E);
-    return d;
+    return (int32_t)__byte_perm(m < 4 ? v.x : v.y, 0u, 0x4440u | (unsigned)(m & 3));
 }
 
-// ------------------------------------------------------------ the tile --
+// 8 gray levels at columns col .. col+7 of the row starting at rp (which is
+// an in-image row); columns outside [0, W) read as 0.  `fast`: the 8 bytes
+// lie inside the row and VEC alignment holds; k = col & 7 (warp-uniform);
+// sel = byte_perm selector for offset k & 3.
+template <bool VEC>
+__device__ __forceinline__ uint2 ld8(const uint8_t *rp, int64_t col, bool fast, int k, unsigned sel,
+                                     int64_t W)
+{
+    if (VEC && fast) {
+        const uint8_t *p = rp + (col - k);
+        const uint2 a = __ldg(reinterpret_cast<const uint2 *>(p));
+        if (k == 0)
+            return a;
+        const uint2 b = __ldg(reinterpret_cast<const uint2 *>(p + 8));
+        return k < 4 ? make_uint2(__byte_perm(a.x, a.y, sel), __byte_perm(a.y, b.x, sel))
+                     : make_uint2(__byte_perm(a.y, b.x, sel), __byte_perm(b.x, b.y, sel));
+    }
+    uint32_t lo = 0, hi = 0;
+#pragma unroll
+    for (int m = 0; m < 8; m++) {
+        const int64_t c = col + m;
+        const uint32_t b = (c >= 0 && c < W) ? (uint32_t)rp[c] : 0u;
+        if (m < 4)
+            lo |= b << (8 * m);
+        else
+            hi |= b << (8 * (m - 4));
+    }
+    return make_uint2(lo, hi);
+}
+
+// Anchor row sums: this lane's share of the columns [c0, c0 + cnt) of one
+// row, as (sum, sum of squares); words of 4 columns, lane-strided.
+template <bool VEC>
+__device__ __forceinline__ void anchor_words(const uint8_t *rp, int64_t a4, int64_t c0, int64_t end,
+                                             int64_t W, int lane, uint32_t &s1, uint32_t &s2)
+{
+    for (int64_t c4 = a4 + 4 * lane; c4 < end; c4 += 128) {
+        uint32_t wd;
+        if (VEC && c4 >= 0 && c4 + 4 <= W) {
+            wd = __ldg(reinterpret_cast<const uint32_t *>(rp + c4));
+        } else {
+            wd = 0;
+#pragma unroll
+            for (int m = 0; m < 4; m++) {
+                const int64_t c = c4 + m;
+                if (c >= 0 && c < W)
+                    wd |= (uint32_t)rp[c] << (8 * m);
+            }
+        }
+        uint32_t keep = 0xFFFFFFFFu;
+        if (c4 < c0)
+            keep &= 0xFFFFFFFFu << (8 * (int)(c0 - c4));
+        if (c4 + 4 > end)
+            keep &= 0xFFFFFFFFu >> (8 * (int)(c4 + 4 - end));
+        wd &= keep;
+        s1 = __dp4a(wd, 0x01010101u, s1);
+        s2 = __dp4a(wd, wd, s2);
+    }
+}
+
+// Canonical FP64 decision for one pixel (kept out of line so that no FP64
+// work is scheduled on the FP32 hot path).
+static __device__ __noinline__ uint32_t fp64_bit(int method, uint32_t I, uint32_t S1, uint64_t S2,
+                                          uint32_t n, double k, double R)
+{
+    return ((double)I <= canonical_t(method, S1, S2, n, k, R)) ? 0u : 1u;
+}
+
 // S2T: uint32_t when h*w <= 66051 (S2 < 2^32), else unsigned long long.
 template <int MODE, bool VEC, typename S2T>
 __device__ __forceinline__ void window_tile(const Image &g, const Window &win, const Thresh &T,
                                             const Outputs &o, int64_t x0, int64_t y0, int64_t y1,
                                             int lane)
 {
+    const int64_t W = g.W, H = g.H;
     const int64_t j0 = x0 + (int64_t)kColsPerLane * lane;
     const int l = win.l, r = win.r, oo = win.o, u = win.u;
 
-    // per-column clipped widths and their reciprocals (Algorithm 1 count)
+    // ---- per-lane constants
+    const int64_t colA = j0 + r, colB = j0 - l;  // entering / leaving edge columns
+    const bool fastA = VEC && colA >= 0 && colA + 8 <= W;
+    const bool fastB = VEC && colB >= 0 && colB + 8 <= W;
+    const int kA = (int)(colA & 7), kB = (int)(colB & 7);  // warp-uniform
+    const unsigned selA = (unsigned)(kA & 3) * 0x1111u + 0x3210u;
+    const unsigned selB = (unsigned)(kB & 3) * 0x1111u + 0x3210u;
+    const bool fastP = VEC && j0 + 8 <= W;
+
     uint32_t cols[kColsPerLane];
     float inv_cols[kColsPerLane];
 #pragma unroll
     for (int m = 0; m < kColsPerLane; m++) {
         const int64_t j = j0 + m;
-        int64_t hi = j + r < g.W - 1 ? j + r : g.W - 1;
-        int64_t lo = j - l > -1 ? j - l : -1;
-        int64_t c = hi - lo;
-        if (c < 1)
-            c = 1;  // only for j >= W (outputs discarded)
-        cols[m] = (uint32_t)c;
-        inv_cols[m] = __frcp_rn((float)c);
+        const int64_t hi = j + r < W - 1 ? j + r : W - 1;
+        const int64_t lo = j - l > -1 ? j - l : -1;
+        const int64_t c = hi - lo;
+        cols[m] = (uint32_t)(c < 1 ? 1 : c);  // c < 1 only for j >= W
+        inv_cols[m] = __frcp_rn((float)cols[m]);
     }
+    // anchor window: columns [x0-l, x0-1+r] (the window of column x0-1)
+    const int64_t ac0 = x0 - l, aend = x0 + r;
+    const int64_t a4 = ac0 >= 0 ? (ac0 & ~(int64_t)3) : -((-ac0 + 3) & ~(int64_t)3);
 
-    // warm-up: E over the window rows of y0, and the anchor S(y0, x0-1)
+    // ---- warm-up: E and the anchor for row y0 (window rows (y0-o, y0+u])
     int32_t E1[kColsPerLane], E2[kColsPerLane];
 #pragma unroll
     for (int m = 0; m < kColsPerLane; m++) {
         E1[m] = 0;
         E2[m] = 0;
     }
-    uint32_t a1p = 0, a2p = 0;  // lane partials of the anchor
-    const int64_t ac0 = x0 - l;  // anchor window columns [x0-l, x0-1+r]
-    const int aw = win.w;
-    for (int64_t a = y0 - oo + 1; a <= y0 + u; a++) {
-        if (a < 0 || a >= g.H)
-            continue;
-        const uint2 A = load8<VEC>(g, a, j0 + r);
-        const uint2 B = load8<VEC>(g, a, j0 - l);
-#pragma unroll
-        for (int m = 0; m < kColsPerLane; m++) {
-            const int32_t av = (int32_t)byte_of(A, m), bv = (int32_t)byte_of(B, m);
-            E1[m] += av - bv;
-            E2[m] += av * av - bv * bv;
-        }
-        row_partial<VEC>(g, a, ac0, aw, lane, a1p, a2p);
-    }
-    S2T A2 = (S2T)(uint32_t)0;
-    uint32_t A1 = (uint32_t)warp_allsum((int32_t)a1p);
+    uint32_t a1p = 0, a2p = 0;
     {
-        // a2 partials may exceed int32 when summed over h rows: reduce in 64 bits
-        unsigned long long v = (unsigned long long)(uint32_t)a2p;
+        int64_t a_lo = y0 - oo + 1, a_hi = y0 + u;
+        if (a_lo < 0)
+            a_lo = 0;
+        if (a_hi > H - 1)
+            a_hi = H - 1;
+        for (int64_t a = a_lo; a <= a_hi; a++) {
+            const uint8_t *rp = g.img + a * g.pitch;
+            const uint2 A = ld8<VEC>(rp, colA, fastA, kA, selA, W);
+            const uint2 B = ld8<VEC>(rp, colB, fastB, kB, selB, W);
+#pragma unroll
+            for (int m = 0; m < kColsPerLane; m++) {
+                const int32_t av = byte_at(A, m), bv = byte_at(B, m);
+                E1[m] += av - bv;
+                E2[m] += av * av - bv * bv;
+            }
+            anchor_words<VEC>(rp, a4, ac0, aend, W, lane, a1p, a2p);
+        }
+    }
+    uint32_t A1 = __reduce_add_sync(0xFFFFFFFFu, a1p);
+    S2T A2;
+    {
+        unsigned long long v = (unsigned long long)a2p;
 #pragma unroll
         for (int d = 16; d >= 1; d >>= 1)
             v += __shfl_xor_sync(0xFFFFFFFFu, v, d);
@@ -283,33 +245,52 @@ __device__ __forceinline__ void window_tile(const Image &g, const Window &win, c
     unsigned long long nfb = 0, nflip = 0;
     double maxdt = 0.0;
 
+    // prefetched slide data for the next row
+    uint2 nA = make_uint2(0, 0), nB = nA, nC = nA, nD = nA;
+    uint32_t nd1 = 0, nd2 = 0;  // anchor increment partials (entering - leaving)
+    auto prefetch = [&](int64_t i) {
+        const int64_t ra = i + u, rb = i - oo;
+        nA = nB = nC = nD = make_uint2(0, 0);
+        uint32_t e1 = 0, e2 = 0, x1 = 0, x2 = 0;
+        if (ra < H) {
+            const uint8_t *rp = g.img + ra * g.pitch;
+            nA = ld8<VEC>(rp, colA, fastA, kA, selA, W);
+            nB = ld8<VEC>(rp, colB, fastB, kB, selB, W);
+            anchor_words<VEC>(rp, a4, ac0, aend, W, lane, e1, e2);
+        }
+        if (rb >= 0) {
+            const uint8_t *rp = g.img + rb * g.pitch;
+            nC = ld8<VEC>(rp, colA, fastA, kA, selA, W);
+            nD = ld8<VEC>(rp, colB, fastB, kB, selB, W);
+            anchor_words<VEC>(rp, a4, ac0, aend, W, lane, x1, x2);
+        }
+        nd1 = e1 - x1;
+        nd2 = e2 - x2;
+    };
+    if (y0 + 1 < y1)
+        prefetch(y0 + 1);
+
     for (int64_t i = y0; i < y1; i++) {
         if (i > y0) {
             // slide every E and the anchor from row i-1 to row i
-            const int64_t ra = i + u, rb = i - oo;
-            const uint2 A = load8<VEC>(g, ra, j0 + r);
-            const uint2 B = load8<VEC>(g, ra, j0 - l);
-            const uint2 C = load8<VEC>(g, rb, j0 + r);
-            const uint2 D = load8<VEC>(g, rb, j0 - l);
 #pragma unroll
             for (int m = 0; m < kColsPerLane; m++) {
-                const int32_t av = (int32_t)byte_of(A, m), bv = (int32_t)byte_of(B, m);
-                const int32_t cv = (int32_t)byte_of(C, m), dv = (int32_t)byte_of(D, m);
-                E1[m] += (av - bv) - (cv - dv);
-                E2[m] += (av * av - bv * bv) - (cv * cv - dv * dv);
+                const int32_t av = byte_at(nA, m), bv = byte_at(nB, m);
+                const int32_t cv = byte_at(nC, m), dv = byte_at(nD, m);
+                E1[m] += (av + dv) - (bv + cv);
+                E2[m] += (av * av + dv * dv) - (bv * bv + cv * cv);
             }
-            uint32_t d1 = 0, d2 = 0, e1 = 0, e2 = 0;
-            row_partial<VEC>(g, ra, ac0, aw, lane, d1, d2);
-            row_partial<VEC>(g, rb, ac0, aw, lane, e1, e2);
-            A1 += (uint32_t)warp_allsum((int32_t)(d1 - e1));
-            A2 += (S2T)(int64_t)warp_allsum((int32_t)(d2 - e2));
+            A1 += (uint32_t)__reduce_add_sync(0xFFFFFFFFu, nd1);
+            A2 += (S2T)(int64_t)(int32_t)__reduce_add_sync(0xFFFFFFFFu, nd2);
+            if (i + 1 < y1)
+                prefetch(i + 1);
         }
 
         // window sums along the row: lane prefix + warp scan + anchor
         uint32_t p1[kColsPerLane];
         S2T p2[kColsPerLane];
         uint32_t run1 = 0;
-        S2T run2 = (S2T)(uint32_t)0;
+        S2T run2 = (S2T)0u;
 #pragma unroll
         for (int m = 0; m < kColsPerLane; m++) {
             run1 += (uint32_t)E1[m];
@@ -322,71 +303,98 @@ __device__ __forceinline__ void window_tile(const Image &g, const Window &win, c
         const uint32_t off1 = A1 + (inc1 - run1);
         const S2T off2 = A2 + (inc2 - run2);
 
-        const int64_t rows = (i + u < g.H - 1 ? i + u : g.H - 1) - (i - oo > -1 ? i - oo : -1);
-        const float inv_rows = __frcp_rn((float)rows);
+        const int64_t rows = (i + u < H - 1 ? i + u : H - 1) - (i - oo > -1 ? i - oo : -1);
+        const uint32_t nrow = (uint32_t)rows;
 
         if (MODE == MODE_SUMS) {
 #pragma unroll
             for (int m = 0; m < kColsPerLane; m++) {
                 const int64_t j = j0 + m;
-                if (j < g.W) {
-                    const int64_t idx = i * g.W + j;
+                if (j < W) {
+                    const int64_t idx = i * W + j;
                     if (o.S1)
                         o.S1[idx] = off1 + p1[m];
                     if (o.S2)
                         o.S2[idx] = (uint64_t)(off2 + p2[m]);
                     if (o.n)
-                        o.n[idx] = (uint32_t)rows * cols[m];
+                        o.n[idx] = nrow * cols[m];
                 }
             }
             continue;
         }
 
-        const uint2 P = load8<VEC>(g, i, j0);  // the pixels themselves
-        uint32_t byte = 0;
+        const float inv_rows = __frcp_rn((float)rows);
+        const uint8_t *prow = g.img + i * g.pitch;
+        const uint2 P = ld8<VEC>(prow, j0, fastP, 0, 0x3210u, W);
+        uint32_t byte = 0, undecided = 0;
 #pragma unroll
         for (int m = 0; m < kColsPerLane; m++) {
-            const int64_t j = j0 + m;
             const uint32_t S1 = off1 + p1[m];
             const uint64_t S2 = (uint64_t)(off2 + p2[m]);
-            const uint32_t n = (uint32_t)rows * cols[m];
-            const uint32_t I = byte_of(P, m);
-            const long long V = (long long)n * (long long)S2 - (long long)S1 * (long long)S1;
+            const uint32_t n = nrow * cols[m];
             uint32_t bit;
             if (MODE == MODE_FP64_DIRECT) {
-                bit = ((double)I <= canonical_t(T.method, S1, S2, n, T.k, T.R)) ? 0u : 1u;
+                bit = fp64_bit(T.method, (uint32_t)byte_at(P, m), S1, S2, n, T.k, T.R);
             } else {
-                const Decision d = decide_f32(T, I, S1, V, inv_rows * inv_cols[m]);
-                bit = d.bit;
+                // exact V = n S2 - S1^2 (< 2^48), converted from two 32-bit halves
+                const uint64_t V = (uint64_t)n * S2 - (uint64_t)S1 * (uint64_t)S1;
+                const float Vhi = __int_as_float(0x4B000000u | (uint32_t)(V >> 32)) - 8388608.0f;
+                const float Vf = fmaf(Vhi, 4294967296.0f, __uint2float_rn((uint32_t)V));
+                const float inv_n = inv_rows * inv_cols[m];
+                const float mu = __uint2float_rn(S1) * inv_n;
+                const float var = (Vf * inv_n) * inv_n;
+                const float s = sqrt_approx(var);
+                const float t = fmaf(fmaf(T.beta, mu, T.gamma), s, T.alpha * mu);
+                // the pixel as a float: 2^23 + I from its byte, minus 2^23
+                const float If =
+                    __int_as_float(__byte_perm(m < 4 ? P.x : P.y, 0x4B000000u, 0x7440u | (unsigned)(m & 3))) -
+                    8388608.0f;
+                const float d = If - t;
+                bit = d > 0.0f ? 1u : 0u;
                 if (MODE == MODE_FP64) {
-                    if (!d.certain && j < g.W) {
-                        bit = ((double)I <= canonical_t(T.method, S1, S2, n, T.k, T.R)) ? 0u : 1u;
-                        nfb++;
-                    }
+                    const float mag = fmaf(fmaf(T.abeta, mu, T.agamma), s, T.aalpha * mu);
+                    const float E = fmaf(T.eps, mag, T.delta64);
+                    undecided |= (fabsf(d) <= E ? 1u : 0u) << m;
                 } else if (MODE == MODE_REPORT) {
-                    if (j < g.W) {
+                    if (j0 + m < W) {
                         const double t64 = canonical_t(T.method, S1, S2, n, T.k, T.R);
+                        const uint32_t I = (uint32_t)byte_at(P, m);
                         const uint32_t b64 = ((double)I <= t64) ? 0u : 1u;
-                        nflip += (b64 != d.bit);
-                        const double dt = fabs((double)d.t32 - t64);
+                        nflip += (b64 != bit);
+                        const double dt = fabs((double)t - t64);
                         maxdt = dt > maxdt ? dt : maxdt;
                     }
                 }
             }
-            if (j < g.W)
-                byte |= bit << m;
+            byte |= bit << m;
         }
-        if (MODE != MODE_REPORT && j0 < g.W)
+        if (MODE == MODE_FP64) {
+            // near-ties: canonical FP64 evaluation, off the hot path
+            if (j0 + 8 > W)
+                undecided &= (1u << (j0 < W ? W - j0 : 0)) - 1u;
+            if (__any_sync(0xFFFFFFFFu, undecided != 0) && undecided) {
+#pragma unroll
+                for (int m = 0; m < kColsPerLane; m++) {
+                    if (undecided >> m & 1u) {
+                        const uint32_t b = fp64_bit(T.method, (uint32_t)byte_at(P, m), off1 + p1[m],
+                                                    (uint64_t)(off2 + p2[m]), nrow * cols[m], T.k, T.R);
+                        byte = (byte & ~(1u << m)) | (b << m);
+                    }
+                }
+                nfb += __popc(undecided);
+            }
+        }
+        if (MODE != MODE_REPORT && j0 < W) {
+            if (j0 + 8 > W)
+                byte &= (1u << (W - j0)) - 1u;  // padding bits are 0
             o.bits[i * o.out_pitch + (j0 >> 3)] = (uint8_t)byte;
+        }
     }
 
     if (MODE == MODE_FP64 && o.fallbacks) {
-        unsigned long long v = nfb;
-#pragma unroll
-        for (int d = 16; d >= 1; d >>= 1)
-            v += __shfl_xor_sync(0xFFFFFFFFu, v, d);
+        const unsigned v = __reduce_add_sync(0xFFFFFFFFu, (unsigned)nfb);
         if (lane == 0 && v)
-            atomicAdd(o.fallbacks, v);
+            atomicAdd(o.fallbacks, (unsigned long long)v);
     }
     if (MODE == MODE_REPORT) {
         unsigned long long v = nflip;

@@ -10,7 +10,7 @@ namespace bz {
 constexpr int kWarpsPerBlock = 4;
 
 template <int MODE, bool VEC, typename S2T>
-__global__ void __launch_bounds__(32 * kWarpsPerBlock)
+__global__ void __launch_bounds__(32 * kWarpsPerBlock, 4)
     k_window(Image g, Window win, Thresh T, Outputs o, int64_t tiles_x, int64_t tiles_total,
              int64_t tile_h)
 {
@@ -66,13 +66,13 @@ Thresh make_thresh(int method, double k, double R)
 int64_t window_tile_rows(int64_t H, int64_t W, int h, int w)
 {
     (void)w;
-    // Enough warps to fill the GPU (~16 per SM on 152 SMs) while keeping the
-    // warm-up (h rows, half the cost of a sliding row) a modest fraction.
+    // About 8 warps per SM on 152 SMs when the image allows it, but never
+    // tiles shorter than the window height (the warm-up of a tile costs about
+    // half a sliding row per window row).
     const int64_t strips = (W + kTileCols - 1) / kTileCols;
-    const int64_t want_warps = 152 * 16;
-    int64_t by_par = (H * strips + want_warps - 1) / want_warps;
-    int64_t by_warm = 2 * (int64_t)h;
-    int64_t th = by_par > by_warm ? by_par : by_warm;
+    const int64_t want_warps = 152 * 8;
+    const int64_t by_par = (H * strips + want_warps - 1) / want_warps;
+    int64_t th = by_par > (int64_t)h ? by_par : (int64_t)h;
     if (th < 16)
         th = 16;
     if (th > H)
