@@ -152,6 +152,28 @@ typedef struct {
 bz_status binarize_batch(const bz_job *jobs_host, int32_t n,
                          bz_precision precision, void *stream);
 
+/* Allocation-free variant of binarize_batch.  The paper has no counterpart:
+ * this exists for callers that cannot allocate device memory at call time,
+ * such as services that reserve all of the GPU's memory up front in their own
+ * arena or caching allocator (a library cudaMalloc would fail or fragment
+ * their pool) and latency-critical loops that must not wait on the driver's
+ * allocator.  It runs the same persistent kernels as binarize_batch, with
+ * identical results, but its device work list lives in one fixed array that
+ * is part of the library image (about 150 KB, held by every GPU that loads
+ * the library until the process exits), and it calls no allocation routine.
+ *   - n <= BZ_NOALLOC_MAX_JOBS; larger n returns BZ_EINVAL, nothing launched.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress, with that device current); make that first
+ *     call before any stream capture on the device.
+ *   - Every call on a device shares the one work list: calls whose work
+ *     overlaps on the GPU (for instance on two streams) race and corrupt each
+ *     other's list.  Order them on one stream or synchronise in between.
+ *   - jobs_host is read before the call returns; the copy to the device is
+ *     ordered on `stream`.  Argument errors are reported synchronously. */
+#define BZ_NOALLOC_MAX_JOBS 512
+bz_status binarize_batch_noalloc(const bz_job *jobs_host, int32_t n,
+                                 bz_precision precision, void *stream);
+
 /* ---------------------------------------------------------------------- */
 /* Served execution: continuous batching of requests on the device.       */
 /* ---------------------------------------------------------------------- */

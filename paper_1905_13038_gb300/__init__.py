@@ -21,6 +21,7 @@ __all__ = [
     "build", "library_path", "FP64", "FP32", "FP64_DIRECT", "SAUVOLA", "NIBLACK", "QUANTILE",
     "BinarizeError", "binarize_sauvola", "binarize_niblack", "binarize_quantile", "window_sums",
     "window_quantile", "binarize_precision_report", "last_fp64_fallbacks", "Job", "binarize_batch",
+    "binarize_batch_noalloc",
     "Server", "status_string",
 ]
 
@@ -78,6 +79,7 @@ def _load():
         "binarize_precision_report": ([i32, P, i64, i64, i64, i32, i32, f64, f64, P, P, P], st),
         "bz_last_fp64_fallbacks": ([P], i64),
         "binarize_batch": ([ctypes.POINTER(_JobC), i32, st, P], st),
+        "binarize_batch_noalloc": ([ctypes.POINTER(_JobC), i32, st, P], st),
         "bz_server_create": ([i64, i32, ctypes.POINTER(P)], st),
         "bz_server_submit": ([P, ctypes.POINTER(_JobC), st, ctypes.POINTER(ctypes.c_uint64)], st),
         "bz_server_wait": ([P, ctypes.c_uint64, i32], st),
@@ -210,6 +212,16 @@ class Job:
 def binarize_batch(jobs, precision="fp64", stream=None):
     arr = (_JobC * len(jobs))(*[j.c for j in jobs])
     _check("binarize_batch", _load().binarize_batch(arr, len(jobs), _PREC[precision], _stream(stream)))
+    return [j.out for j in jobs]
+
+
+def binarize_batch_noalloc(jobs, precision="fp64", stream=None):
+    """Same results as binarize_batch without any device allocation (at most
+    512 jobs per call; calls that overlap on the GPU race on the shared work
+    list)."""
+    arr = (_JobC * len(jobs))(*[j.c for j in jobs])
+    _check("binarize_batch_noalloc",
+           _load().binarize_batch_noalloc(arr, len(jobs), _PREC[precision], _stream(stream)))
     return [j.out for j in jobs]
 
 

@@ -10,6 +10,8 @@
 // the single-image kernels, so every result is bit-identical to the
 // single-image call.  The graph topology is fixed per precision; only the
 // list contents change between launches.
+#include <stddef.h>
+
 #include <algorithm>
 #include <mutex>
 #include <vector>
@@ -395,4 +397,189 @@ extern "C" bz_status binarize_batch(const bz_job *jobs_host, int32_t n, bz_preci
     if (!s)
         return BZ_ECUDA;
     return bz::run_batch(*s, jobs_host, n, precision, (cudaStream_t)stream);
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free batched entry point.
+//
+// Some callers cannot allocate device memory when they binarize: services
+// that reserve all of the GPU's memory up front in their own arena or caching
+// allocator (so a cudaMalloc from inside a library would fail or fragment
+// their pool), and latency-critical loops that must never wait on the
+// driver's allocator.  binarize_batch keeps its work list in device memory it
+// allocates on first use; this variant keeps it in one fixed array that is
+// part of the library image instead, so it never allocates.  The cost is a
+// hard cap on the number of jobs per call and a single shared work list.
+// ---------------------------------------------------------------------------
+namespace bz {
+
+constexpr int kNoAllocMaxJobs = BZ_NOALLOC_MAX_JOBS;
+
+struct NoAllocTable {
+    BatchHeader hdr;
+    unsigned long long fallbacks;  // FP64-fallback counter of the call
+    WinJobDev win[kNoAllocMaxJobs];
+    QJobDev q[kNoAllocMaxJobs];
+};
+
+// The work list of every binarize_batch_noalloc call on a device.  In host
+// code this name is only a host-side stand-in: the device address must come
+// from cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocTable)];
+
+static std::mutex g_noalloc_mu;             // guards the host staging copy
+static NoAllocTable g_noalloc_host;         // host staging copy (static storage)
+static int g_noalloc_order[kNoAllocMaxJobs];
+static void *g_noalloc_dev[64] = {nullptr};  // symbol address per device
+
+// Once per device, with that device current: resolve the device address of
+// the static work list.  Returns nullptr on failure.
+static void *noalloc_scratch_address(int device)
+{
+    if (device < 0 || device >= 64)
+        return nullptr;
+    if (!g_noalloc_dev[device]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        g_noalloc_dev[device] = p;
+    }
+    return g_noalloc_dev[device];
+}
+
+template <int MODE>
+static cudaError_t noalloc_launch(NoAllocTable *dev, int nsm, cudaStream_t stream)
+{
+    const size_t qsmem = batch_quant_smem();
+    cudaError_t e = cudaFuncSetAttribute(k_batch_quantile,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qsmem);
+    if (e != cudaSuccess)
+        return e;
+    int occ_w = 0, occ_q = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_w, k_batch_window<MODE>, 32 * kBatchWarps, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_q, k_batch_quantile, kQuantNT, qsmem);
+    if (occ_w < 1)
+        occ_w = 1;
+    if (occ_q < 1)
+        occ_q = 1;
+    k_batch_window<MODE><<<nsm * occ_w, 32 * kBatchWarps, 0, stream>>>(&dev->hdr, dev->win,
+                                                                       &dev->fallbacks);
+    k_batch_quantile<<<nsm * occ_q, kQuantNT, qsmem, stream>>>(&dev->hdr, dev->q);
+    return cudaGetLastError();
+}
+
+}  // namespace bz
+
+extern "C" bz_status binarize_batch_noalloc(const bz_job *jobs, int32_t n, bz_precision precision,
+                                            void *stream)
+{
+    using namespace bz;
+    if (n < 0 || (n > 0 && !jobs))
+        return BZ_EINVAL;
+    if (n > kNoAllocMaxJobs)
+        return BZ_EINVAL;  // more jobs than the static work list holds
+    int mode;
+    switch (precision) {
+    case BZ_FP64: mode = 0; break;
+    case BZ_FP32: mode = 1; break;
+    case BZ_FP64_DIRECT: mode = 2; break;
+    default: return BZ_EINVAL;
+    }
+    for (int32_t i = 0; i < n; i++) {
+        const bz_status st = validate_job(jobs[i]);
+        if (st != BZ_OK)
+            return st;
+    }
+    if (n == 0)
+        return BZ_OK;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess)
+        return BZ_ECUDA;
+    int nsm = 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
+        return BZ_ECUDA;
+
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    NoAllocTable *dtab = (NoAllocTable *)noalloc_scratch_address(dev);
+    if (!dtab)
+        return BZ_ECUDA;
+    NoAllocTable &t = g_noalloc_host;
+    // window jobs first, most expensive tiles first (same order as binarize_batch)
+    int nw = 0, nq = 0;
+    for (int32_t i = 0; i < n; i++)
+        if (jobs[i].method != BZ_QUANTILE)
+            g_noalloc_order[nw++] = i;
+    std::sort(g_noalloc_order, g_noalloc_order + nw, [&](int a, int b) {
+        const int64_t ca = batch_tile_rows(jobs[a].H, jobs[a].h) + jobs[a].h;
+        const int64_t cb = batch_tile_rows(jobs[b].H, jobs[b].h) + jobs[b].h;
+        return ca != cb ? ca > cb : a < b;
+    });
+    int64_t tb = 0;
+    for (int a = 0; a < nw; a++) {
+        const bz_job &j = jobs[g_noalloc_order[a]];
+        WinJobDev &d = t.win[a];
+        d.g = Image{j.image, j.H, j.W, j.in_pitch};
+        d.win = make_window(j.h, j.w);
+        d.T = make_thresh(j.method == BZ_SAUVOLA ? 0 : 1, j.k, j.method == BZ_SAUVOLA ? j.R : 128.0);
+        d.out = j.out;
+        d.out_pitch = j.out_pitch;
+        d.tile_h = batch_tile_rows(j.H, j.h);
+        d.tiles_x = (j.W + kTileCols - 1) / kTileCols;
+        d.tile_begin = tb;
+        d.vec = ((uintptr_t)j.image % 8 == 0) && (j.in_pitch % 8 == 0);
+        d.wide = (int64_t)j.h * j.w > 66051;
+        tb += d.tiles_x * ((j.H + d.tile_h - 1) / d.tile_h);
+    }
+    t.hdr.win_tiles = tb;
+    for (int32_t i = 0; i < n; i++)
+        if (jobs[i].method == BZ_QUANTILE)
+            g_noalloc_order[nq++] = i;
+    std::sort(g_noalloc_order, g_noalloc_order + nq, [&](int a, int b) {
+        const int64_t ca = (int64_t)jobs[a].w * (quant_tile_rows(jobs[a].H, jobs[a].h) + jobs[a].h);
+        const int64_t cb = (int64_t)jobs[b].w * (quant_tile_rows(jobs[b].H, jobs[b].h) + jobs[b].h);
+        return ca != cb ? ca > cb : a < b;
+    });
+    tb = 0;
+    for (int a = 0; a < nq; a++) {
+        const bz_job &j = jobs[g_noalloc_order[a]];
+        QJobDev &d = t.q[a];
+        d.g = Image{j.image, j.H, j.W, j.in_pitch};
+        d.win = make_window(j.h, j.w);
+        d.q_num = j.q_num;
+        d.q_den = j.q_den;
+        d.offset = j.offset;
+        d.ct32 = (int64_t)j.h * j.w > 65535;
+        d.out = j.out;
+        d.out_pitch = j.out_pitch;
+        d.tile_h = quant_tile_rows(j.H, j.h);
+        d.tiles_x = (j.W + kQuantNT - 1) / kQuantNT;
+        d.tile_begin = tb;
+        tb += d.tiles_x * ((j.H + d.tile_h - 1) / d.tile_h);
+    }
+    t.hdr.q_tiles = tb;
+    t.hdr.n_win = nw;
+    t.hdr.n_q = nq;
+    // everything that must start at zero for this call: the two work-list
+    // cursors and the fallback counter (the array keeps the previous call's
+    // contents otherwise)
+    t.hdr.win_next = 0;
+    t.hdr.q_next = 0;
+    t.hdr.pad = 0;
+    t.fallbacks = 0;
+    // Only the used part of the list is copied.  The source is pageable host
+    // memory: the copy has consumed it when cudaMemcpyAsync returns, so the
+    // staging copy may be refilled by the next call.
+    const size_t used_win = offsetof(NoAllocTable, win) + sizeof(WinJobDev) * (size_t)nw;
+    if (cudaMemcpyAsync(dtab, &t, used_win, cudaMemcpyHostToDevice, (cudaStream_t)stream) !=
+        cudaSuccess)
+        return BZ_ECUDA;
+    if (nq > 0 && cudaMemcpyAsync(dtab->q, t.q, sizeof(QJobDev) * (size_t)nq,
+                                  cudaMemcpyHostToDevice, (cudaStream_t)stream) != cudaSuccess)
+        return BZ_ECUDA;
+    const cudaError_t e = mode == 0   ? noalloc_launch<MODE_FP64>(dtab, nsm, (cudaStream_t)stream)
+                          : mode == 1 ? noalloc_launch<MODE_FP32>(dtab, nsm, (cudaStream_t)stream)
+                                      : noalloc_launch<MODE_FP64_DIRECT>(dtab, nsm, (cudaStream_t)stream);
+    return e == cudaSuccess ? BZ_OK : BZ_ECUDA;
 }
