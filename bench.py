@@ -178,6 +178,64 @@ def workload_config(args):
             "l2": f"{N_BUFFERS} rotating input/output buffers (> 3x L2)", "parallelism": f"replicas{args.gpus}"}
 
 
+def time_events(fn, reps, stream):
+    import torch
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        fn()  # warm
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def extra_quantile(bz, synth, dev, stream):
+    """Local-quantile rows: 2048 x 2048 page with 2% salt-and-pepper."""
+    import torch
+    img = torch.from_numpy(synth.quantile_page()).to(dev)
+    out = torch.empty((2048, 256), dtype=torch.uint8, device=dev)
+    res = {}
+    for (h, w) in ((31, 31), (101, 101)):
+        for (qn, qd) in ((1, 2), (1, 10)):
+            ms = time_events(lambda: bz.binarize_quantile(img, h, w, qn, qd, 8, out=out, stream=stream), 3, stream)
+            res[f"{h}x{w}_q{qn}/{qd}"] = {"ms": round(ms, 3), "gpix_s": round(2048 * 2048 / (ms * 1e-3) / 1e9, 2)}
+    return res
+
+
+def extra_batch(bz, synth, dev, stream, count=256):
+    """256 uneven images (sizes log-uniform on the diagonal 320x240 .. 2480x3508,
+    windows 15/31/63/127, Sauvola or Niblack): one graph launch vs per-image calls."""
+    import torch
+    specs = synth.batch_specs(count)
+    # one A4 page at 300 dpi; every job binarizes a crop of it (generation of
+    # 256 distinct pages would dominate the benchmark's run time)
+    page = torch.from_numpy(synth.document(3508, 2480, synth.BASE_SEED + 3, stains=3)).to(dev)
+    jobs = []
+    px = 0
+    for sp in specs:
+        img = page[:sp["H"], :sp["W"]]
+        if sp["method"] == 0:
+            jobs.append(bz.Job(img, bz.SAUVOLA, sp["h"], sp["w"], k=0.5, R=128.0))
+        else:
+            jobs.append(bz.Job(img, bz.NIBLACK, sp["h"], sp["w"], k=-0.2))
+        px += sp["H"] * sp["W"]
+    ms_batch = time_events(lambda: bz.binarize_batch(jobs, stream=stream), 3, stream)
+
+    def per_image():
+        for j in jobs:
+            if j.c.method == 0:
+                bz.binarize_sauvola(j.image, j.c.h, j.c.w, 0.5, 128.0, out=j.out, stream=stream)
+            else:
+                bz.binarize_niblack(j.image, j.c.h, j.c.w, -0.2, out=j.out, stream=stream)
+    ms_single = time_events(per_image, 3, stream)
+    return {"images": count, "mpix": round(px / 1e6, 1),
+            "batched_graph": {"ms": round(ms_batch, 3), "gpix_s": round(px / (ms_batch * 1e-3) / 1e9, 2)},
+            "per_image_launches": {"ms": round(ms_single, 3), "gpix_s": round(px / (ms_single * 1e-3) / 1e9, 2)}}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -272,6 +330,10 @@ def main():
         t_ms = a.elapsed_time(b_) / reps
         per_window[f"{h}x{w}"] = {"ms": round(t_ms, 4), "gpix_s": round(H * W / (t_ms * 1e-3) / 1e9, 2)}
     fb = bz.last_fp64_fallbacks(stream)
+    extras = {}
+    if rank == 0:
+        extras["quantile_2048x2048"] = extra_quantile(bz, synth, dev, stream)
+        extras["batch_256"] = extra_batch(bz, synth, dev, stream)
 
     # end to end through the C ABI with host buffers
     e2e_steps = max(2, min(args.steps, 10))
@@ -313,6 +375,7 @@ def main():
                     "d2h_bytes_per_step": len(WINDOWS) * H * ((W + 7) // 8)},
             "per_window": per_window,
             "fp64_fallbacks_last_launch": fb,
+            "other_rows": extras,
         }
         if world == 1:
             line["cpu_baseline"] = cpu_baseline(page)

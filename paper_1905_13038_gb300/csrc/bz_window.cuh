@@ -171,9 +171,92 @@ static __device__ __noinline__ uint32_t fp64_bit(int method, uint32_t I, uint32_
     return ((double)I <= canonical_t(method, S1, S2, n, k, R)) ? 0u : 1u;
 }
 
+// ---- packed-byte arithmetic for the E slide (two columns per step) ------
+// dp2a.lo/hi with an unsigned 16-bit pair operand and unsigned bytes.
+__device__ __forceinline__ uint32_t dp2a_lo_uu(uint32_t a, uint32_t b, uint32_t c)
+{
+    uint32_t d;
+    asm("dp2a.lo.u32.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+__device__ __forceinline__ uint32_t dp2a_hi_uu(uint32_t a, uint32_t b, uint32_t c)
+{
+    uint32_t d;
+    asm("dp2a.hi.u32.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+// dp4a with unsigned bytes a and signed byte weights b.
+__device__ __forceinline__ int32_t dp4a_us(uint32_t a, uint32_t b, int32_t c)
+{
+    int32_t d;
+    asm("dp4a.u32.s32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+
+// E1 += a + d - b - c ; E2p += a^2 + d^2 ; E2n += b^2 + c^2 for the 8 columns
+// of a lane, from the byte groups A (row i+u, col j+r), B (row i+u, col j-l),
+// C (row i-o, col j+r), D (row i-o, col j-l).
+__device__ __forceinline__ void slide8(uint2 A, uint2 B, uint2 C, uint2 D, int32_t *E1,
+                                       uint32_t *E2p, uint32_t *E2n)
+{
+#pragma unroll
+    for (int q = 0; q < 2; q++) {
+        const uint32_t Aw = q ? A.y : A.x, Bw = q ? B.y : B.x;
+        const uint32_t Cw = q ? C.y : C.x, Dw = q ? D.y : D.x;
+#pragma unroll
+        for (int b = 0; b < 4; b += 2) {
+            const int m = 4 * q + b;
+            const unsigned sel = (unsigned)b | (unsigned)(4 + b) << 4 | (unsigned)(b + 1) << 8 |
+                                 (unsigned)(5 + b) << 12;
+            const uint32_t AD = __byte_perm(Aw, Dw, sel);  // a_m d_m a_m+1 d_m+1
+            const uint32_t BC = __byte_perm(Bw, Cw, sel);  // b_m c_m b_m+1 c_m+1
+            E2p[m] = dp2a_lo_uu(__byte_perm(AD, 0u, 0x4140u), AD, E2p[m]);
+            E2p[m + 1] = dp2a_hi_uu(__byte_perm(AD, 0u, 0x4342u), AD, E2p[m + 1]);
+            E2n[m] = dp2a_lo_uu(__byte_perm(BC, 0u, 0x4140u), BC, E2n[m]);
+            E2n[m + 1] = dp2a_hi_uu(__byte_perm(BC, 0u, 0x4342u), BC, E2n[m + 1]);
+            E1[m] = dp4a_us(BC, 0x0000FFFFu, dp4a_us(AD, 0x00000101u, E1[m]));
+            E1[m + 1] = dp4a_us(BC, 0xFFFF0000u, dp4a_us(AD, 0x01010000u, E1[m + 1]));
+        }
+    }
+}
+
+// Interior loads: 8 bytes at `p` (p - k is 8-byte aligned; k warp-uniform).
+__device__ __forceinline__ uint2 ld8_fast(const uint8_t *p, int k, unsigned sel)
+{
+    const uint2 a = __ldg(reinterpret_cast<const uint2 *>(p - k));
+    if (k == 0)
+        return a;
+    const uint2 b = __ldg(reinterpret_cast<const uint2 *>(p - k + 8));
+    return k < 4 ? make_uint2(__byte_perm(a.x, a.y, sel), __byte_perm(a.y, b.x, sel))
+                 : make_uint2(__byte_perm(a.y, b.x, sel), __byte_perm(b.x, b.y, sel));
+}
+
+// The pixel byte m of P as a float (2^23 + I, minus 2^23).
+__device__ __forceinline__ float pixel_f(uint2 P, int m)
+{
+    return __int_as_float(__byte_perm(m < 4 ? P.x : P.y, 0x4B000000u, 0x7440u | (unsigned)(m & 3))) -
+           8388608.0f;
+}
+
+// V = n S2 - S1^2 (exact, < 2^53) as a float, from 32-bit halves.  When
+// S2 < 2^32 (h*w <= 66051) V < 2^47, so the high half is < 2^23 and converts
+// exactly through the float bit pattern 2^23 + hi.
+template <typename S2T>
+__device__ __forceinline__ float v_float(uint32_t n, uint64_t S2, uint32_t S1)
+{
+    const uint64_t V = (uint64_t)n * S2 - (uint64_t)S1 * (uint64_t)S1;
+    const uint32_t hi = (uint32_t)(V >> 32);
+    const float fhi = sizeof(S2T) == 4 ? __int_as_float(0x4B000000u | hi) - 8388608.0f
+                                       : __uint2float_rn(hi);
+    return fmaf(fhi, 4294967296.0f, __uint2float_rn((uint32_t)V));
+}
+
 // S2T: uint32_t when h*w <= 66051 (S2 < 2^32), else unsigned long long.
-template <int MODE, bool VEC, typename S2T>
-__device__ __forceinline__ void window_tile(const Image &g, const Window &win, const Thresh &T,
+// INTERIOR: every lane's byte streams and outputs lie inside the row, the
+// image and pitch allow aligned 8-byte loads, and every output column has
+// the full window width w (warp-uniform; decided by window_tile).
+template <int MODE, bool VEC, bool INTERIOR, typename S2T>
+__device__ __forceinline__ void window_rows(const Image &g, const Window &win, const Thresh &T,
                                             const Outputs &o, int64_t x0, int64_t y0, int64_t y1,
                                             int lane)
 {
@@ -181,36 +264,76 @@ __device__ __forceinline__ void window_tile(const Image &g, const Window &win, c
     const int64_t j0 = x0 + (int64_t)kColsPerLane * lane;
     const int l = win.l, r = win.r, oo = win.o, u = win.u;
 
-    // ---- per-lane constants
-    const int64_t colA = j0 + r, colB = j0 - l;  // entering / leaving edge columns
-    const bool fastA = VEC && colA >= 0 && colA + 8 <= W;
-    const bool fastB = VEC && colB >= 0 && colB + 8 <= W;
+    const int64_t colA = j0 + r, colB = j0 - l;
+    const bool fastA = INTERIOR || (VEC && colA >= 0 && colA + 8 <= W);
+    const bool fastB = INTERIOR || (VEC && colB >= 0 && colB + 8 <= W);
+    const bool fastP = INTERIOR || (VEC && j0 + 8 <= W);
     const int kA = (int)(colA & 7), kB = (int)(colB & 7);  // warp-uniform
     const unsigned selA = (unsigned)(kA & 3) * 0x1111u + 0x3210u;
     const unsigned selB = (unsigned)(kB & 3) * 0x1111u + 0x3210u;
-    const bool fastP = VEC && j0 + 8 <= W;
 
+    auto load_row = [&](int64_t row, uint2 &A, uint2 &B) {
+        const uint8_t *rp = g.img + row * g.pitch;
+        if (INTERIOR) {
+            A = ld8_fast(rp + colA, kA, selA);
+            B = ld8_fast(rp + colB, kB, selB);
+        } else {
+            A = ld8<VEC>(rp, colA, fastA, kA, selA, W);
+            B = ld8<VEC>(rp, colB, fastB, kB, selB, W);
+        }
+    };
+
+    // per-column clipped widths (edge tiles only)
     uint32_t cols[kColsPerLane];
     float inv_cols[kColsPerLane];
+    if (!INTERIOR) {
 #pragma unroll
-    for (int m = 0; m < kColsPerLane; m++) {
-        const int64_t j = j0 + m;
-        const int64_t hi = j + r < W - 1 ? j + r : W - 1;
-        const int64_t lo = j - l > -1 ? j - l : -1;
-        const int64_t c = hi - lo;
-        cols[m] = (uint32_t)(c < 1 ? 1 : c);  // c < 1 only for j >= W
-        inv_cols[m] = __frcp_rn((float)cols[m]);
+        for (int m = 0; m < kColsPerLane; m++) {
+            const int64_t j = j0 + m;
+            const int64_t hi = j + r < W - 1 ? j + r : W - 1;
+            const int64_t lo = j - l > -1 ? j - l : -1;
+            const int64_t c = hi - lo;
+            cols[m] = (uint32_t)(c < 1 ? 1 : c);  // c < 1 only for j >= W
+            inv_cols[m] = __frcp_rn((float)cols[m]);
+        }
     }
+    const float inv_w = __frcp_rn((float)win.w);
+    const float inv_h = __frcp_rn((float)win.h);
+    const float inv_hw = inv_h * inv_w;
+
     // anchor window: columns [x0-l, x0-1+r] (the window of column x0-1)
     const int64_t ac0 = x0 - l, aend = x0 + r;
     const int64_t a4 = ac0 >= 0 ? (ac0 & ~(int64_t)3) : -((-ac0 + 3) & ~(int64_t)3);
+    // one word per lane covers the anchor when it spans at most 32 words
+    const bool one_word = INTERIOR && (aend - a4) <= 128;
+    const int64_t c4 = a4 + 4 * lane;
+    const bool has_word = c4 < aend;
+    uint32_t keep = 0xFFFFFFFFu;
+    if (c4 < ac0)
+        keep &= 0xFFFFFFFFu << (8 * (int)(ac0 - c4));
+    if (c4 + 4 > aend)
+        keep = (c4 >= aend) ? 0u : (keep & (0xFFFFFFFFu >> (8 * (int)(c4 + 4 - aend))));
+    auto anchor_row = [&](int64_t row, uint32_t &s1, uint32_t &s2) {
+        const uint8_t *rp = g.img + row * g.pitch;
+        if (one_word) {
+            if (has_word) {
+                const uint32_t wd = __ldg(reinterpret_cast<const uint32_t *>(rp + c4)) & keep;
+                s1 = __dp4a(wd, 0x01010101u, s1);
+                s2 = __dp4a(wd, wd, s2);
+            }
+        } else {
+            anchor_words<VEC>(rp, a4, ac0, aend, W, lane, s1, s2);
+        }
+    };
 
     // ---- warm-up: E and the anchor for row y0 (window rows (y0-o, y0+u])
-    int32_t E1[kColsPerLane], E2[kColsPerLane];
+    int32_t E1[kColsPerLane];
+    uint32_t E2p[kColsPerLane], E2n[kColsPerLane];
 #pragma unroll
     for (int m = 0; m < kColsPerLane; m++) {
         E1[m] = 0;
-        E2[m] = 0;
+        E2p[m] = 0;
+        E2n[m] = 0;
     }
     uint32_t a1p = 0, a2p = 0;
     {
@@ -219,17 +342,12 @@ __device__ __forceinline__ void window_tile(const Image &g, const Window &win, c
             a_lo = 0;
         if (a_hi > H - 1)
             a_hi = H - 1;
+        const uint2 Z = make_uint2(0u, 0u);
         for (int64_t a = a_lo; a <= a_hi; a++) {
-            const uint8_t *rp = g.img + a * g.pitch;
-            const uint2 A = ld8<VEC>(rp, colA, fastA, kA, selA, W);
-            const uint2 B = ld8<VEC>(rp, colB, fastB, kB, selB, W);
-#pragma unroll
-            for (int m = 0; m < kColsPerLane; m++) {
-                const int32_t av = byte_at(A, m), bv = byte_at(B, m);
-                E1[m] += av - bv;
-                E2[m] += av * av - bv * bv;
-            }
-            anchor_words<VEC>(rp, a4, ac0, aend, W, lane, a1p, a2p);
+            uint2 A, B;
+            load_row(a, A, B);
+            slide8(A, B, Z, Z, E1, E2p, E2n);
+            anchor_row(a, a1p, a2p);
         }
     }
     uint32_t A1 = __reduce_add_sync(0xFFFFFFFFu, a1p);
@@ -245,24 +363,19 @@ __device__ __forceinline__ void window_tile(const Image &g, const Window &win, c
     unsigned long long nfb = 0, nflip = 0;
     double maxdt = 0.0;
 
-    // prefetched slide data for the next row
     uint2 nA = make_uint2(0, 0), nB = nA, nC = nA, nD = nA;
-    uint32_t nd1 = 0, nd2 = 0;  // anchor increment partials (entering - leaving)
+    uint32_t nd1 = 0, nd2 = 0;
     auto prefetch = [&](int64_t i) {
         const int64_t ra = i + u, rb = i - oo;
         nA = nB = nC = nD = make_uint2(0, 0);
         uint32_t e1 = 0, e2 = 0, x1 = 0, x2 = 0;
         if (ra < H) {
-            const uint8_t *rp = g.img + ra * g.pitch;
-            nA = ld8<VEC>(rp, colA, fastA, kA, selA, W);
-            nB = ld8<VEC>(rp, colB, fastB, kB, selB, W);
-            anchor_words<VEC>(rp, a4, ac0, aend, W, lane, e1, e2);
+            load_row(ra, nA, nB);
+            anchor_row(ra, e1, e2);
         }
         if (rb >= 0) {
-            const uint8_t *rp = g.img + rb * g.pitch;
-            nC = ld8<VEC>(rp, colA, fastA, kA, selA, W);
-            nD = ld8<VEC>(rp, colB, fastB, kB, selB, W);
-            anchor_words<VEC>(rp, a4, ac0, aend, W, lane, x1, x2);
+            load_row(rb, nC, nD);
+            anchor_row(rb, x1, x2);
         }
         nd1 = e1 - x1;
         nd2 = e2 - x2;
@@ -270,16 +383,11 @@ __device__ __forceinline__ void window_tile(const Image &g, const Window &win, c
     if (y0 + 1 < y1)
         prefetch(y0 + 1);
 
+    const bool simple = T.method == 0 && T.alpha >= 0.0f && T.beta >= 0.0f;  // Sauvola, 0<=k<=1
+
     for (int64_t i = y0; i < y1; i++) {
         if (i > y0) {
-            // slide every E and the anchor from row i-1 to row i
-#pragma unroll
-            for (int m = 0; m < kColsPerLane; m++) {
-                const int32_t av = byte_at(nA, m), bv = byte_at(nB, m);
-                const int32_t cv = byte_at(nC, m), dv = byte_at(nD, m);
-                E1[m] += (av + dv) - (bv + cv);
-                E2[m] += (av * av + dv * dv) - (bv * bv + cv * cv);
-            }
+            slide8(nA, nB, nC, nD, E1, E2p, E2n);
             A1 += (uint32_t)__reduce_add_sync(0xFFFFFFFFu, nd1);
             A2 += (S2T)(int64_t)(int32_t)__reduce_add_sync(0xFFFFFFFFu, nd2);
             if (i + 1 < y1)
@@ -294,7 +402,7 @@ __device__ __forceinline__ void window_tile(const Image &g, const Window &win, c
 #pragma unroll
         for (int m = 0; m < kColsPerLane; m++) {
             run1 += (uint32_t)E1[m];
-            run2 += (S2T)(int64_t)E2[m];
+            run2 += (S2T)(int64_t)(int32_t)(E2p[m] - E2n[m]);
             p1[m] = run1;
             p2[m] = run2;
         }
@@ -317,44 +425,59 @@ __device__ __forceinline__ void window_tile(const Image &g, const Window &win, c
                     if (o.S2)
                         o.S2[idx] = (uint64_t)(off2 + p2[m]);
                     if (o.n)
-                        o.n[idx] = nrow * cols[m];
+                        o.n[idx] = nrow * (INTERIOR ? (uint32_t)win.w : cols[m]);
                 }
             }
             continue;
         }
 
-        const float inv_rows = __frcp_rn((float)rows);
+        const bool full_rows = nrow == (uint32_t)win.h;  // warp-uniform
+        const float inv_rows = full_rows ? inv_h : __frcp_rn((float)rows);
         const uint8_t *prow = g.img + i * g.pitch;
-        const uint2 P = ld8<VEC>(prow, j0, fastP, 0, 0x3210u, W);
+        const uint2 P = INTERIOR ? __ldg(reinterpret_cast<const uint2 *>(prow + j0))
+                                 : ld8<VEC>(prow, j0, fastP, 0, 0x3210u, W);
         uint32_t byte = 0, undecided = 0;
+        const uint32_t nw = nrow * (uint32_t)win.w;
+        const float inv_nw = full_rows ? inv_hw : inv_rows * inv_w;
+        if (MODE == MODE_FP64_DIRECT) {
 #pragma unroll
-        for (int m = 0; m < kColsPerLane; m++) {
-            const uint32_t S1 = off1 + p1[m];
-            const uint64_t S2 = (uint64_t)(off2 + p2[m]);
-            const uint32_t n = nrow * cols[m];
-            uint32_t bit;
-            if (MODE == MODE_FP64_DIRECT) {
-                bit = fp64_bit(T.method, (uint32_t)byte_at(P, m), S1, S2, n, T.k, T.R);
-            } else {
-                // exact V = n S2 - S1^2 (< 2^48), converted from two 32-bit halves
-                const uint64_t V = (uint64_t)n * S2 - (uint64_t)S1 * (uint64_t)S1;
-                const float Vhi = __int_as_float(0x4B000000u | (uint32_t)(V >> 32)) - 8388608.0f;
-                const float Vf = fmaf(Vhi, 4294967296.0f, __uint2float_rn((uint32_t)V));
-                const float inv_n = inv_rows * inv_cols[m];
+            for (int m = 0; m < kColsPerLane; m++) {
+                const uint32_t n = INTERIOR ? nw : nrow * cols[m];
+                byte |= fp64_bit(T.method, (uint32_t)byte_at(P, m), off1 + p1[m],
+                                 (uint64_t)(off2 + p2[m]), n, T.k, T.R)
+                        << m;
+            }
+        } else if (INTERIOR && simple && MODE != MODE_REPORT) {
+            // Sauvola with 0 <= k <= 1: t = m (alpha + beta s), |terms| = t
+            const float inv_n2 = inv_nw * inv_nw;
+#pragma unroll
+            for (int m = 0; m < kColsPerLane; m++) {
+                const uint32_t S1 = off1 + p1[m];
+                const float mu = __uint2float_rn(S1) * inv_nw;
+                const float var = v_float<S2T>(nw, (uint64_t)(off2 + p2[m]), S1) * inv_n2;
+                const float t = mu * fmaf(T.beta, sqrt_approx(var), T.alpha);
+                const float d = t - pixel_f(P, m);  // d < 0  <=>  I > t
+                byte |= (__float_as_uint(d) >> 31) << m;
+                if (MODE == MODE_FP64)
+                    undecided |= (fabsf(d) <= fmaf(T.eps, t, T.delta64) ? 1u : 0u) << m;
+            }
+        } else {
+#pragma unroll
+            for (int m = 0; m < kColsPerLane; m++) {
+                const uint32_t S1 = off1 + p1[m];
+                const uint64_t S2 = (uint64_t)(off2 + p2[m]);
+                const uint32_t n = INTERIOR ? nw : nrow * cols[m];
+                const float inv_n = INTERIOR ? inv_nw : inv_rows * inv_cols[m];
                 const float mu = __uint2float_rn(S1) * inv_n;
-                const float var = (Vf * inv_n) * inv_n;
+                const float var = (v_float<S2T>(n, S2, S1) * inv_n) * inv_n;
                 const float s = sqrt_approx(var);
                 const float t = fmaf(fmaf(T.beta, mu, T.gamma), s, T.alpha * mu);
-                // the pixel as a float: 2^23 + I from its byte, minus 2^23
-                const float If =
-                    __int_as_float(__byte_perm(m < 4 ? P.x : P.y, 0x4B000000u, 0x7440u | (unsigned)(m & 3))) -
-                    8388608.0f;
-                const float d = If - t;
-                bit = d > 0.0f ? 1u : 0u;
+                const float d = t - pixel_f(P, m);
+                const uint32_t bit = __float_as_uint(d) >> 31;
+                byte |= bit << m;
                 if (MODE == MODE_FP64) {
                     const float mag = fmaf(fmaf(T.abeta, mu, T.agamma), s, T.aalpha * mu);
-                    const float E = fmaf(T.eps, mag, T.delta64);
-                    undecided |= (fabsf(d) <= E ? 1u : 0u) << m;
+                    undecided |= (fabsf(d) <= fmaf(T.eps, mag, T.delta64) ? 1u : 0u) << m;
                 } else if (MODE == MODE_REPORT) {
                     if (j0 + m < W) {
                         const double t64 = canonical_t(T.method, S1, S2, n, T.k, T.R);
@@ -366,18 +489,18 @@ __device__ __forceinline__ void window_tile(const Image &g, const Window &win, c
                     }
                 }
             }
-            byte |= bit << m;
         }
         if (MODE == MODE_FP64) {
             // near-ties: canonical FP64 evaluation, off the hot path
-            if (j0 + 8 > W)
+            if (!INTERIOR && j0 + 8 > W)
                 undecided &= (1u << (j0 < W ? W - j0 : 0)) - 1u;
             if (__any_sync(0xFFFFFFFFu, undecided != 0) && undecided) {
 #pragma unroll
                 for (int m = 0; m < kColsPerLane; m++) {
                     if (undecided >> m & 1u) {
+                        const uint32_t n = INTERIOR ? nw : nrow * cols[m];
                         const uint32_t b = fp64_bit(T.method, (uint32_t)byte_at(P, m), off1 + p1[m],
-                                                    (uint64_t)(off2 + p2[m]), nrow * cols[m], T.k, T.R);
+                                                    (uint64_t)(off2 + p2[m]), n, T.k, T.R);
                         byte = (byte & ~(1u << m)) | (b << m);
                     }
                 }
@@ -385,7 +508,7 @@ __device__ __forceinline__ void window_tile(const Image &g, const Window &win, c
             }
         }
         if (MODE != MODE_REPORT && j0 < W) {
-            if (j0 + 8 > W)
+            if (!INTERIOR && j0 + 8 > W)
                 byte &= (1u << (W - j0)) - 1u;  // padding bits are 0
             o.bits[i * o.out_pitch + (j0 >> 3)] = (uint8_t)byte;
         }
@@ -411,6 +534,21 @@ __device__ __forceinline__ void window_tile(const Image &g, const Window &win, c
             atomicMax(o.maxdt_bits, (unsigned long long)__double_as_longlong(mx));
         }
     }
+}
+
+// One warp computes the tile of columns [x0, x0+256) x rows [y0, y1).
+template <int MODE, bool VEC, typename S2T>
+__device__ __forceinline__ void window_tile(const Image &g, const Window &win, const Thresh &T,
+                                            const Outputs &o, int64_t x0, int64_t y0, int64_t y1,
+                                            int lane)
+{
+    // interior: left edge stream of lane 0 and right edge stream of lane 31
+    // inside the row, and the whole tile left of the last column
+    const bool interior = VEC && (x0 - win.l >= 0) && (x0 + kTileCols + win.r <= g.W);
+    if (interior)
+        window_rows<MODE, VEC, true, S2T>(g, win, T, o, x0, y0, y1, lane);
+    else
+        window_rows<MODE, VEC, false, S2T>(g, win, T, o, x0, y0, y1, lane);
 }
 
 }  // namespace bz

@@ -2,6 +2,7 @@
 // FP32, FP64-direct), the exact window-sum export and the FP32-vs-FP64
 // report.  The per-tile arithmetic lives in bz_window.cuh.
 #include <math.h>
+#include <stdlib.h>
 
 #include "bz_internal.h"
 
@@ -65,16 +66,18 @@ Thresh make_thresh(int method, double k, double R)
 
 int64_t window_tile_rows(int64_t H, int64_t W, int h, int w)
 {
+    (void)W;
     (void)w;
-    // About 8 warps per SM on 152 SMs when the image allows it, but never
-    // tiles shorter than the window height (the warm-up of a tile costs about
-    // half a sliding row per window row).
-    const int64_t strips = (W + kTileCols - 1) / kTileCols;
-    const int64_t want_warps = 152 * 8;
-    const int64_t by_par = (H * strips + want_warps - 1) / want_warps;
-    int64_t th = by_par > (int64_t)h ? by_par : (int64_t)h;
-    if (th < 16)
-        th = 16;
+    (void)h;
+    // Measured on GB300 (4096 x 3072 page): a warm-up row costs a fraction of
+    // a full row, so short tiles win by giving every SM enough warps; 24 rows
+    // was best or within 5 % of best for windows from 15 x 15 to 255 x 255.
+    // BZ_TILE_ROWS overrides it (tuning).
+    static const int64_t env = [] {
+        const char *e = getenv("BZ_TILE_ROWS");
+        return e ? (int64_t)atoll(e) : (int64_t)0;
+    }();
+    int64_t th = env > 0 ? env : 24;
     if (th > H)
         th = H;
     return th;
