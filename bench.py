@@ -210,13 +210,15 @@ def extra_batch(bz, synth, dev, stream, count=256):
     windows 15/31/63/127, Sauvola or Niblack): one graph launch vs per-image calls."""
     import torch
     specs = synth.batch_specs(count)
-    # one A4 page at 300 dpi; every job binarizes a crop of it (generation of
-    # 256 distinct pages would dominate the benchmark's run time)
-    page = torch.from_numpy(synth.document(3508, 2480, synth.BASE_SEED + 3, stains=3)).to(dev)
+    # 16 distinct A4 pages at 300 dpi (139 MB, more than L2); job b binarizes
+    # a crop of page b % 16 (generating 256 full pages would dominate the
+    # benchmark's run time)
+    pages = [torch.from_numpy(synth.document(3508, 2480, synth.BASE_SEED + 3 + 1000 * p, stains=3)).to(dev)
+             for p in range(16)]
     jobs = []
     px = 0
-    for sp in specs:
-        img = page[:sp["H"], :sp["W"]]
+    for b, sp in enumerate(specs):
+        img = pages[b % 16][:sp["H"], :sp["W"]]
         if sp["method"] == 0:
             jobs.append(bz.Job(img, bz.SAUVOLA, sp["h"], sp["w"], k=0.5, R=128.0))
         else:

@@ -343,11 +343,28 @@ __device__ __forceinline__ void window_rows(const Image &g, const Window &win, c
         if (a_hi > H - 1)
             a_hi = H - 1;
         const uint2 Z = make_uint2(0u, 0u);
+        // one row of look-ahead: the loads of row a+1 are in flight while row
+        // a is accumulated
+        uint2 A = Z, B = Z;
+        uint32_t w1 = 0, w2 = 0;
+        if (a_lo <= a_hi) {
+            load_row(a_lo, A, B);
+            anchor_row(a_lo, w1, w2);
+        }
         for (int64_t a = a_lo; a <= a_hi; a++) {
-            uint2 A, B;
-            load_row(a, A, B);
+            uint2 An = Z, Bn = Z;
+            uint32_t v1 = 0, v2 = 0;
+            if (a < a_hi) {
+                load_row(a + 1, An, Bn);
+                anchor_row(a + 1, v1, v2);
+            }
             slide8(A, B, Z, Z, E1, E2p, E2n);
-            anchor_row(a, a1p, a2p);
+            a1p += w1;
+            a2p += w2;
+            A = An;
+            B = Bn;
+            w1 = v1;
+            w2 = v2;
         }
     }
     uint32_t A1 = __reduce_add_sync(0xFFFFFFFFu, a1p);
@@ -363,11 +380,18 @@ __device__ __forceinline__ void window_rows(const Image &g, const Window &win, c
     unsigned long long nfb = 0, nflip = 0;
     double maxdt = 0.0;
 
-    uint2 nA = make_uint2(0, 0), nB = nA, nC = nA, nD = nA;
+    uint2 nA = make_uint2(0, 0), nB = nA, nC = nA, nD = nA, nP = nA;
     uint32_t nd1 = 0, nd2 = 0;
+    auto load_centre = [&](int64_t i) {
+        const uint8_t *prow = g.img + i * g.pitch;
+        return INTERIOR ? __ldg(reinterpret_cast<const uint2 *>(prow + j0))
+                        : ld8<VEC>(prow, j0, fastP, 0, 0x3210u, W);
+    };
     auto prefetch = [&](int64_t i) {
         const int64_t ra = i + u, rb = i - oo;
         nA = nB = nC = nD = make_uint2(0, 0);
+        if (MODE != MODE_SUMS)
+            nP = load_centre(i);
         uint32_t e1 = 0, e2 = 0, x1 = 0, x2 = 0;
         if (ra < H) {
             load_row(ra, nA, nB);
@@ -380,6 +404,7 @@ __device__ __forceinline__ void window_rows(const Image &g, const Window &win, c
         nd1 = e1 - x1;
         nd2 = e2 - x2;
     };
+    uint2 P = MODE != MODE_SUMS ? load_centre(y0) : make_uint2(0u, 0u);
     if (y0 + 1 < y1)
         prefetch(y0 + 1);
 
@@ -387,6 +412,7 @@ __device__ __forceinline__ void window_rows(const Image &g, const Window &win, c
 
     for (int64_t i = y0; i < y1; i++) {
         if (i > y0) {
+            P = nP;
             slide8(nA, nB, nC, nD, E1, E2p, E2n);
             A1 += (uint32_t)__reduce_add_sync(0xFFFFFFFFu, nd1);
             A2 += (S2T)(int64_t)(int32_t)__reduce_add_sync(0xFFFFFFFFu, nd2);
@@ -433,9 +459,6 @@ __device__ __forceinline__ void window_rows(const Image &g, const Window &win, c
 
         const bool full_rows = nrow == (uint32_t)win.h;  // warp-uniform
         const float inv_rows = full_rows ? inv_h : __frcp_rn((float)rows);
-        const uint8_t *prow = g.img + i * g.pitch;
-        const uint2 P = INTERIOR ? __ldg(reinterpret_cast<const uint2 *>(prow + j0))
-                                 : ld8<VEC>(prow, j0, fastP, 0, 0x3210u, W);
         uint32_t byte = 0, undecided = 0;
         const uint32_t nw = nrow * (uint32_t)win.w;
         const float inv_nw = full_rows ? inv_hw : inv_rows * inv_w;
