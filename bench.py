@@ -178,6 +178,19 @@ def workload_config(args):
             "l2": f"{N_BUFFERS} rotating input/output buffers (> 3x L2)", "parallelism": f"replicas{args.gpus}"}
 
 
+def max_over_ranks(value: float, device) -> float:
+    """Maximum of a per-rank float over the process group (identity when not
+    distributed).  Replicas share nothing else: no collective touches the
+    data path."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def time_events(fn, reps, stream):
     import torch
     a = torch.cuda.Event(enable_timing=True)
@@ -302,12 +315,7 @@ def main():
             graph.replay()  # replays on the current stream: `stream`
             e1.record(stream)
         barrier()
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), dev)
     px_step = len(WINDOWS) * H * W
     value = world * px_step * args.steps / (ms * 1e-3) / 1e9
     launches = args.steps * len(WINDOWS)
@@ -353,12 +361,7 @@ def main():
                 host_out[wi].copy_(outs[wi], non_blocking=True)
         e2[1].record(stream)
     barrier()
-    e2e_ms = e2[0].elapsed_time(e2[1])
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_ms = float(tt.item())
+    e2e_ms = max_over_ranks(e2[0].elapsed_time(e2[1]), dev)
     e2e_value = world * px_step * e2e_steps / (e2e_ms * 1e-3) / 1e9
 
     if rank == 0:

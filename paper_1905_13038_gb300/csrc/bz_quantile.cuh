@@ -14,23 +14,6 @@
 
 namespace bz {
 
-// Adds `delta` (+1 or -1) to bin x of this thread's histogram with a
-// shared-memory reduction (no returned value, so consecutive updates do not
-// form a load-add-store dependency chain).  16-bit counters of threads tid
-// and tid^1 share a 32-bit word; a counter never drops below zero, so no
-// borrow crosses into the neighbour's half.
-template <typename CT, int NT>
-__device__ __forceinline__ void hist_add(CT *hist, int x, int tid, int delta)
-{
-    if (sizeof(CT) == 2) {
-        unsigned *w = reinterpret_cast<unsigned *>(hist) + ((x * NT + tid) >> 1);
-        const unsigned inc = 1u << (16 * (tid & 1));
-        atomicAdd(w, delta > 0 ? inc : (unsigned)(0u - inc));
-    } else {
-        atomicAdd(reinterpret_cast<unsigned *>(hist) + x * NT + tid, (unsigned)delta);
-    }
-}
-
 // One block (NT threads) computes output columns [x0, x0+NT) x rows [y0, y1).
 // smem: 256*NT counters of type CT followed by two staging rows.
 template <typename CT, int NT>
@@ -77,7 +60,7 @@ __device__ __forceinline__ void quantile_tile(const Image &g, const Window &win,
         stage(rin, a);
         __syncthreads();
         for (int c = c_lo; c <= c_hi; c++)
-            hist_add<CT, NT>(hist, (int)rin[tid + c], tid, 1);
+            hist[(int)rin[tid + c] * NT + tid] += 1;
     }
 
     const int64_t cols_hi = j + r < g.W - 1 ? j + r : g.W - 1;
@@ -98,14 +81,14 @@ __device__ __forceinline__ void quantile_tile(const Image &g, const Window &win,
             if (ra < g.H) {
                 for (int c = c_lo; c <= c_hi; c++) {
                     const int x = rin[tid + c];
-                    hist_add<CT, NT>(hist, x, tid, 1);
+                    hist[x * NT + tid] += 1;
                     below += (x < Q);
                 }
             }
             if (rb >= 0) {
                 for (int c = c_lo; c <= c_hi; c++) {
                     const int x = rout[tid + c];
-                    hist_add<CT, NT>(hist, x, tid, -1);
+                    hist[x * NT + tid] -= 1;
                     below -= (x < Q);
                 }
             }

@@ -193,11 +193,11 @@ __device__ __forceinline__ int32_t dp4a_us(uint32_t a, uint32_t b, int32_t c)
     return d;
 }
 
-// E1 += a + d - b - c ; E2p += a^2 + d^2 ; E2n += b^2 + c^2 for the 8 columns
+// E1 += a + d - b - c ; E2 += a^2 + d^2 - b^2 - c^2 for the 8 columns
 // of a lane, from the byte groups A (row i+u, col j+r), B (row i+u, col j-l),
 // C (row i-o, col j+r), D (row i-o, col j-l).
 __device__ __forceinline__ void slide8(uint2 A, uint2 B, uint2 C, uint2 D, int32_t *E1,
-                                       uint32_t *E2p, uint32_t *E2n)
+                                       uint32_t *E2)
 {
 #pragma unroll
     for (int q = 0; q < 2; q++) {
@@ -210,14 +210,43 @@ __device__ __forceinline__ void slide8(uint2 A, uint2 B, uint2 C, uint2 D, int32
                                  (unsigned)(5 + b) << 12;
             const uint32_t AD = __byte_perm(Aw, Dw, sel);  // a_m d_m a_m+1 d_m+1
             const uint32_t BC = __byte_perm(Bw, Cw, sel);  // b_m c_m b_m+1 c_m+1
-            E2p[m] = dp2a_lo_uu(__byte_perm(AD, 0u, 0x4140u), AD, E2p[m]);
-            E2p[m + 1] = dp2a_hi_uu(__byte_perm(AD, 0u, 0x4342u), AD, E2p[m + 1]);
-            E2n[m] = dp2a_lo_uu(__byte_perm(BC, 0u, 0x4140u), BC, E2n[m]);
-            E2n[m + 1] = dp2a_hi_uu(__byte_perm(BC, 0u, 0x4342u), BC, E2n[m + 1]);
+            E2[m] = dp2a_lo_uu(__byte_perm(AD, 0u, 0x4140u), AD, E2[m]) -
+                    dp2a_lo_uu(__byte_perm(BC, 0u, 0x4140u), BC, 0u);
+            E2[m + 1] = dp2a_hi_uu(__byte_perm(AD, 0u, 0x4342u), AD, E2[m + 1]) -
+                        dp2a_hi_uu(__byte_perm(BC, 0u, 0x4342u), BC, 0u);
             E1[m] = dp4a_us(BC, 0x0000FFFFu, dp4a_us(AD, 0x00000101u, E1[m]));
             E1[m + 1] = dp4a_us(BC, 0xFFFF0000u, dp4a_us(AD, 0x01010000u, E1[m + 1]));
         }
     }
+}
+
+// Warm-up step: E1 += a - b ; E2 += a^2 - b^2 (entering rows only).
+__device__ __forceinline__ void warm8(uint2 A, uint2 B, int32_t *E1, uint32_t *E2)
+{
+#pragma unroll
+    for (int q = 0; q < 2; q++) {
+        const uint32_t Aw = q ? A.y : A.x, Bw = q ? B.y : B.x;
+#pragma unroll
+        for (int b = 0; b < 4; b++) {
+            const int m = 4 * q + b;
+            const int32_t av = (int32_t)__byte_perm(Aw, 0u, 0x4440u | (unsigned)b);
+            const int32_t bv = (int32_t)__byte_perm(Bw, 0u, 0x4440u | (unsigned)b);
+            E1[m] += av - bv;
+            E2[m] += (uint32_t)((av - bv) * (av + bv));
+        }
+    }
+}
+
+// 8 bytes at p (p - k4 is 4-byte aligned, k4 = byte offset in 0..3, sel the
+// matching byte_perm selector), from three aligned 32-bit loads and no branch.
+// The third word is only needed when k4 > 0; when k4 == 0 the second word is
+// read again, so no byte past p + 8 is touched.  Requires image base and
+// pitch to be multiples of 4 and the 8 bytes to lie inside the row.
+__device__ __forceinline__ uint2 ld8_w3(const uint8_t *p, int k4, unsigned sel)
+{
+    const uint32_t *q = reinterpret_cast<const uint32_t *>(p - k4);
+    const uint32_t w0 = __ldg(q), w1 = __ldg(q + 1), w2 = __ldg(q + (k4 ? 2 : 1));
+    return make_uint2(__byte_perm(w0, w1, sel), __byte_perm(w1, w2, sel));
 }
 
 // Interior loads: 8 bytes at `p` (p - k is 8-byte aligned; k warp-uniform).
@@ -328,12 +357,11 @@ __device__ __forceinline__ void window_rows(const Image &g, const Window &win, c
 
     // ---- warm-up: E and the anchor for row y0 (window rows (y0-o, y0+u])
     int32_t E1[kColsPerLane];
-    uint32_t E2p[kColsPerLane], E2n[kColsPerLane];
+    uint32_t E2[kColsPerLane];
 #pragma unroll
     for (int m = 0; m < kColsPerLane; m++) {
         E1[m] = 0;
-        E2p[m] = 0;
-        E2n[m] = 0;
+        E2[m] = 0;
     }
     uint32_t a1p = 0, a2p = 0;
     {
@@ -358,7 +386,7 @@ __device__ __forceinline__ void window_rows(const Image &g, const Window &win, c
                 load_row(a + 1, An, Bn);
                 anchor_row(a + 1, v1, v2);
             }
-            slide8(A, B, Z, Z, E1, E2p, E2n);
+            warm8(A, B, E1, E2);
             a1p += w1;
             a2p += w2;
             A = An;
@@ -413,7 +441,7 @@ __device__ __forceinline__ void window_rows(const Image &g, const Window &win, c
     for (int64_t i = y0; i < y1; i++) {
         if (i > y0) {
             P = nP;
-            slide8(nA, nB, nC, nD, E1, E2p, E2n);
+            slide8(nA, nB, nC, nD, E1, E2);
             A1 += (uint32_t)__reduce_add_sync(0xFFFFFFFFu, nd1);
             A2 += (S2T)(int64_t)(int32_t)__reduce_add_sync(0xFFFFFFFFu, nd2);
             if (i + 1 < y1)
@@ -428,7 +456,7 @@ __device__ __forceinline__ void window_rows(const Image &g, const Window &win, c
 #pragma unroll
         for (int m = 0; m < kColsPerLane; m++) {
             run1 += (uint32_t)E1[m];
-            run2 += (S2T)(int64_t)(int32_t)(E2p[m] - E2n[m]);
+            run2 += (S2T)(int64_t)(int32_t)E2[m];
             p1[m] = run1;
             p2[m] = run2;
         }
@@ -559,19 +587,254 @@ __device__ __forceinline__ void window_rows(const Image &g, const Window &win, c
     }
 }
 
+// Interior tiles, binarize modes, 32-bit S2: a one-row software pipeline.
+// Iteration i computes the window sums of row i (slide, lane prefix, warp
+// scan) and stores them to a warp-private shared-memory slot, then evaluates
+// the threshold of row i-1 from the other slot.  The two halves are
+// independent, and the loop body has no data-dependent branch except the
+// rare FP64 near-tie path at its end, so the compiler can interleave the
+// scan's latency chain with the threshold arithmetic.  Rows outside the image
+// are handled without branches (safe row pointer + zero mask).
+// smem: 4096 bytes per warp.
+template <int MODE>
+__device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &win, const Thresh &T,
+                                                 const Outputs &o, int64_t x0, int64_t y0,
+                                                 int64_t y1, int lane, uint4 *slots)
+{
+    typedef uint32_t S2T;
+    const int64_t H = g.H;
+    const int64_t j0 = x0 + (int64_t)kColsPerLane * lane;
+    const int l = win.l, r = win.r, oo = win.o, u = win.u;
+    const int64_t colA = j0 + r, colB = j0 - l;
+    const int kA = (int)(colA & 3), kB = (int)(colB & 3);  // warp-uniform
+    const unsigned selA = (unsigned)kA * 0x1111u + 0x3210u;
+    const unsigned selB = (unsigned)kB * 0x1111u + 0x3210u;
+    const float inv_w = __frcp_rn((float)win.w);
+    const float inv_h = __frcp_rn((float)win.h);
+    const float inv_hw = inv_h * inv_w;
+
+    // anchor words: the caller guarantees (aend - a4) <= 128, one word per
+    // lane; lanes past the window read the first word and mask it to zero
+    const int64_t ac0 = x0 - l, aend = x0 + r;
+    const int64_t a4 = ac0 & ~(int64_t)3;  // ac0 >= 0 for interior tiles
+    const int64_t c4 = a4 + 4 * lane;
+    const bool has_word = c4 < aend;
+    uint32_t keep = 0xFFFFFFFFu;
+    if (c4 < ac0)
+        keep &= 0xFFFFFFFFu << (8 * (int)(ac0 - c4));
+    if (c4 + 4 > aend)
+        keep = (c4 >= aend) ? 0u : (keep & (0xFFFFFFFFu >> (8 * (int)(c4 + 4 - aend))));
+    const int64_t aoff = has_word ? c4 : a4;
+    auto anchor_row = [&](const uint8_t *rp, uint32_t &s1, uint32_t &s2) {
+        const uint32_t wd = __ldg(reinterpret_cast<const uint32_t *>(rp + aoff)) & keep;
+        s1 = __dp4a(wd, 0x01010101u, s1);
+        s2 = __dp4a(wd, wd, s2);
+    };
+
+    // ---- warm-up (row y0), one row of look-ahead
+    int32_t E1[kColsPerLane];
+    uint32_t E2[kColsPerLane];
+#pragma unroll
+    for (int m = 0; m < kColsPerLane; m++) {
+        E1[m] = 0;
+        E2[m] = 0;
+    }
+    uint32_t a1p = 0, a2p = 0;
+    {
+        int64_t a_lo = y0 - oo + 1, a_hi = y0 + u;
+        if (a_lo < 0)
+            a_lo = 0;
+        if (a_hi > H - 1)
+            a_hi = H - 1;
+        const uint2 Z = make_uint2(0u, 0u);
+        uint2 A = Z, B = Z;
+        uint32_t w1 = 0, w2 = 0;
+        if (a_lo <= a_hi) {
+            const uint8_t *rp = g.img + a_lo * g.pitch;
+            A = ld8_w3(rp + colA, kA, selA);
+            B = ld8_w3(rp + colB, kB, selB);
+            anchor_row(rp, w1, w2);
+        }
+        for (int64_t a = a_lo; a <= a_hi; a++) {
+            uint2 An = Z, Bn = Z;
+            uint32_t v1 = 0, v2 = 0;
+            if (a < a_hi) {
+                const uint8_t *rp = g.img + (a + 1) * g.pitch;
+                An = ld8_w3(rp + colA, kA, selA);
+                Bn = ld8_w3(rp + colB, kB, selB);
+                anchor_row(rp, v1, v2);
+            }
+            warm8(A, B, E1, E2);
+            a1p += w1;
+            a2p += w2;
+            A = An;
+            B = Bn;
+            w1 = v1;
+            w2 = v2;
+        }
+    }
+    uint32_t A1 = __reduce_add_sync(0xFFFFFFFFu, a1p);
+    S2T A2 = (S2T)__reduce_add_sync(0xFFFFFFFFu, a2p);  // < 2^32 when h*w <= 66051
+
+    // branch-free slide data for row i: rows outside the image read row 0
+    // and are masked to zero
+    uint2 nA, nB, nC, nD;
+    uint32_t nd1, nd2;
+    auto fetch = [&](int64_t i) {
+        const int64_t ra = i + u, rb = i - oo;
+        const bool va = ra < H, vb = rb >= 0;
+        const uint8_t *pa = g.img + (va ? ra : 0) * g.pitch;
+        const uint8_t *pb = g.img + (vb ? rb : 0) * g.pitch;
+        uint2 A = ld8_w3(pa + colA, kA, selA), B = ld8_w3(pa + colB, kB, selB);
+        uint2 C = ld8_w3(pb + colA, kA, selA), D = ld8_w3(pb + colB, kB, selB);
+        uint32_t e1 = 0, e2 = 0, x1 = 0, x2 = 0;
+        anchor_row(pa, e1, e2);
+        anchor_row(pb, x1, x2);
+        const uint32_t ma = va ? 0xFFFFFFFFu : 0u, mb = vb ? 0xFFFFFFFFu : 0u;
+        nA = make_uint2(A.x & ma, A.y & ma);
+        nB = make_uint2(B.x & ma, B.y & ma);
+        nC = make_uint2(C.x & mb, C.y & mb);
+        nD = make_uint2(D.x & mb, D.y & mb);
+        nd1 = (e1 & ma) - (x1 & mb);
+        nd2 = (e2 & ma) - (x2 & mb);
+    };
+
+    // window sums of the current row -> slot (i & 1)
+    auto sums_to_slot = [&](int64_t i) {
+        uint32_t p1[kColsPerLane], p2[kColsPerLane];
+        uint32_t run1 = 0, run2 = 0;
+#pragma unroll
+        for (int m = 0; m < kColsPerLane; m++) {
+            run1 += (uint32_t)E1[m];
+            run2 += E2[m];
+            p1[m] = run1;
+            p2[m] = run2;
+        }
+        const uint32_t inc1 = warp_incl_scan<uint32_t>(run1, lane);
+        const uint32_t inc2 = warp_incl_scan<uint32_t>(run2, lane);
+        const uint32_t off1 = A1 + (inc1 - run1);
+        const uint32_t off2 = A2 + (inc2 - run2);
+        uint4 *sl = slots + (int)(i & 1) * 128;
+        sl[0 * 32 + lane] = make_uint4(off1 + p1[0], off1 + p1[1], off1 + p1[2], off1 + p1[3]);
+        sl[1 * 32 + lane] = make_uint4(off1 + p1[4], off1 + p1[5], off1 + p1[6], off1 + p1[7]);
+        sl[2 * 32 + lane] = make_uint4(off2 + p2[0], off2 + p2[1], off2 + p2[2], off2 + p2[3]);
+        sl[3 * 32 + lane] = make_uint4(off2 + p2[4], off2 + p2[5], off2 + p2[6], off2 + p2[7]);
+    };
+
+    const bool simple = T.method == 0 && T.alpha >= 0.0f && T.beta >= 0.0f;
+    unsigned long long nfb = 0;
+
+    // threshold of row i from slot (i & 1) and its pixels P; stores the byte
+    auto threshold_row = [&](int64_t i, uint2 P) {
+        const uint4 *sl = slots + (int)(i & 1) * 128;
+        const uint4 s1a = sl[0 * 32 + lane], s1b = sl[1 * 32 + lane];
+        const uint4 s2a = sl[2 * 32 + lane], s2b = sl[3 * 32 + lane];
+        const uint32_t S1v[8] = {s1a.x, s1a.y, s1a.z, s1a.w, s1b.x, s1b.y, s1b.z, s1b.w};
+        const uint32_t S2v[8] = {s2a.x, s2a.y, s2a.z, s2a.w, s2b.x, s2b.y, s2b.z, s2b.w};
+        const int64_t rows = (i + u < H - 1 ? i + u : H - 1) - (i - oo > -1 ? i - oo : -1);
+        const uint32_t nrow = (uint32_t)rows;
+        const uint32_t nw = nrow * (uint32_t)win.w;
+        const float inv_nw = nrow == (uint32_t)win.h ? inv_hw : __frcp_rn((float)rows) * inv_w;
+        const float inv_n2 = inv_nw * inv_nw;
+        // slack[m] = |d| - E (certified when > 0); only the row minimum is
+        // kept on the hot path, the undecided set is rebuilt when it is <= 0
+        uint32_t byte = 0;
+        float minslack = 1.0f;
+        float slack[kColsPerLane];
+        if (simple) {
+#pragma unroll
+            for (int m = 0; m < kColsPerLane; m++) {
+                const float mu = __uint2float_rn(S1v[m]) * inv_nw;
+                const float var = v_float<S2T>(nw, (uint64_t)S2v[m], S1v[m]) * inv_n2;
+                const float t = mu * fmaf(T.beta, sqrt_approx(var), T.alpha);
+                const float d = t - pixel_f(P, m);
+                byte |= (__float_as_uint(d) >> 31) << m;
+                if (MODE == MODE_FP64) {
+                    slack[m] = fabsf(d) - fmaf(T.eps, t, T.delta64);
+                    minslack = fminf(minslack, slack[m]);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int m = 0; m < kColsPerLane; m++) {
+                const float mu = __uint2float_rn(S1v[m]) * inv_nw;
+                const float var = v_float<S2T>(nw, (uint64_t)S2v[m], S1v[m]) * inv_n2;
+                const float s = sqrt_approx(var);
+                const float t = fmaf(fmaf(T.beta, mu, T.gamma), s, T.alpha * mu);
+                const float d = t - pixel_f(P, m);
+                byte |= (__float_as_uint(d) >> 31) << m;
+                if (MODE == MODE_FP64) {
+                    const float mag = fmaf(fmaf(T.abeta, mu, T.agamma), s, T.aalpha * mu);
+                    slack[m] = fabsf(d) - fmaf(T.eps, mag, T.delta64);
+                    minslack = fminf(minslack, slack[m]);
+                }
+            }
+        }
+        if (MODE == MODE_FP64 && __any_sync(0xFFFFFFFFu, !(minslack > 0.0f)) && !(minslack > 0.0f)) {
+            uint32_t undecided = 0;
+#pragma unroll
+            for (int m = 0; m < kColsPerLane; m++)
+                undecided |= (!(slack[m] > 0.0f) ? 1u : 0u) << m;
+#pragma unroll
+            for (int m = 0; m < kColsPerLane; m++) {
+                if (undecided >> m & 1u) {
+                    const uint32_t b = fp64_bit(T.method, (uint32_t)byte_at(P, m), S1v[m],
+                                                (uint64_t)S2v[m], nw, T.k, T.R);
+                    byte = (byte & ~(1u << m)) | (b << m);
+                }
+            }
+            nfb += __popc(undecided);
+        }
+        o.bits[i * o.out_pitch + (j0 >> 3)] = (uint8_t)byte;
+    };
+
+    auto centre = [&](int64_t i) { return __ldg(reinterpret_cast<const uint2 *>(g.img + i * g.pitch + j0)); };
+
+    // prologue: row y0
+    sums_to_slot(y0);
+    uint2 Pprev = centre(y0);
+    if (y0 + 1 < y1)
+        fetch(y0 + 1);
+    for (int64_t i = y0 + 1; i < y1; i++) {
+        const uint2 Pcur = centre(i);
+        slide8(nA, nB, nC, nD, E1, E2);
+        A1 += (uint32_t)__reduce_add_sync(0xFFFFFFFFu, nd1);
+        A2 += (S2T)__reduce_add_sync(0xFFFFFFFFu, nd2);
+        fetch(i + 1 < y1 ? i + 1 : i);  // the last fetch is unused (no branch)
+        sums_to_slot(i);
+        threshold_row(i - 1, Pprev);
+        Pprev = Pcur;
+    }
+    threshold_row(y1 - 1, Pprev);
+
+    if (MODE == MODE_FP64 && o.fallbacks) {
+        const unsigned v = __reduce_add_sync(0xFFFFFFFFu, (unsigned)nfb);
+        if (lane == 0 && v)
+            atomicAdd(o.fallbacks, (unsigned long long)v);
+    }
+}
+
 // One warp computes the tile of columns [x0, x0+256) x rows [y0, y1).
-template <int MODE, bool VEC, typename S2T>
+// PIPE: the caller provides 4 KB of shared memory per warp (`slots`) for the
+// pipelined interior path.
+template <int MODE, bool VEC, typename S2T, bool PIPE>
 __device__ __forceinline__ void window_tile(const Image &g, const Window &win, const Thresh &T,
                                             const Outputs &o, int64_t x0, int64_t y0, int64_t y1,
-                                            int lane)
+                                            int lane, uint4 *slots)
 {
     // interior: left edge stream of lane 0 and right edge stream of lane 31
     // inside the row, and the whole tile left of the last column
     const bool interior = VEC && (x0 - win.l >= 0) && (x0 + kTileCols + win.r <= g.W);
-    if (interior)
-        window_rows<MODE, VEC, true, S2T>(g, win, T, o, x0, y0, y1, lane);
-    else
+    if (interior) {
+        // the pipelined path loads the anchor window as one word per lane
+        const bool one_word = win.w + ((4 - (win.l & 3)) & 3) <= 128;
+        if (PIPE && (MODE == MODE_FP64 || MODE == MODE_FP32) && sizeof(S2T) == 4 && one_word)
+            window_rows_pipe<MODE>(g, win, T, o, x0, y0, y1, lane, slots);
+        else
+            window_rows<MODE, VEC, true, S2T>(g, win, T, o, x0, y0, y1, lane);
+    } else {
         window_rows<MODE, VEC, false, S2T>(g, win, T, o, x0, y0, y1, lane);
+    }
 }
 
 }  // namespace bz

@@ -15,6 +15,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4)
     k_window(Image g, Window win, Thresh T, Outputs o, int64_t tiles_x, int64_t tiles_total,
              int64_t tile_h)
 {
+    __shared__ uint4 slots[kWarpsPerBlock][256];  // 4 KB per warp (pipelined path)
     const int lane = threadIdx.x & 31;
     const int64_t wid = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
     const int64_t stride = (int64_t)gridDim.x * kWarpsPerBlock;
@@ -22,7 +23,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4)
         const int64_t tx = t % tiles_x, ty = t / tiles_x;
         const int64_t x0 = tx * kTileCols, y0 = ty * tile_h;
         const int64_t y1 = y0 + tile_h < g.H ? y0 + tile_h : g.H;
-        window_tile<MODE, VEC, S2T>(g, win, T, o, x0, y0, y1, lane);
+        window_tile<MODE, VEC, S2T, true>(g, win, T, o, x0, y0, y1, lane, slots[threadIdx.x >> 5]);
     }
 }
 
