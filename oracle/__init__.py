@@ -28,6 +28,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
 SAUVOLA, NIBLACK = 0, 1
+WOLF, FENG, RAIS, NICK, PHANSALKAR = 3, 4, 5, 6, 7
 
 
 def build(force: bool = False) -> str:
@@ -68,6 +69,9 @@ def _load():
         "oracle_window_quantile_at": ([P, i64, i64, i64, i32, i32, i32, i32, P, P, i64, P], None),
         "oracle_binarize_quantile": ([P, i64, i64, i64, i32, i32, i32, i32, i32, P, P, i64, i32], ctypes.c_int),
         "oracle_window_params": ([i32, i32, P, P, P, P], None),
+        "oracle_global_stats": ([P, i64, i64, i64, P, P], ctypes.c_int),
+        "oracle_threshold_ext_array": ([i32, P, P, P, i64, P, P, P], None),
+        "oracle_binarize_ext": ([i32, P, i64, i64, i64, i32, i32, P, P, P, i64], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -251,4 +255,49 @@ def binarize_quantile(img: np.ndarray, h: int, w: int, q_num: int, q_den: int, o
     _check(_load().oracle_binarize_quantile(img.ctypes.data, H, W, pitch, h, w, q_num, q_den, offset,
                                             bits.ctypes.data, packed.ctypes.data, out_pitch, threads),
            "binarize_quantile")
+    return bits, packed
+
+
+# ---------------------------------------------------------------- Table 1 --
+def params(k: float = 0.5, R: float = 128.0, alpha1: float = 0.88, k1: float = 0.25,
+           k2: float = 0.04, gamma: float = 2.0, p: float = 2.0, q: float = 10.0 / 255.0) -> np.ndarray:
+    """The parameter vector of the Table 1 thresholds: {k, R, alpha1, k1, k2, gamma, p, q}."""
+    return np.array([k, R, alpha1, k1, k2, gamma, p, q], np.float64)
+
+
+def global_stats(img: np.ndarray, W: int | None = None):
+    """((L, M, S) as float64, (sum, sumsq, N) as ints): Table 1's global
+    minimum, mean and population standard deviation."""
+    img, H, W, pitch = _img(img, W)
+    st = np.empty(3, np.float64)
+    sums = np.empty(3, np.uint64)
+    _check(_load().oracle_global_stats(img.ctypes.data, H, W, pitch, st.ctypes.data, sums.ctypes.data),
+           "global_stats")
+    return st, tuple(int(v) for v in sums)
+
+
+def threshold_ext(method: int, S1, S2, n, prm, glob) -> np.ndarray:
+    """Canonical FP64 threshold of any Table 1 method, element-wise; glob = (L, M, S)."""
+    S1 = np.ascontiguousarray(S1, np.uint32)
+    S2 = np.ascontiguousarray(S2, np.uint64)
+    n = np.ascontiguousarray(n, np.uint32)
+    prm = np.ascontiguousarray(prm, np.float64)
+    glob = np.ascontiguousarray(glob, np.float64)
+    t = np.empty(S1.shape, np.float64)
+    _load().oracle_threshold_ext_array(method, S1.ctypes.data, S2.ctypes.data, n.ctypes.data, S1.size,
+                                       prm.ctypes.data, glob.ctypes.data, t.ctypes.data)
+    return t
+
+
+def binarize_ext(method: int, img: np.ndarray, h: int, w: int, prm, W: int | None = None,
+                 out_pitch: int | None = None):
+    """(bits, packed) of any Table 1 method (global statistics + Algorithm 1
+    sums + canonical FP64 threshold)."""
+    img, H, W, pitch = _img(img, W)
+    out_pitch = (W + 7) // 8 if out_pitch is None else out_pitch
+    prm = np.ascontiguousarray(prm, np.float64)
+    bits = np.empty((H, W), np.uint8)
+    packed = np.empty((H, out_pitch), np.uint8)
+    _check(_load().oracle_binarize_ext(method, img.ctypes.data, H, W, pitch, h, w, prm.ctypes.data,
+                                       bits.ctypes.data, packed.ctypes.data, out_pitch), "binarize_ext")
     return bits, packed

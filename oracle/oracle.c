@@ -751,3 +751,147 @@ void oracle_window_quantile_at(const uint8_t *img, int64_t H, int64_t W,
         Q[q] = hist_select(hist, quantile_rank(cnt, q_num, q_den));
     }
 }
+
+/* ------------------------------------------------------------------------ */
+/* (ix) The other Table 1 methods (Wolf, Feng, Rais, Khurshid's NICK,         */
+/*      Phansalkar): each keeps Algorithm 1's window statistics and changes   */
+/*      only the threshold (Sec. 3.4).  Three of them also use the global     */
+/*      minimum L, mean M and standard deviation S of the whole image         */
+/*      (Table 1 notations).                                                  */
+/* ------------------------------------------------------------------------ */
+
+/* Global statistics by plain loops: L = min I, M = sum/N and
+ * S = sqrt(Vg / (N*N)) with the exact numerator Vg = N*sumsq - sum^2
+ * (population standard deviation, as the local s).  Vg needs 128 bits; its
+ * conversion to double is the C conversion, round to nearest. */
+int oracle_global_stats(const uint8_t *img, int64_t H, int64_t W, int64_t pitch,
+                        double *stats, uint64_t *sums)
+{
+    if (H < 1 || W < 1 || pitch < W)
+        return 1;
+    uint32_t L = 255;
+    uint64_t sum = 0, sumsq = 0;
+    for (int64_t i = 0; i < H; i++)
+        for (int64_t j = 0; j < W; j++) {
+            uint32_t v = img[i * pitch + j];
+            L = v < L ? v : L;
+            sum += v;
+            sumsq += (uint64_t)v * v;
+        }
+    uint64_t N = (uint64_t)H * (uint64_t)W;
+    unsigned __int128 Vg = (unsigned __int128)N * sumsq - (unsigned __int128)sum * sum;
+    double Nd = (double)N;
+    stats[0] = (double)L;
+    stats[1] = (double)sum / Nd;
+    stats[2] = sqrt((double)Vg / (Nd * Nd));
+    if (sums) {
+        sums[0] = sum;
+        sums[1] = sumsq;
+        sums[2] = N;
+    }
+    return 0;
+}
+
+/* Canonical FP64 thresholds of Table 1, one operation at a time, in this
+ * order (m and s as in oracle_threshold; L, M, S from oracle_global_stats;
+ * prm = {k, R, alpha1, k1, k2, gamma, p, q}):
+ *   Wolf        t = m - (k*(m - L)) * (1 - s/R)
+ *   Feng        x = s/R;  t = (alpha1*m + (k1*pow(x, 1+gamma))*(m - L))
+ *                             + (k2*pow(x, gamma))*L
+ *   Rais        d = max(m*s, M*S);  f = d > 0 ? (m*s - M*S)/d : 0;
+ *               t = m + (k*f)*s
+ *   NICK        t = m + k*sqrt(V/(n*n) + (m*m)*((n - 1)/n))
+ *               (Table 1 writes hw; the clipped count n takes its place at
+ *               the border, as it does in m and s)
+ *   Phansalkar  t = m * ((1 + p*exp(-(q*m))) + k*(s/R - 1))
+ * Sauvola and Niblack are oracle_threshold. */
+double oracle_threshold_ext(int32_t method, uint32_t S1, uint64_t S2, uint32_t n,
+                            const double *prm, const double *glob)
+{
+    const double k = prm[0], R = prm[1];
+    if (method == ORACLE_SAUVOLA || method == ORACLE_NIBLACK)
+        return oracle_threshold(method, S1, S2, n, k, R);
+    int64_t V = variance_numerator(S1, S2, n);
+    double nd = (double)n;
+    double m = (double)S1 / nd;
+    double v = (double)V / (nd * nd);
+    double s = sqrt(v);
+    double L = glob[0], M = glob[1], S = glob[2];
+    switch (method) {
+    case ORACLE_WOLF:
+        return m - (k * (m - L)) * (1.0 - s / R);
+    case ORACLE_FENG: {
+        double alpha1 = prm[2], k1 = prm[3], k2 = prm[4], gamma = prm[5];
+        double x = s / R;
+        double a = alpha1 * m;
+        double b = (k1 * pow(x, 1.0 + gamma)) * (m - L);
+        double c = (k2 * pow(x, gamma)) * L;
+        return (a + b) + c;
+    }
+    case ORACLE_RAIS: {
+        double ms = m * s, MS = M * S;
+        double d = ms > MS ? ms : MS;
+        double f = d > 0.0 ? (ms - MS) / d : 0.0;
+        return m + (k * f) * s;
+    }
+    case ORACLE_NICK:
+        return m + k * sqrt(v + (m * m) * ((nd - 1.0) / nd));
+    case ORACLE_PHANSALKAR: {
+        double p = prm[6], q = prm[7];
+        return m * ((1.0 + p * exp(-(q * m))) + k * (s / R - 1.0));
+    }
+    default:
+        return NAN;
+    }
+}
+
+void oracle_threshold_ext_array(int32_t method, const uint32_t *S1, const uint64_t *S2,
+                                const uint32_t *n, int64_t count, const double *prm,
+                                const double *glob, double *t)
+{
+    for (int64_t x = 0; x < count; x++)
+        t[x] = oracle_threshold_ext(method, S1[x], S2[x], n[x], prm, glob);
+}
+
+/* Full binarization with any Table 1 method: global statistics, Algorithm 1
+ * window sums, canonical threshold, I <= t -> 0. */
+int oracle_binarize_ext(int32_t method, const uint8_t *img, int64_t H, int64_t W,
+                        int64_t pitch, int32_t h, int32_t w, const double *prm,
+                        uint8_t *bits, uint8_t *out, int64_t out_pitch)
+{
+    if (check_args(H, W, pitch, h, w) || method < 0 || method > ORACLE_PHANSALKAR ||
+        method == 2)
+        return 1;
+    if (out && out_pitch < (W + 7) / 8)
+        return 1;
+    double glob[3];
+    oracle_global_stats(img, H, W, pitch, glob, NULL);
+    size_t HW = (size_t)(H * W);
+    uint32_t *S1 = (uint32_t *)malloc(HW * sizeof(uint32_t));
+    uint64_t *S2 = (uint64_t *)malloc(HW * sizeof(uint64_t));
+    uint32_t *n = (uint32_t *)malloc(HW * sizeof(uint32_t));
+    uint8_t *b = bits ? bits : (uint8_t *)malloc(HW);
+    if (!S1 || !S2 || !n || !b) {
+        free(S1);
+        free(S2);
+        free(n);
+        if (!bits)
+            free(b);
+        return 2;
+    }
+    oracle_window_sums_recursive(img, H, W, pitch, h, w, S1, S2, n);
+    for (int64_t i = 0; i < H; i++)
+        for (int64_t j = 0; j < W; j++) {
+            int64_t x = i * W + j;
+            b[x] = decide(img[i * pitch + j],
+                          oracle_threshold_ext(method, S1[x], S2[x], n[x], prm, glob));
+        }
+    if (out)
+        oracle_pack_bits(b, H, W, out, out_pitch);
+    free(S1);
+    free(S2);
+    free(n);
+    if (!bits)
+        free(b);
+    return 0;
+}

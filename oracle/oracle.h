@@ -8,6 +8,12 @@
 
 #define ORACLE_SAUVOLA 0
 #define ORACLE_NIBLACK 1
+/* 2 is the quantile method */
+#define ORACLE_WOLF 3
+#define ORACLE_FENG 4
+#define ORACLE_RAIS 5
+#define ORACLE_NICK 6
+#define ORACLE_PHANSALKAR 7
 
 void oracle_window_params(int32_t h, int32_t w, int32_t *l, int32_t *r,
                           int32_t *o, int32_t *u);
@@ -75,4 +81,14 @@ void oracle_window_quantile_at(const uint8_t *img, int64_t H, int64_t W,
                                int64_t pitch, int32_t h, int32_t w, int32_t q_num,
                                int32_t q_den, const int64_t *ii, const int64_t *jj,
                                int64_t count, uint8_t *Q);
+int oracle_global_stats(const uint8_t *img, int64_t H, int64_t W, int64_t pitch,
+                        double *stats, uint64_t *sums);
+double oracle_threshold_ext(int32_t method, uint32_t S1, uint64_t S2, uint32_t n,
+                            const double *prm, const double *glob);
+void oracle_threshold_ext_array(int32_t method, const uint32_t *S1, const uint64_t *S2,
+                                const uint32_t *n, int64_t count, const double *prm,
+                                const double *glob, double *t);
+int oracle_binarize_ext(int32_t method, const uint8_t *img, int64_t H, int64_t W,
+                        int64_t pitch, int32_t h, int32_t w, const double *prm,
+                        uint8_t *bits, uint8_t *out, int64_t out_pitch);
 #endif
