@@ -238,6 +238,81 @@ def extra_quantile(bz, synth, dev, stream):
     return res
 
 
+def extra_serve(bz, synth, dev, pages, n_req=1500, seed=5):
+    """Served path: requests over pre-staged device images (crops of the batch
+    pages, area log-uniform 0.1-8.7 Mpix, aspect 1:sqrt(2) portrait or
+    landscape, method uniform over Sauvola/Niblack/median, odd window uniform
+    in [15, 255]) arriving as a Poisson process.  The saturation rate is
+    measured first (all requests submitted at once); then the rates 0.5x and
+    0.9x of it.  Latency = submit -> bz_server_wait returns."""
+    import concurrent.futures as cf
+    import numpy as np
+    import torch
+    rng = np.random.default_rng(seed)
+    PH, PW = pages[0].shape
+    jobs = []
+    px_total = 0
+    for q in range(n_req):
+        area = 0.1e6 * (8.7e6 / 0.1e6) ** rng.random()
+        if rng.random() < 0.5:
+            H = int(round((area * 2 ** 0.5) ** 0.5)); W = int(round(area / H))
+        else:
+            W = int(round((area * 2 ** 0.5) ** 0.5)); H = int(round(area / W))
+        H, W = max(1, min(H, PH)), max(1, min(W, PW))
+        win = int(rng.integers(7, 128)) * 2 + 1
+        img = pages[q % len(pages)][:H, :W]
+        m = int(rng.integers(0, 3))
+        if m == 0:
+            jobs.append(bz.Job(img, bz.SAUVOLA, win, win, k=0.5, R=128.0))
+        elif m == 1:
+            jobs.append(bz.Job(img, bz.NIBLACK, win, win, k=-0.2))
+        else:
+            jobs.append(bz.Job(img, bz.QUANTILE, win, win, q_num=1, q_den=2, offset=8))
+        px_total += H * W
+    budget = 8 << 30
+    pool = cf.ThreadPoolExecutor(max_workers=192)
+
+    def run(rate):
+        srv = bz.Server(hbm_budget_bytes=budget, max_slots=64)
+        t_sub = np.zeros(n_req)
+        t_done = np.zeros(n_req)
+        futs = []
+        gaps = rng.exponential(1.0 / rate, n_req) if rate else np.zeros(n_req)
+        t0 = time.perf_counter()
+        nxt = t0
+        for q, job in enumerate(jobs):
+            nxt += gaps[q]
+            while True:
+                now = time.perf_counter()
+                if now >= nxt:
+                    break
+                time.sleep(min(nxt - now, 0.0005))
+            t_sub[q] = time.perf_counter()
+            tk = srv.submit(job)
+
+            def wait(tk=tk, q=q):
+                st = srv.wait(tk, 120000)
+                t_done[q] = time.perf_counter()
+                return st
+            futs.append(pool.submit(wait))
+        sts = [f.result() for f in futs]
+        t1 = t_done.max()
+        srv.close()
+        lat = (t_done - t_sub) * 1e3
+        return {"rate_req_s": round(rate, 1) if rate else None, "p50_ms": round(float(np.percentile(lat, 50)), 3),
+                "p99_ms": round(float(np.percentile(lat, 99)), 3),
+                "gpix_s": round(px_total / (t1 - t0) / 1e9, 2), "ok": int(sum(1 for x in sts if x == 0))}
+
+    torch.cuda.synchronize()
+    sat = run(0)  # everything at once: saturation throughput
+    sat_rate = n_req / (px_total / (sat["gpix_s"] * 1e9))
+    res = {"requests": n_req, "mpix_total": round(px_total / 1e6, 1), "saturation": sat}
+    for f in (0.5, 0.9):
+        res[f"load_{f}"] = run(f * sat_rate)
+    pool.shutdown()
+    return res
+
+
 def extra_batch(bz, synth, dev, stream, count=256):
     """256 uneven images (sizes log-uniform on the diagonal 320x240 .. 2480x3508,
     windows 15/31/63/127, Sauvola or Niblack): one graph launch vs per-image calls."""
@@ -266,6 +341,7 @@ def extra_batch(bz, synth, dev, stream, count=256):
             else:
                 bz.binarize_niblack(j.image, j.c.h, j.c.w, -0.2, out=j.out, stream=stream)
     ms_single = time_events(per_image, 3, stream)
+    extra_batch.pages = pages
     return {"images": count, "mpix": round(px / 1e6, 1),
             "batched_graph": {"ms": round(ms_batch, 3), "gpix_s": round(px / (ms_batch * 1e-3) / 1e9, 2)},
             "per_image_launches": {"ms": round(ms_single, 3), "gpix_s": round(px / (ms_single * 1e-3) / 1e9, 2)}}
@@ -364,6 +440,7 @@ def main():
     if rank == 0:
         extras["quantile_2048x2048"] = extra_quantile(bz, synth, dev, stream)
         extras["batch_256"] = extra_batch(bz, synth, dev, stream)
+        extras["serve"] = extra_serve(bz, synth, dev, extra_batch.pages)
 
     # end to end through the C ABI with host buffers
     e2e_steps = max(2, min(args.steps, 10))
