@@ -238,6 +238,43 @@ def extra_quantile(bz, synth, dev, stream):
     return res
 
 
+def extra_table1(bz, imgs, outs, dev, stream, windows=((15, 15), (31, 31), (63, 63))):
+    """The other Table 1 methods on the 4096 x 3072 page (BZ_FP64, the same
+    rotating buffers): per launch the global-statistics pass plus the window
+    pass, 2.125 algorithmic bytes per pixel (the page is read twice)."""
+    import torch
+    methods = {
+        "wolf": lambda t, h, w, o: bz.binarize_wolf(t, h, w, 0.5, 128.0, out=o, stream=stream),
+        "feng": lambda t, h, w, o: bz.binarize_feng(t, h, w, out=o, stream=stream),
+        "rais": lambda t, h, w, o: bz.binarize_rais(t, h, w, 0.3, out=o, stream=stream),
+        "nick": lambda t, h, w, o: bz.binarize_nick(t, h, w, -0.1, out=o, stream=stream),
+        "phansalkar": lambda t, h, w, o: bz.binarize_phansalkar(t, h, w, out=o, stream=stream),
+    }
+    res = {}
+    reps = 8
+    for name, fn in methods.items():
+        row = {}
+        for (h, w) in windows:
+            with torch.cuda.stream(stream):
+                fn(imgs[0], h, w, outs[0])  # warm
+                a = torch.cuda.Event(enable_timing=True)
+                b_ = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                for r in range(reps):
+                    b = (r * 7 + 3) % N_BUFFERS
+                    fn(imgs[b], h, w, outs[b])
+                b_.record(stream)
+            torch.cuda.synchronize(dev)
+            ms = a.elapsed_time(b_) / reps
+            row[f"{h}x{w}"] = {"ms": round(ms, 4), "gpix_s": round(H * W / (ms * 1e-3) / 1e9, 2),
+                               "fp64_fallbacks": bz.last_fp64_fallbacks(stream)}
+        res[name] = row
+    stats = torch.empty(3, dtype=torch.float64, device=dev)
+    ms = time_events(lambda: bz.global_stats(imgs[1], stream=stream), 8, stream)
+    res["global_stats_pass"] = {"ms": round(ms, 4), "gb_s": round(H * W / (ms * 1e-3) / 1e9, 1)}
+    return res
+
+
 def extra_serve(bz, synth, dev, pages, n_req=1500, seed=5):
     """Served path: requests over pre-staged device images (crops of the batch
     pages, area log-uniform 0.1-8.7 Mpix, aspect 1:sqrt(2) portrait or
@@ -438,6 +475,7 @@ def main():
     fb = bz.last_fp64_fallbacks(stream)
     extras = {}
     if rank == 0:
+        extras["table1_4096x3072_fp64"] = extra_table1(bz, imgs, outs, dev, stream)
         extras["quantile_2048x2048"] = extra_quantile(bz, synth, dev, stream)
         extras["batch_256"] = extra_batch(bz, synth, dev, stream)
         extras["serve"] = extra_serve(bz, synth, dev, extra_batch.pages)

@@ -73,7 +73,16 @@ typedef enum {
     BZ_FP64_DIRECT = 2  /* canonical FP64 threshold evaluated for every pixel */
 } bz_precision;
 
-typedef enum { BZ_SAUVOLA = 0, BZ_NIBLACK = 1, BZ_QUANTILE = 2 } bz_method;
+typedef enum {
+    BZ_SAUVOLA = 0,
+    BZ_NIBLACK = 1,
+    BZ_QUANTILE = 2,
+    BZ_WOLF = 3,
+    BZ_FENG = 4,
+    BZ_RAIS = 5,
+    BZ_NICK = 6,
+    BZ_PHANSALKAR = 7
+} bz_method;
 
 /* Human-readable name of a status code (static string, never NULL). */
 const char *bz_status_string(bz_status s);
@@ -131,6 +140,84 @@ bz_status binarize_precision_report(int32_t method, const uint8_t *image,
  * decide in FP32 and evaluated in FP64, read back synchronously after the
  * stream finishes.  Diagnostic only; returns -1 when unknown. */
 int64_t bz_last_fp64_fallbacks(void *stream);
+
+/* ---------------------------------------------------------------------- */
+/* The other Table 1 methods (Sec. 3.4: one changed condition on the same */
+/* window statistics).  L, M and S are the global minimum, mean and        */
+/* population standard deviation of the image (Table 1 notations), found   */
+/* by one reduction pass on `stream` before the window pass.  The library  */
+/* takes 24 bytes of stream-ordered scratch (cudaMallocAsync) per call and */
+/* frees it on the stream: allocation failure -> BZ_ENOMEM.                */
+/*                                                                        */
+/* Canonical FP64 thresholds (every operation binary64 round-to-nearest,   */
+/* no contraction, in this order; m, s, V as above, nd = n):               */
+/*   Wolf        t = m - (k*(m - L)) * (1 - s/R)                           */
+/*   Feng        x = s/R;  t = (alpha1*m + (k1*pow(x, 1+gamma))*(m - L))   */
+/*                             + (k2*pow(x, gamma))*L                      */
+/*   Rais        d = max(m*s, M*S);  f = d > 0 ? (m*s - M*S)/d : 0;        */
+/*               t = m + (k*f)*s                                           */
+/*   NICK        t = m + k*sqrt(V/(nd*nd) + (m*m)*((nd - 1)/nd))           */
+/*               (Table 1's window area hw is the clipped count n)          */
+/*   Phansalkar  t = m * ((1 + p*exp(-(q*m))) + k*(s/R - 1))               */
+/* with L = min I, M = sum/N, S = sqrt(Vg/(N*N)), Vg = N*sumsq - sum^2     */
+/* exact (128-bit) and rounded once to double.  Feng and Phansalkar use    */
+/* the device pow/exp, which may differ from another libm by an ulp, so    */
+/* their decisions can differ from another implementation only where       */
+/* |I - t| is a few ulps of t.  The precision modes are those of Sauvola:  */
+/* BZ_FP64 (certified FP32 + FP64 near-ties), BZ_FP32, BZ_FP64_DIRECT.     */
+/*                                                                        */
+/* Parameters: finite, |x| <= 1e6; R in [1e-6, 1e9]; Feng gamma in [0, 16];*/
+/* Phansalkar q >= 0 (on gray levels 0..255: the published normalised     */
+/* setting p = 2, q = 10, k = 0.25, R = 0.5 is q = 10/255, R = 127.5 here).*/
+/* Image limit for these methods: H*W <= 2^44.                             */
+/* ---------------------------------------------------------------------- */
+bz_status binarize_wolf(const uint8_t *image, int64_t H, int64_t W,
+                        int64_t in_pitch, int32_t h, int32_t w, double k,
+                        double R, uint8_t *out, int64_t out_pitch,
+                        bz_precision precision, void *stream);
+
+/* Feng (Table 1 form): alpha1 multiplies m directly. */
+bz_status binarize_feng(const uint8_t *image, int64_t H, int64_t W,
+                        int64_t in_pitch, int32_t h, int32_t w, double alpha1,
+                        double k1, double k2, double gamma, double R,
+                        uint8_t *out, int64_t out_pitch,
+                        bz_precision precision, void *stream);
+
+/* Rais (Table 1 prints k = 0.3). */
+bz_status binarize_rais(const uint8_t *image, int64_t H, int64_t W,
+                        int64_t in_pitch, int32_t h, int32_t w, double k,
+                        uint8_t *out, int64_t out_pitch,
+                        bz_precision precision, void *stream);
+
+/* NICK (Khurshid et al.), k typically in [-0.2, -0.1]. */
+bz_status binarize_nick(const uint8_t *image, int64_t H, int64_t W,
+                        int64_t in_pitch, int32_t h, int32_t w, double k,
+                        uint8_t *out, int64_t out_pitch,
+                        bz_precision precision, void *stream);
+
+bz_status binarize_phansalkar(const uint8_t *image, int64_t H, int64_t W,
+                              int64_t in_pitch, int32_t h, int32_t w,
+                              double k, double R, double p, double q,
+                              uint8_t *out, int64_t out_pitch,
+                              bz_precision precision, void *stream);
+
+/* Parity export of the global statistics: stats_dev[0..2] = (L, M, S) as
+ * doubles, sums_dev[0..2] = (sum I, sum I^2, N) (sums_dev may be NULL);
+ * both caller-owned device arrays.  H*W <= 2^44. */
+bz_status global_stats(const uint8_t *image, int64_t H, int64_t W,
+                       int64_t in_pitch, double *stats_dev, uint64_t *sums_dev,
+                       void *stream);
+
+/* FP32-versus-FP64 report for any Table 1 method (bz_method other than
+ * BZ_QUANTILE).  params: HOST array of 8 doubles {k, R, alpha1, k1, k2,
+ * gamma, p, q} (unused entries ignored).  Semantics as
+ * binarize_precision_report. */
+bz_status binarize_precision_report_ext(int32_t method, const uint8_t *image,
+                                        int64_t H, int64_t W, int64_t in_pitch,
+                                        int32_t h, int32_t w,
+                                        const double *params,
+                                        uint64_t *flips_dev,
+                                        double *max_abs_dt_dev, void *stream);
 
 /* ---------------------------------------------------------------------- */
 /* Batched execution: many images of uneven sizes in one launch.          */

@@ -1,4 +1,4 @@
-"""GB300 local adaptive binarization (Sauvola, Niblack, local quantile).
+"""GB300 local adaptive binarization (the Table 1 methods and the local quantile).
 
 Thin ctypes binding over the C ABI declared in ``include/binarize.h``: every
 function here only marshals torch tensors (device memory) and the current CUDA
@@ -23,10 +23,13 @@ __all__ = [
     "window_quantile", "binarize_precision_report", "last_fp64_fallbacks", "Job", "binarize_batch",
     "binarize_batch_noalloc",
     "Server", "status_string",
+    "WOLF", "FENG", "RAIS", "NICK", "PHANSALKAR", "binarize_wolf", "binarize_feng", "binarize_rais",
+    "binarize_nick", "binarize_phansalkar", "global_stats", "binarize_precision_report_ext",
 ]
 
 FP64, FP32, FP64_DIRECT = 0, 1, 2
 SAUVOLA, NIBLACK, QUANTILE = 0, 1, 2
+WOLF, FENG, RAIS, NICK, PHANSALKAR = 3, 4, 5, 6, 7
 _PREC = {"fp64": FP64, "fp32": FP32, "fp64_direct": FP64_DIRECT, FP64: FP64, FP32: FP32,
          FP64_DIRECT: FP64_DIRECT}
 
@@ -78,6 +81,13 @@ def _load():
         "window_quantile": ([P, i64, i64, i64, i32, i32, i32, i32, P, P], st),
         "binarize_precision_report": ([i32, P, i64, i64, i64, i32, i32, f64, f64, P, P, P], st),
         "bz_last_fp64_fallbacks": ([P], i64),
+        "binarize_wolf": ([P, i64, i64, i64, i32, i32, f64, f64, P, i64, st, P], st),
+        "binarize_feng": ([P, i64, i64, i64, i32, i32, f64, f64, f64, f64, f64, P, i64, st, P], st),
+        "binarize_rais": ([P, i64, i64, i64, i32, i32, f64, P, i64, st, P], st),
+        "binarize_nick": ([P, i64, i64, i64, i32, i32, f64, P, i64, st, P], st),
+        "binarize_phansalkar": ([P, i64, i64, i64, i32, i32, f64, f64, f64, f64, P, i64, st, P], st),
+        "global_stats": ([P, i64, i64, i64, P, P, P], st),
+        "binarize_precision_report_ext": ([i32, P, i64, i64, i64, i32, i32, P, P, P, P], st),
         "binarize_batch": ([ctypes.POINTER(_JobC), i32, st, P], st),
         "binarize_batch_noalloc": ([ctypes.POINTER(_JobC), i32, st, P], st),
         "bz_server_create": ([i64, i32, ctypes.POINTER(P)], st),
@@ -190,6 +200,87 @@ def binarize_precision_report(method: int, image, h: int, w: int, k: float, R: f
     _check("binarize_precision_report",
            _load().binarize_precision_report(method, ptr, H, W, pitch, h, w, k, R, flips.data_ptr(),
                                              maxdt.data_ptr(), _stream(stream)))
+    return int(flips.item()), float(maxdt.item())
+
+
+def binarize_wolf(image, h: int, w: int, k: float = 0.5, R: float = 128.0, out=None,
+                  precision="fp64", W: int | None = None, stream=None):
+    """Wolf et al. (Table 1): t = m - k (m - L)(1 - s/R), L the global minimum."""
+    ptr, H, W, pitch = _image(image, W)
+    out, op = _out(out, H, W, image.device)
+    _check("binarize_wolf", _load().binarize_wolf(ptr, H, W, pitch, h, w, k, R, out.data_ptr(), op,
+                                                  _PREC[precision], _stream(stream)))
+    return out
+
+
+def binarize_feng(image, h: int, w: int, alpha1: float = 0.88, k1: float = 0.25, k2: float = 0.04,
+                  gamma: float = 2.0, R: float = 128.0, out=None, precision="fp64",
+                  W: int | None = None, stream=None):
+    """Feng et al. in the Table 1 form
+    t = alpha1 m + k1 (s/R)^(1+gamma) (m - L) + k2 (s/R)^gamma L."""
+    ptr, H, W, pitch = _image(image, W)
+    out, op = _out(out, H, W, image.device)
+    _check("binarize_feng", _load().binarize_feng(ptr, H, W, pitch, h, w, alpha1, k1, k2, gamma, R,
+                                                  out.data_ptr(), op, _PREC[precision], _stream(stream)))
+    return out
+
+
+def binarize_rais(image, h: int, w: int, k: float = 0.3, out=None, precision="fp64",
+                  W: int | None = None, stream=None):
+    """Rais et al. (Table 1): t = m + k (m s - M S) / max(m s, M S) s."""
+    ptr, H, W, pitch = _image(image, W)
+    out, op = _out(out, H, W, image.device)
+    _check("binarize_rais", _load().binarize_rais(ptr, H, W, pitch, h, w, k, out.data_ptr(), op,
+                                                  _PREC[precision], _stream(stream)))
+    return out
+
+
+def binarize_nick(image, h: int, w: int, k: float = -0.1, out=None, precision="fp64",
+                  W: int | None = None, stream=None):
+    """Khurshid et al. (NICK, Table 1): t = m + k sqrt(s^2 + m^2 (n - 1)/n)."""
+    ptr, H, W, pitch = _image(image, W)
+    out, op = _out(out, H, W, image.device)
+    _check("binarize_nick", _load().binarize_nick(ptr, H, W, pitch, h, w, k, out.data_ptr(), op,
+                                                  _PREC[precision], _stream(stream)))
+    return out
+
+
+def binarize_phansalkar(image, h: int, w: int, k: float = 0.25, R: float = 127.5, p: float = 2.0,
+                        q: float = 10.0 / 255.0, out=None, precision="fp64", W: int | None = None,
+                        stream=None):
+    """Phansalkar et al. (Table 1): t = m (1 + p exp(-q m) + k (s/R - 1)) on gray
+    levels 0..255 (the published normalised p = 2, q = 10, R = 0.5 are the defaults)."""
+    ptr, H, W, pitch = _image(image, W)
+    out, op = _out(out, H, W, image.device)
+    _check("binarize_phansalkar", _load().binarize_phansalkar(ptr, H, W, pitch, h, w, k, R, p, q,
+                                                              out.data_ptr(), op, _PREC[precision],
+                                                              _stream(stream)))
+    return out
+
+
+def global_stats(image, W: int | None = None, stream=None):
+    """((L, M, S) float64 CUDA tensor, (sum, sumsq, N) int64 CUDA tensor)."""
+    import torch
+    ptr, H, W, pitch = _image(image, W)
+    stats = torch.empty(3, dtype=torch.float64, device=image.device)
+    sums = torch.empty(3, dtype=torch.int64, device=image.device)
+    _check("global_stats", _load().global_stats(ptr, H, W, pitch, stats.data_ptr(), sums.data_ptr(),
+                                                _stream(stream)))
+    return stats, sums
+
+
+def binarize_precision_report_ext(method: int, image, h: int, w: int, params, W: int | None = None,
+                                  stream=None):
+    """(flips, max |t32 - t64|) for any Table 1 method; params = {k, R, alpha1,
+    k1, k2, gamma, p, q} (8 floats)."""
+    import torch
+    ptr, H, W, pitch = _image(image, W)
+    prm = (ctypes.c_double * 8)(*[float(x) for x in params])
+    flips = torch.zeros(1, dtype=torch.int64, device=image.device)
+    maxdt = torch.zeros(1, dtype=torch.float64, device=image.device)
+    _check("binarize_precision_report_ext",
+           _load().binarize_precision_report_ext(method, ptr, H, W, pitch, h, w, prm, flips.data_ptr(),
+                                                 maxdt.data_ptr(), _stream(stream)))
     return int(flips.item()), float(maxdt.item())
 
 

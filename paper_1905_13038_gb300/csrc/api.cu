@@ -111,6 +111,90 @@ static bz_status run_threshold(int method, const uint8_t *image, int64_t H, int6
                                                                                   : BZ_ECUDA;
 }
 
+// Parameter ranges of the other Table 1 methods; prm = {k, R, alpha1, k1,
+// k2, gamma, p, q}.  Every parameter is finite with |x| <= 1e6; R (where
+// used) in [1e-6, 1e9]; Feng's gamma in [0, 16]; Phansalkar's q >= 0.
+static bool ext_params_ok(int method, const double *prm)
+{
+    for (int i = 0; i < 8; i++)
+        if (!isfinite(prm[i]) || fabs(prm[i]) > 1e6)
+            return false;
+    const bool usesR = method == METHOD_WOLF || method == METHOD_FENG || method == METHOD_PHANSALKAR;
+    if (usesR && (prm[1] < 1e-6 || prm[1] > 1e9))
+        return false;
+    if (method == METHOD_FENG && (prm[5] < 0.0 || prm[5] > 16.0))
+        return false;
+    if (method == METHOD_PHANSALKAR && prm[7] < 0.0)
+        return false;
+    return method >= METHOD_WOLF && method <= METHOD_PHANSALKAR;
+}
+
+// The global sums need sum < 2^53 and N*sumsq < 2^128: H*W <= 2^44.
+static bool global_size_ok(int64_t H, int64_t W)
+{
+    return (double)H * (double)W <= 17592186044416.0;
+}
+
+// Global statistics, then the window kernel reading them, on `stream`.
+// The 24-byte GStats scratch is a stream-ordered allocation, freed on the
+// stream after the kernel, so concurrent calls on different streams do not
+// share it.
+static bz_status run_ext(int method, const uint8_t *image, int64_t H, int64_t W, int64_t in_pitch,
+                         int32_t h, int32_t w, const double *prm, int mode, Outputs o,
+                         void *stream)
+{
+    if (!ext_params_ok(method, prm) || !global_size_ok(H, W))
+        return BZ_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    Image g{image, H, W, in_pitch};
+    GStats *gs = nullptr;
+    if (cudaMallocAsync((void **)&gs, sizeof(GStats), s) != cudaSuccess)
+        return BZ_ENOMEM;
+    bz_status st = BZ_OK;
+    const unsigned long long N = (unsigned long long)H * (unsigned long long)W;
+    ThreshExt T = make_thresh_ext(method, prm, gs, N);
+    if (launch_global_stats(g, gs, s) != cudaSuccess ||
+        launch_window_ext(mode, g, make_window(h, w), T, o, s) != cudaSuccess)
+        st = BZ_ECUDA;
+    if (cudaFreeAsync(gs, s) != cudaSuccess)
+        st = BZ_ECUDA;
+    return st;
+}
+
+static bz_status run_ext_binarize(int method, const uint8_t *image, int64_t H, int64_t W,
+                                  int64_t in_pitch, int32_t h, int32_t w, const double *prm,
+                                  uint8_t *out, int64_t out_pitch, bz_precision precision,
+                                  void *stream)
+{
+    bz_status st = check_image(image, H, W, in_pitch, h, w);
+    if (st != BZ_OK)
+        return st;
+    st = check_out(image, H, W, in_pitch, out, out_pitch);
+    if (st != BZ_OK)
+        return st;
+    int mode;
+    switch (precision) {
+    case BZ_FP64: mode = MODE_FP64; break;
+    case BZ_FP32: mode = MODE_FP32; break;
+    case BZ_FP64_DIRECT: mode = MODE_FP64_DIRECT; break;
+    default: return BZ_EINVAL;
+    }
+    Outputs o{};
+    o.bits = out;
+    o.out_pitch = out_pitch;
+    if (mode == MODE_FP64) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess)
+            return BZ_ECUDA;
+        o.fallbacks = fallback_counter(dev);
+        if (o.fallbacks &&
+            cudaMemsetAsync(o.fallbacks, 0, sizeof(unsigned long long), (cudaStream_t)stream) !=
+                cudaSuccess)
+            return BZ_ECUDA;
+    }
+    return run_ext(method, image, H, W, in_pitch, h, w, prm, mode, o, stream);
+}
+
 }  // namespace bz
 
 using namespace bz;
@@ -228,6 +312,96 @@ bz_status binarize_precision_report(int32_t method, const uint8_t *image, int64_
                    cudaSuccess
                ? BZ_OK
                : BZ_ECUDA;
+}
+
+bz_status binarize_wolf(const uint8_t *image, int64_t H, int64_t W, int64_t in_pitch, int32_t h,
+                        int32_t w, double k, double R, uint8_t *out, int64_t out_pitch,
+                        bz_precision precision, void *stream)
+{
+    const double prm[8] = {k, R, 0, 0, 0, 0, 0, 0};
+    return run_ext_binarize(METHOD_WOLF, image, H, W, in_pitch, h, w, prm, out, out_pitch,
+                            precision, stream);
+}
+
+bz_status binarize_feng(const uint8_t *image, int64_t H, int64_t W, int64_t in_pitch, int32_t h,
+                        int32_t w, double alpha1, double k1, double k2, double gamma, double R,
+                        uint8_t *out, int64_t out_pitch, bz_precision precision, void *stream)
+{
+    const double prm[8] = {0, R, alpha1, k1, k2, gamma, 0, 0};
+    return run_ext_binarize(METHOD_FENG, image, H, W, in_pitch, h, w, prm, out, out_pitch,
+                            precision, stream);
+}
+
+bz_status binarize_rais(const uint8_t *image, int64_t H, int64_t W, int64_t in_pitch, int32_t h,
+                        int32_t w, double k, uint8_t *out, int64_t out_pitch,
+                        bz_precision precision, void *stream)
+{
+    const double prm[8] = {k, 128.0, 0, 0, 0, 0, 0, 0};
+    return run_ext_binarize(METHOD_RAIS, image, H, W, in_pitch, h, w, prm, out, out_pitch,
+                            precision, stream);
+}
+
+bz_status binarize_nick(const uint8_t *image, int64_t H, int64_t W, int64_t in_pitch, int32_t h,
+                        int32_t w, double k, uint8_t *out, int64_t out_pitch,
+                        bz_precision precision, void *stream)
+{
+    const double prm[8] = {k, 128.0, 0, 0, 0, 0, 0, 0};
+    return run_ext_binarize(METHOD_NICK, image, H, W, in_pitch, h, w, prm, out, out_pitch,
+                            precision, stream);
+}
+
+bz_status binarize_phansalkar(const uint8_t *image, int64_t H, int64_t W, int64_t in_pitch,
+                              int32_t h, int32_t w, double k, double R, double p, double q,
+                              uint8_t *out, int64_t out_pitch, bz_precision precision,
+                              void *stream)
+{
+    const double prm[8] = {k, R, 0, 0, 0, 0, p, q};
+    return run_ext_binarize(METHOD_PHANSALKAR, image, H, W, in_pitch, h, w, prm, out, out_pitch,
+                            precision, stream);
+}
+
+bz_status global_stats(const uint8_t *image, int64_t H, int64_t W, int64_t in_pitch,
+                       double *stats_dev, uint64_t *sums_dev, void *stream)
+{
+    if (!image || !stats_dev || H < 1 || W < 1 || H > 2147483647LL || W > 2147483647LL ||
+        in_pitch < W || in_pitch > (INT64_MAX / H) || !global_size_ok(H, W))
+        return BZ_EINVAL;
+    const size_t img_bytes = (size_t)((H - 1) * in_pitch + W);
+    if (ranges_overlap(image, img_bytes, stats_dev, 3 * sizeof(double)) ||
+        (sums_dev && ranges_overlap(image, img_bytes, sums_dev, 3 * sizeof(uint64_t))))
+        return BZ_EOVERLAP;
+    cudaStream_t s = (cudaStream_t)stream;
+    GStats *gs = nullptr;
+    if (cudaMallocAsync((void **)&gs, sizeof(GStats), s) != cudaSuccess)
+        return BZ_ENOMEM;
+    Image g{image, H, W, in_pitch};
+    bz_status st = BZ_OK;
+    if (launch_global_stats(g, gs, s) != cudaSuccess ||
+        launch_global_finalize(gs, (unsigned long long)H * (unsigned long long)W, stats_dev,
+                               sums_dev, s) != cudaSuccess)
+        st = BZ_ECUDA;
+    if (cudaFreeAsync(gs, s) != cudaSuccess)
+        st = BZ_ECUDA;
+    return st;
+}
+
+bz_status binarize_precision_report_ext(int32_t method, const uint8_t *image, int64_t H,
+                                        int64_t W, int64_t in_pitch, int32_t h, int32_t w,
+                                        const double *params, uint64_t *flips_dev,
+                                        double *max_abs_dt_dev, void *stream)
+{
+    bz_status st = check_image(image, H, W, in_pitch, h, w);
+    if (st != BZ_OK)
+        return st;
+    if (!params || !flips_dev || !max_abs_dt_dev)
+        return BZ_EINVAL;
+    if (method == METHOD_SAUVOLA || method == METHOD_NIBLACK)
+        return binarize_precision_report(method, image, H, W, in_pitch, h, w, params[0],
+                                         params[1], flips_dev, max_abs_dt_dev, stream);
+    Outputs o{};
+    o.flips = (unsigned long long *)flips_dev;
+    o.maxdt_bits = (unsigned long long *)max_abs_dt_dev;
+    return run_ext(method, image, H, W, in_pitch, h, w, params, MODE_REPORT, o, stream);
 }
 
 int64_t bz_last_fp64_fallbacks(void *stream)

@@ -30,6 +30,15 @@ int64_t window_tile_rows(int64_t H, int64_t W, int h, int w);
 cudaError_t launch_window(int mode, const Image &g, const Window &win, const Thresh &T,
                           const Outputs &o, cudaStream_t stream);
 
+// The other Table 1 methods (k_table1.cu).  prm = {k, R, alpha1, k1, k2,
+// gamma, p, q}.
+ThreshExt make_thresh_ext(int method, const double *prm, const GStats *gs, unsigned long long N);
+cudaError_t launch_global_stats(const Image &g, GStats *gs, cudaStream_t stream);
+cudaError_t launch_global_finalize(const GStats *gs, unsigned long long N, double *stats,
+                                   uint64_t *sums, cudaStream_t stream);
+cudaError_t launch_window_ext(int mode, const Image &g, const Window &win, const ThreshExt &T,
+                              const Outputs &o, cudaStream_t stream);
+
 cudaError_t launch_quantile(const Image &g, const Window &win, int32_t q_num, int32_t q_den,
                             int32_t offset, uint8_t *out, int64_t out_pitch, uint8_t *Q,
                             cudaStream_t stream);

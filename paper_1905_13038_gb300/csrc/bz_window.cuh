@@ -40,6 +40,11 @@ struct Window {
     int h, w, l, r, o, u;
 };
 
+__device__ __forceinline__ float sqrt_approx(float x);
+}  // namespace bz
+#include "bz_table1.cuh"
+namespace bz {
+
 // t = alpha*m + (beta*m + gamma)*s ; Sauvola: alpha = 1-k, beta = k/R,
 // gamma = 0 ; Niblack: alpha = 1, beta = 0, gamma = k.
 struct Thresh {
@@ -48,7 +53,15 @@ struct Thresh {
     float eps;      // relative part of the certified bound
     float delta64;  // absolute bound on |t64 - t_exact|
     double k, R;    // canonical FP64 parameters
-    int method;     // 0 Sauvola, 1 Niblack
+    int method;     // a bz::Method other than METHOD_QUANTILE
+};
+
+// The other Table 1 methods add their parameters and the global sums (kept
+// out of Thresh so that the batched work list does not grow).
+struct ThreshExt : Thresh {
+    ExtParams X;           // Feng and Phansalkar parameters
+    const GStats *gs;      // global sums (Wolf, Feng, Rais, Phansalkar)
+    unsigned long long N;  // pixels of the image, for the global statistics
 };
 
 struct Outputs {
@@ -171,6 +184,27 @@ static __device__ __noinline__ uint32_t fp64_bit(int method, uint32_t I, uint32_
     return ((double)I <= canonical_t(method, S1, S2, n, k, R)) ? 0u : 1u;
 }
 
+// The same for the other Table 1 methods (scalars only, so that nothing is
+// spilled to local memory for the call).
+static __device__ __noinline__ uint32_t fp64_bit_ext(int method, uint32_t I, uint32_t S1, uint64_t S2,
+                                                     uint32_t n, double k, double R, double alpha1,
+                                                     double k1, double k2, double gamma, double p,
+                                                     double q, double L, double M, double S)
+{
+    ExtParams X;
+    X.alpha1 = alpha1;
+    X.k1 = k1;
+    X.k2 = k2;
+    X.gamma = gamma;
+    X.p = p;
+    X.q = q;
+    Global G;
+    G.L = L;
+    G.M = M;
+    G.S = S;
+    return ((double)I <= canonical_t_ext(method, S1, S2, n, k, R, X, G)) ? 0u : 1u;
+}
+
 // ---- packed-byte arithmetic for the E slide (two columns per step) ------
 // dp2a.lo/hi with an unsigned 16-bit pair operand and unsigned bytes.
 __device__ __forceinline__ uint32_t dp2a_lo_uu(uint32_t a, uint32_t b, uint32_t c)
@@ -280,11 +314,52 @@ __device__ __forceinline__ float v_float(uint32_t n, uint64_t S2, uint32_t S1)
     return fmaf(fhi, 4294967296.0f, __uint2float_rn((uint32_t)V));
 }
 
+// The 8 pixels of one lane and row with a Table 1 threshold other than
+// Sauvola and Niblack: FP32 threshold, and in MODE_FP64 the certified bound
+// (undecided pixels go to the out-of-line FP64 decision); in MODE_REPORT the
+// FP32-vs-FP64 flips and the largest |t32 - t64|.
+template <int METHOD, int MODE, bool INTERIOR, typename S2T>
+__device__ __forceinline__ void ext_row8(const ExtF &F, const ThreshExt &T, const Global &G, uint2 P,
+                                         uint32_t off1, const uint32_t (&p1)[kColsPerLane], S2T off2,
+                                         const S2T (&p2)[kColsPerLane], uint32_t nw, uint32_t nrow,
+                                         const uint32_t (&cols)[kColsPerLane], float inv_nw,
+                                         float inv_rows, const float (&inv_cols)[kColsPerLane],
+                                         int64_t j0, int64_t W, uint32_t &byte, uint32_t &undecided,
+                                         unsigned long long &nflip, double &maxdt)
+{
+#pragma unroll
+    for (int m = 0; m < kColsPerLane; m++) {
+        const uint32_t S1 = off1 + p1[m];
+        const uint64_t S2 = (uint64_t)(off2 + p2[m]);
+        const uint32_t n = INTERIOR ? nw : nrow * cols[m];
+        const float inv_n = INTERIOR ? inv_nw : inv_rows * inv_cols[m];
+        const float mu = __uint2float_rn(S1) * inv_n;
+        const float var = (v_float<S2T>(n, S2, S1) * inv_n) * inv_n;
+        float bnd;
+        const float t = ext_t32<METHOD>(F, mu, var, inv_n, bnd);
+        const float d = t - pixel_f(P, m);
+        const uint32_t bit = __float_as_uint(d) >> 31;
+        byte |= bit << m;
+        if (MODE == MODE_FP64) {
+            undecided |= (fabsf(d) <= bnd ? 1u : 0u) << m;
+        } else if (MODE == MODE_REPORT) {
+            if (j0 + m < W) {
+                const double t64 = canonical_t_ext(METHOD, S1, S2, n, T.k, T.R, T.X, G);
+                const uint32_t b64 = ((double)byte_at(P, m) <= t64) ? 0u : 1u;
+                nflip += (b64 != bit);
+                const double dt = fabs((double)t - t64);
+                maxdt = dt > maxdt ? dt : maxdt;
+            }
+        }
+    }
+}
+
 // S2T: uint32_t when h*w <= 66051 (S2 < 2^32), else unsigned long long.
+// EXT: the Table 1 thresholds other than Sauvola and Niblack (T.method).
 // INTERIOR: every lane's byte streams and outputs lie inside the row, the
 // image and pitch allow aligned 8-byte loads, and every output column has
 // the full window width w (warp-uniform; decided by window_tile).
-template <int MODE, bool VEC, bool INTERIOR, typename S2T>
+template <int MODE, bool VEC, bool INTERIOR, typename S2T, bool EXT = false>
 __device__ __forceinline__ void window_rows(const Image &g, const Window &win, const Thresh &T,
                                             const Outputs &o, int64_t x0, int64_t y0, int64_t y1,
                                             int lane)
@@ -436,7 +511,15 @@ __device__ __forceinline__ void window_rows(const Image &g, const Window &win, c
     if (y0 + 1 < y1)
         prefetch(y0 + 1);
 
-    const bool simple = T.method == 0 && T.alpha >= 0.0f && T.beta >= 0.0f;  // Sauvola, 0<=k<=1
+    const bool simple = !EXT && T.method == 0 && T.alpha >= 0.0f && T.beta >= 0.0f;  // Sauvola, 0<=k<=1
+    Global G{};
+    ExtF F{};
+    // only instantiated with EXT for a ThreshExt argument (k_window_ext)
+    const ThreshExt &TX = static_cast<const ThreshExt &>(T);
+    if (EXT) {
+        G = global_lms(*TX.gs, TX.N);
+        F = make_extf(T.method, T.k, T.R, TX.X, G, T.eps);
+    }
 
     for (int64_t i = y0; i < y1; i++) {
         if (i > y0) {
@@ -494,10 +577,25 @@ __device__ __forceinline__ void window_rows(const Image &g, const Window &win, c
 #pragma unroll
             for (int m = 0; m < kColsPerLane; m++) {
                 const uint32_t n = INTERIOR ? nw : nrow * cols[m];
-                byte |= fp64_bit(T.method, (uint32_t)byte_at(P, m), off1 + p1[m],
-                                 (uint64_t)(off2 + p2[m]), n, T.k, T.R)
+                byte |= (EXT ? fp64_bit_ext(T.method, (uint32_t)byte_at(P, m), off1 + p1[m],
+                                            (uint64_t)(off2 + p2[m]), n, T.k, T.R, TX.X.alpha1,
+                                            TX.X.k1, TX.X.k2, TX.X.gamma, TX.X.p, TX.X.q, G.L, G.M, G.S)
+                             : fp64_bit(T.method, (uint32_t)byte_at(P, m), off1 + p1[m],
+                                        (uint64_t)(off2 + p2[m]), n, T.k, T.R))
                         << m;
             }
+        } else if (EXT) {
+#define BZ_EXT_ROW(M_)                                                                             \
+    ext_row8<M_, MODE, INTERIOR, S2T>(F, TX, G, P, off1, p1, off2, p2, nw, nrow, cols, inv_nw, inv_rows, \
+                                      inv_cols, j0, W, byte, undecided, nflip, maxdt)
+            switch (T.method) {
+            case METHOD_WOLF: BZ_EXT_ROW(METHOD_WOLF); break;
+            case METHOD_FENG: BZ_EXT_ROW(METHOD_FENG); break;
+            case METHOD_RAIS: BZ_EXT_ROW(METHOD_RAIS); break;
+            case METHOD_NICK: BZ_EXT_ROW(METHOD_NICK); break;
+            default: BZ_EXT_ROW(METHOD_PHANSALKAR); break;
+            }
+#undef BZ_EXT_ROW
         } else if (INTERIOR && simple && MODE != MODE_REPORT) {
             // Sauvola with 0 <= k <= 1: t = m (alpha + beta s), |terms| = t
             const float inv_n2 = inv_nw * inv_nw;
@@ -550,8 +648,13 @@ __device__ __forceinline__ void window_rows(const Image &g, const Window &win, c
                 for (int m = 0; m < kColsPerLane; m++) {
                     if (undecided >> m & 1u) {
                         const uint32_t n = INTERIOR ? nw : nrow * cols[m];
-                        const uint32_t b = fp64_bit(T.method, (uint32_t)byte_at(P, m), off1 + p1[m],
-                                                    (uint64_t)(off2 + p2[m]), n, T.k, T.R);
+                        const uint32_t b =
+                            EXT ? fp64_bit_ext(T.method, (uint32_t)byte_at(P, m), off1 + p1[m],
+                                               (uint64_t)(off2 + p2[m]), n, T.k, T.R, TX.X.alpha1,
+                                               TX.X.k1, TX.X.k2, TX.X.gamma, TX.X.p, TX.X.q, G.L, G.M,
+                                               G.S)
+                                : fp64_bit(T.method, (uint32_t)byte_at(P, m), off1 + p1[m],
+                                           (uint64_t)(off2 + p2[m]), n, T.k, T.R);
                         byte = (byte & ~(1u << m)) | (b << m);
                     }
                 }

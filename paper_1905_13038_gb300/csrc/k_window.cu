@@ -36,7 +36,7 @@ constexpr float kEpsF32 = 24.0f / 16777216.0f;
 
 Thresh make_thresh(int method, double k, double R)
 {
-    Thresh T;
+    Thresh T{};
     T.method = method;
     T.k = k;
     T.R = R;

@@ -26,7 +26,9 @@ def test_header_declares_expected_entry_points():
     for n in ["binarize_sauvola", "binarize_niblack", "binarize_quantile", "window_sums",
               "window_quantile", "binarize_precision_report", "binarize_batch", "bz_server_create",
               "bz_server_submit", "bz_server_wait", "bz_server_cancel", "bz_server_destroy",
-              "bz_status_string", "bz_last_fp64_fallbacks"]:
+              "bz_status_string", "bz_last_fp64_fallbacks", "binarize_wolf", "binarize_feng",
+              "binarize_rais", "binarize_nick", "binarize_phansalkar", "global_stats",
+              "binarize_precision_report_ext", "binarize_batch_noalloc"]:
         assert n in names, n
 
 

@@ -1,0 +1,193 @@
+"""GPU parity of the other Table 1 methods (Wolf, Feng, Rais, NICK,
+Phansalkar) and of the global statistics, against the CPU oracle, through
+the C ABI.
+
+Bar:
+* global L, M, S: bit-exact doubles; sums exact.
+* Wolf, Rais, NICK in BZ_FP64 and BZ_FP64_DIRECT: bit-exact (every operation
+  of the canonical formula is a correctly rounded IEEE operation on both
+  sides).
+* Feng and Phansalkar in BZ_FP64 / BZ_FP64_DIRECT: the device pow/exp and
+  the host libm may differ by an ulp, so a pixel may differ only where
+  |I - t_oracle| <= 1e-9 (a few ulps of t <= 255 plus the propagated error).
+* BZ_FP32: a pixel may differ only where |I - t_oracle| <= 2e-3.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_helpers import check_packed, out_buffer, to_device, unpack
+
+pytestmark = pytest.mark.gpu
+
+PRM = {
+    oracle.WOLF: dict(k=0.5, R=128.0),
+    oracle.FENG: dict(alpha1=0.88, k1=0.25, k2=0.04, gamma=2.0, R=128.0),
+    oracle.RAIS: dict(k=0.3),
+    oracle.NICK: dict(k=-0.1),
+    oracle.PHANSALKAR: dict(k=0.25, R=127.5, p=2.0, q=10.0 / 255.0),
+}
+EXACT = {oracle.WOLF, oracle.RAIS, oracle.NICK}
+NAMES = {oracle.WOLF: "wolf", oracle.FENG: "feng", oracle.RAIS: "rais", oracle.NICK: "nick",
+         oracle.PHANSALKAR: "phansalkar"}
+
+SHAPES = [
+    # H, W, h, w
+    (97, 600, 15, 15),
+    (130, 515, 31, 127),
+    (40, 33, 2, 3),
+    (1, 700, 5, 9),
+    (700, 1, 9, 5),
+    (17, 23, 100, 120),
+    (270, 290, 260, 257),  # 64-bit S2
+    (64, 520, 511, 511),
+]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built(cuda_device):
+    import paper_1905_13038_gb300 as bz
+    bz.build()
+    return bz
+
+
+def run_gpu(method, t, h, w, W, precision, out=None):
+    import paper_1905_13038_gb300 as bz
+    fn = getattr(bz, f"binarize_{NAMES[method]}")
+    return fn(t, h, w, **PRM[method], out=out, precision=precision, W=W)
+
+
+def oracle_params(method):
+    return oracle.params(**PRM[method])
+
+
+def compare(method, img, W, h, w, got_packed, precision):
+    """Bit-exact where the bar says so; otherwise only near-ties may differ."""
+    prm = oracle_params(method)
+    bits, packed = oracle.binarize_ext(method, img, h, w, prm, W=W)
+    if precision != "fp32" and method in EXACT:
+        check_packed(got_packed, packed, W)
+        return 0
+    got = unpack(got_packed.cpu().numpy()[:, : (W + 7) // 8], W)
+    diff = got != bits
+    if diff.any():
+        S1, S2, n = oracle.window_sums(img, h, w, W=W)
+        glob, _ = oracle.global_stats(img, W=W)
+        tt = oracle.threshold_ext(method, S1, S2, n, prm, glob)
+        I = img[:, :W].astype(np.float64)
+        tol = 2e-3 if precision == "fp32" else 1e-9
+        gap = np.abs(I - tt)[diff]
+        assert gap.max() <= tol, f"{diff.sum()} pixels differ, largest |I - t| = {gap.max()}"
+    # padding bits and bytes past ceil(W/8)
+    wb = (W + 7) // 8
+    raw = got_packed.cpu().numpy()
+    if W % 8:
+        assert (raw[:, wb - 1] >> (W % 8) == 0).all()
+    return int(diff.sum())
+
+
+@pytest.mark.parametrize("H,W", [(1, 1), (3, 17), (97, 600), (130, 515), (700, 1)])
+@pytest.mark.parametrize("layout", ["aligned", "pitch+5", "misaligned"])
+def test_global_stats_exact(H, W, layout):
+    import paper_1905_13038_gb300 as bz
+    extra = 5 if layout == "pitch+5" else 0
+    img = synth.document(H, W, 7 + H * W, pitch=W + extra)
+    if extra:
+        img[:, W:] = 0  # padding must not reach L, M or S
+    t, _ = to_device(img, W, misalign=3 if layout == "misaligned" else 0)
+    stats, sums = bz.global_stats(t, W=W)
+    est, esums = oracle.global_stats(img, W=W)
+    np.testing.assert_array_equal(stats.cpu().numpy(), est)
+    assert tuple(int(v) for v in sums.cpu().numpy()) == esums
+
+
+def test_global_stats_128bit_numerator():
+    import paper_1905_13038_gb300 as bz
+    img = synth.uniform(4400, 4400, 5, lo=235, hi=255)
+    t, _ = to_device(img)
+    stats, sums = bz.global_stats(t)
+    est, (sm, sq, N) = oracle.global_stats(img)
+    assert N * sq > 2**64
+    np.testing.assert_array_equal(stats.cpu().numpy(), est)
+
+
+@pytest.mark.parametrize("method", list(PRM))
+@pytest.mark.parametrize("precision", ["fp64", "fp64_direct", "fp32"])
+@pytest.mark.parametrize("H,W,h,w", SHAPES)
+def test_table1_parity(method, precision, H, W, h, w):
+    img = synth.document(H, W, 31 * H + W + method, stains=1 if min(H, W) > 20 else 0)
+    t, _ = to_device(img, W)
+    out = out_buffer(H, W, extra=2)
+    run_gpu(method, t, h, w, W, precision, out=out)
+    compare(method, img, W, h, w, out, precision)
+
+
+@pytest.mark.parametrize("method", list(PRM))
+@pytest.mark.parametrize("layout", ["pitch+5", "misaligned"])
+def test_table1_layouts(method, layout):
+    H, W, h, w = 150, 777, 31, 31
+    extra = 5 if layout == "pitch+5" else 0
+    img = synth.document(H, W, 4242 + method, stains=1, pitch=W + extra)
+    t, _ = to_device(img, W, misalign=3 if layout == "misaligned" else 0)
+    out = out_buffer(H, W, extra=1)
+    run_gpu(method, t, h, w, W, "fp64", out=out)
+    compare(method, img[:, :W] if not extra else img, W, h, w, out, "fp64")
+
+
+@pytest.mark.parametrize("method", list(PRM))
+def test_table1_full_page(method):
+    # the bench's page size, one launch as the bench would time it
+    img = synth.document(3072, 4096, 0x19051303800 + 2, stains=3)
+    t, _ = to_device(img)
+    out = run_gpu(method, t, 31, 31, 4096, "fp64")
+    compare(method, img, 4096, 31, 31, out, "fp64")
+
+
+@pytest.mark.parametrize("method", list(PRM))
+def test_table1_degenerate_images(method):
+    import paper_1905_13038_gb300 as bz
+    # constant image: S = 0, s = 0 everywhere (Rais takes f = 0), L = m
+    for val in (0, 77, 255):
+        img = np.full((40, 300), val, np.uint8)
+        t, _ = to_device(img)
+        out = run_gpu(method, t, 7, 9, 300, "fp64")
+        compare(method, img, 300, 7, 9, out, "fp64")
+    # two-level image (salt and pepper only)
+    img = (synth.uniform(50, 260, 3, 0, 1) * 255).astype(np.uint8)
+    t, _ = to_device(img)
+    out = run_gpu(method, t, 5, 5, 260, "fp64")
+    compare(method, img, 260, 5, 5, out, "fp64")
+
+
+@pytest.mark.parametrize("method", list(PRM))
+def test_precision_report_ext_counts_fp32_flips(method):
+    import paper_1905_13038_gb300 as bz
+    img = synth.document(300, 1000, 77 + method, stains=2)
+    t, _ = to_device(img)
+    prm = oracle_params(method)
+    flips, maxdt = bz.binarize_precision_report_ext(method, t, 31, 31, prm)
+    o32 = run_gpu(method, t, 31, 31, 1000, "fp32")
+    o64 = run_gpu(method, t, 31, 31, 1000, "fp64_direct")
+    a = unpack(o32.cpu().numpy(), 1000)
+    b = unpack(o64.cpu().numpy(), 1000)
+    assert flips == int((a != b).sum())
+    assert 0.0 <= maxdt <= 2e-3
+
+
+def test_table1_rejects_bad_parameters():
+    import paper_1905_13038_gb300 as bz
+    img = synth.document(20, 40, 1)
+    t, _ = to_device(img)
+    with pytest.raises(bz.BinarizeError):
+        bz.binarize_feng(t, 5, 5, gamma=-1.0)
+    with pytest.raises(bz.BinarizeError):
+        bz.binarize_feng(t, 5, 5, gamma=17.0)
+    with pytest.raises(bz.BinarizeError):
+        bz.binarize_wolf(t, 5, 5, R=0.0)
+    with pytest.raises(bz.BinarizeError):
+        bz.binarize_phansalkar(t, 5, 5, q=-1.0)
+    with pytest.raises(bz.BinarizeError):
+        bz.binarize_nick(t, 5, 5, k=float("nan"))
+    with pytest.raises(bz.BinarizeError):
+        bz.binarize_rais(t, 0, 5)
