@@ -70,6 +70,10 @@ def _load():
         "oracle_binarize_quantile": ([P, i64, i64, i64, i32, i32, i32, i32, i32, P, P, i64, i32], ctypes.c_int),
         "oracle_window_params": ([i32, i32, P, P, P, P], None),
         "oracle_global_stats": ([P, i64, i64, i64, P, P], ctypes.c_int),
+        "oracle_window_minmax_bruteforce": ([P, i64, i64, i64, i32, i32, P, P], ctypes.c_int),
+        "oracle_window_minmax_deque": ([P, i64, i64, i64, i32, i32, P, P], ctypes.c_int),
+        "oracle_binarize_bernsen": ([P, i64, i64, i64, i32, i32, i32, P, P, i64], ctypes.c_int),
+        "oracle_window_minmax_at": ([P, i64, i64, i64, i32, i32, P, P, i64, P, P], None),
         "oracle_threshold_ext_array": ([i32, P, P, P, i64, P, P, P], None),
         "oracle_binarize_ext": ([i32, P, i64, i64, i64, i32, i32, P, P, P, i64], ctypes.c_int),
     }
@@ -300,4 +304,42 @@ def binarize_ext(method: int, img: np.ndarray, h: int, w: int, prm, W: int | Non
     packed = np.empty((H, out_pitch), np.uint8)
     _check(_load().oracle_binarize_ext(method, img.ctypes.data, H, W, pitch, h, w, prm.ctypes.data,
                                        bits.ctypes.data, packed.ctypes.data, out_pitch), "binarize_ext")
+    return bits, packed
+
+
+# ------------------------------------------------------- local min / max --
+def window_minmax(img: np.ndarray, h: int, w: int, route: str = "deque", W: int | None = None):
+    """(min, max) of the clipped window, each (H, W) uint8.  route: 'deque'
+    (separable monotonic deques) or 'bruteforce' (direct loops)."""
+    img, H, W, pitch = _img(img, W)
+    mn = np.empty((H, W), np.uint8)
+    mx = np.empty((H, W), np.uint8)
+    fn = getattr(_load(), f"oracle_window_minmax_{route}")
+    _check(fn(img.ctypes.data, H, W, pitch, h, w, mn.ctypes.data, mx.ctypes.data), route)
+    return mn, mx
+
+
+def window_minmax_at(img: np.ndarray, h: int, w: int, ii, jj, W: int | None = None):
+    img, H, W, pitch = _img(img, W)
+    ii = np.ascontiguousarray(ii, np.int64)
+    jj = np.ascontiguousarray(jj, np.int64)
+    if ii.size and (ii.min() < 0 or ii.max() >= H or jj.min() < 0 or jj.max() >= W):
+        raise ValueError("sample position outside the image")
+    mn = np.empty(ii.size, np.uint8)
+    mx = np.empty(ii.size, np.uint8)
+    _load().oracle_window_minmax_at(img.ctypes.data, H, W, pitch, h, w, ii.ctypes.data, jj.ctypes.data,
+                                    ii.size, mn.ctypes.data, mx.ctypes.data)
+    return mn, mx
+
+
+def binarize_bernsen(img: np.ndarray, h: int, w: int, contrast_limit: int = 15, W: int | None = None,
+                     out_pitch: int | None = None):
+    """(bits, packed) of Bernsen's midrange threshold with a contrast limit."""
+    img, H, W, pitch = _img(img, W)
+    out_pitch = (W + 7) // 8 if out_pitch is None else out_pitch
+    bits = np.empty((H, W), np.uint8)
+    packed = np.empty((H, out_pitch), np.uint8)
+    _check(_load().oracle_binarize_bernsen(img.ctypes.data, H, W, pitch, h, w, contrast_limit,
+                                           bits.ctypes.data, packed.ctypes.data, out_pitch),
+           "binarize_bernsen")
     return bits, packed

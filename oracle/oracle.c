@@ -895,3 +895,170 @@ int oracle_binarize_ext(int32_t method, const uint8_t *img, int64_t H, int64_t W
         free(b);
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* (x) Local minimum and maximum (Sec. 3.4: Bernsen's midrange and the local  */
+/*     contrast, computed recursively with deques).  The window is Algorithm  */
+/*     1's, clipped to the image: out-of-image pixels take no part (a 0 would */
+/*     be a false minimum).  The window always holds its own centre pixel.    */
+/* ------------------------------------------------------------------------ */
+
+/* Definition: direct loops over the clipped window. */
+int oracle_window_minmax_bruteforce(const uint8_t *img, int64_t H, int64_t W,
+                                    int64_t pitch, int32_t h, int32_t w,
+                                    uint8_t *mn, uint8_t *mx)
+{
+    if (check_args(H, W, pitch, h, w))
+        return 1;
+    int32_t l, r, o, u;
+    oracle_window_params(h, w, &l, &r, &o, &u);
+    for (int64_t i = 0; i < H; i++)
+        for (int64_t j = 0; j < W; j++) {
+            uint32_t lo = 255, hi = 0;
+            for (int64_t a = i - o + 1; a <= i + u; a++)
+                for (int64_t b = j - l + 1; b <= j + r; b++) {
+                    if (a < 0 || a >= H || b < 0 || b >= W)
+                        continue;
+                    uint32_t v = img[a * pitch + b];
+                    lo = v < lo ? v : lo;
+                    hi = v > hi ? v : hi;
+                }
+            mn[i * W + j] = (uint8_t)lo;
+            mx[i * W + j] = (uint8_t)hi;
+        }
+    return 0;
+}
+
+/* Sliding extremum of one line of `len` values (stride `step`) over the
+ * window (x - back, x + fwd] clipped to [0, len), with a monotonic deque of
+ * indices: each index enters once and leaves once, so Theta(len) for any
+ * window (the recursive scheme Sec. 3.4 names).  want_max selects max. */
+static void slide_extremum(const uint8_t *src, int64_t step, int64_t len,
+                           int32_t back, int32_t fwd, int want_max,
+                           uint8_t *dst, int64_t dstep, int64_t *dq)
+{
+    int64_t head = 0, tail = 0; /* deque dq[head, tail) */
+    int64_t next = 0;           /* next index to enter */
+    for (int64_t x = 0; x < len; x++) {
+        int64_t last = x + fwd < len - 1 ? x + fwd : len - 1;
+        while (next <= last) {
+            uint8_t v = src[next * step];
+            while (tail > head) {
+                uint8_t b = src[dq[tail - 1] * step];
+                if (want_max ? (b <= v) : (b >= v))
+                    tail--;
+                else
+                    break;
+            }
+            dq[tail++] = next++;
+        }
+        while (dq[head] <= x - back)
+            head++;
+        dst[x * dstep] = src[dq[head] * step];
+    }
+}
+
+/* Separable sliding min/max: vertical extrema of every column over rows
+ * (i-o, i+u], then horizontal extrema of those over columns (j-l, j+r]. */
+int oracle_window_minmax_deque(const uint8_t *img, int64_t H, int64_t W,
+                               int64_t pitch, int32_t h, int32_t w,
+                               uint8_t *mn, uint8_t *mx)
+{
+    if (check_args(H, W, pitch, h, w))
+        return 1;
+    int32_t l, r, o, u;
+    oracle_window_params(h, w, &l, &r, &o, &u);
+    size_t HW = (size_t)(H * W);
+    uint8_t *vmn = (uint8_t *)malloc(HW), *vmx = (uint8_t *)malloc(HW);
+    int64_t *dq = (int64_t *)malloc((size_t)(H > W ? H : W) * sizeof(int64_t));
+    if (!vmn || !vmx || !dq) {
+        free(vmn);
+        free(vmx);
+        free(dq);
+        return 2;
+    }
+    for (int64_t j = 0; j < W; j++) {
+        slide_extremum(img + j, pitch, H, o, u, 0, vmn + j, W, dq);
+        slide_extremum(img + j, pitch, H, o, u, 1, vmx + j, W, dq);
+    }
+    for (int64_t i = 0; i < H; i++) {
+        slide_extremum(vmn + i * W, 1, W, l, r, 0, mn + i * W, 1, dq);
+        slide_extremum(vmx + i * W, 1, W, l, r, 1, mx + i * W, 1, dq);
+    }
+    free(vmn);
+    free(vmx);
+    free(dq);
+    return 0;
+}
+
+/* Bernsen's decision from the window extrema, in integers:
+ *   contrast c = mx - mn;
+ *   c >= contrast_limit:  bit = 0 iff I <= (mn + mx)/2, i.e. 2I <= mn + mx;
+ *   c <  contrast_limit:  the window is one class, dark (0) iff its
+ *                         midrange is at most 127.5, i.e. mn + mx <= 255. */
+static inline uint8_t bernsen_bit(uint32_t I, uint32_t lo, uint32_t hi,
+                                  int32_t contrast_limit)
+{
+    if ((int32_t)(hi - lo) >= contrast_limit)
+        return (2 * I <= lo + hi) ? 0 : 1;
+    return (lo + hi <= 255) ? 0 : 1;
+}
+
+int oracle_binarize_bernsen(const uint8_t *img, int64_t H, int64_t W,
+                            int64_t pitch, int32_t h, int32_t w,
+                            int32_t contrast_limit, uint8_t *bits,
+                            uint8_t *out, int64_t out_pitch)
+{
+    if (check_args(H, W, pitch, h, w) || contrast_limit < 0 || contrast_limit > 256)
+        return 1;
+    if (out && out_pitch < (W + 7) / 8)
+        return 1;
+    size_t HW = (size_t)(H * W);
+    uint8_t *mn = (uint8_t *)malloc(HW), *mx = (uint8_t *)malloc(HW);
+    uint8_t *b = bits ? bits : (uint8_t *)malloc(HW);
+    if (!mn || !mx || !b) {
+        free(mn);
+        free(mx);
+        if (!bits)
+            free(b);
+        return 2;
+    }
+    int rc = oracle_window_minmax_deque(img, H, W, pitch, h, w, mn, mx);
+    if (rc == 0) {
+        for (int64_t i = 0; i < H; i++)
+            for (int64_t j = 0; j < W; j++)
+                b[i * W + j] = bernsen_bit(img[i * pitch + j], mn[i * W + j],
+                                           mx[i * W + j], contrast_limit);
+        if (out)
+            oracle_pack_bits(b, H, W, out, out_pitch);
+    }
+    free(mn);
+    free(mx);
+    if (!bits)
+        free(b);
+    return rc;
+}
+
+/* Window extrema at sampled positions (direct loops), for full-size checks. */
+void oracle_window_minmax_at(const uint8_t *img, int64_t H, int64_t W,
+                             int64_t pitch, int32_t h, int32_t w,
+                             const int64_t *ii, const int64_t *jj, int64_t count,
+                             uint8_t *mn, uint8_t *mx)
+{
+    int32_t l, r, o, u;
+    oracle_window_params(h, w, &l, &r, &o, &u);
+    for (int64_t x = 0; x < count; x++) {
+        int64_t i = ii[x], j = jj[x];
+        uint32_t lo = 255, hi = 0;
+        for (int64_t a = i - o + 1; a <= i + u; a++)
+            for (int64_t b = j - l + 1; b <= j + r; b++) {
+                if (a < 0 || a >= H || b < 0 || b >= W)
+                    continue;
+                uint32_t v = img[a * pitch + b];
+                lo = v < lo ? v : lo;
+                hi = v > hi ? v : hi;
+            }
+        mn[x] = (uint8_t)lo;
+        mx[x] = (uint8_t)hi;
+    }
+}

@@ -91,4 +91,18 @@ void oracle_threshold_ext_array(int32_t method, const uint32_t *S1, const uint64
 int oracle_binarize_ext(int32_t method, const uint8_t *img, int64_t H, int64_t W,
                         int64_t pitch, int32_t h, int32_t w, const double *prm,
                         uint8_t *bits, uint8_t *out, int64_t out_pitch);
+int oracle_window_minmax_bruteforce(const uint8_t *img, int64_t H, int64_t W,
+                                    int64_t pitch, int32_t h, int32_t w,
+                                    uint8_t *mn, uint8_t *mx);
+int oracle_window_minmax_deque(const uint8_t *img, int64_t H, int64_t W,
+                               int64_t pitch, int32_t h, int32_t w,
+                               uint8_t *mn, uint8_t *mx);
+int oracle_binarize_bernsen(const uint8_t *img, int64_t H, int64_t W,
+                            int64_t pitch, int32_t h, int32_t w,
+                            int32_t contrast_limit, uint8_t *bits,
+                            uint8_t *out, int64_t out_pitch);
+void oracle_window_minmax_at(const uint8_t *img, int64_t H, int64_t W,
+                             int64_t pitch, int32_t h, int32_t w,
+                             const int64_t *ii, const int64_t *jj, int64_t count,
+                             uint8_t *mn, uint8_t *mx);
 #endif
