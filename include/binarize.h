@@ -142,6 +142,29 @@ bz_status binarize_precision_report(int32_t method, const uint8_t *image,
 int64_t bz_last_fp64_fallbacks(void *stream);
 
 /* ---------------------------------------------------------------------- */
+/* Local minimum and maximum (Sec. 3.4: Bernsen's midrange and the local  */
+/* contrast, kept recursively).  The window is Algorithm 1's, clipped to  */
+/* the image; pixels outside the image take no part (they are neither a   */
+/* minimum nor a maximum), so every window holds at least its own centre.  */
+/* ---------------------------------------------------------------------- */
+
+/* Parity export: mn and mx, dense H x W uint8 device arrays (caller-owned,
+ * neither overlapping the image nor each other). */
+bz_status window_minmax(const uint8_t *image, int64_t H, int64_t W,
+                        int64_t in_pitch, int32_t h, int32_t w, uint8_t *mn,
+                        uint8_t *mx, void *stream);
+
+/* Bernsen binarization, in integers: with c = mx - mn,
+ *   c >= contrast_limit:  bit = 0 iff 2 I <= mn + mx   (I <= midrange);
+ *   c <  contrast_limit:  the window is one class, bit = 0 iff
+ *                         mn + mx <= 255 (its midrange is dark).
+ * 0 <= contrast_limit <= 256 (0: midrange everywhere; 256: never). */
+bz_status binarize_bernsen(const uint8_t *image, int64_t H, int64_t W,
+                           int64_t in_pitch, int32_t h, int32_t w,
+                           int32_t contrast_limit, uint8_t *out,
+                           int64_t out_pitch, void *stream);
+
+/* ---------------------------------------------------------------------- */
 /* The other Table 1 methods (Sec. 3.4: one changed condition on the same */
 /* window statistics).  L, M and S are the global minimum, mean and        */
 /* population standard deviation of the image (Table 1 notations), found   */

@@ -25,6 +25,7 @@ __all__ = [
     "Server", "status_string",
     "WOLF", "FENG", "RAIS", "NICK", "PHANSALKAR", "binarize_wolf", "binarize_feng", "binarize_rais",
     "binarize_nick", "binarize_phansalkar", "global_stats", "binarize_precision_report_ext",
+    "window_minmax", "binarize_bernsen",
 ]
 
 FP64, FP32, FP64_DIRECT = 0, 1, 2
@@ -87,6 +88,8 @@ def _load():
         "binarize_nick": ([P, i64, i64, i64, i32, i32, f64, P, i64, st, P], st),
         "binarize_phansalkar": ([P, i64, i64, i64, i32, i32, f64, f64, f64, f64, P, i64, st, P], st),
         "global_stats": ([P, i64, i64, i64, P, P, P], st),
+        "window_minmax": ([P, i64, i64, i64, i32, i32, P, P, P], st),
+        "binarize_bernsen": ([P, i64, i64, i64, i32, i32, i32, P, i64, P], st),
         "binarize_precision_report_ext": ([i32, P, i64, i64, i64, i32, i32, P, P, P, P], st),
         "binarize_batch": ([ctypes.POINTER(_JobC), i32, st, P], st),
         "binarize_batch_noalloc": ([ctypes.POINTER(_JobC), i32, st, P], st),
@@ -282,6 +285,28 @@ def binarize_precision_report_ext(method: int, image, h: int, w: int, params, W:
            _load().binarize_precision_report_ext(method, ptr, H, W, pitch, h, w, prm, flips.data_ptr(),
                                                  maxdt.data_ptr(), _stream(stream)))
     return int(flips.item()), float(maxdt.item())
+
+
+def window_minmax(image, h: int, w: int, W: int | None = None, stream=None):
+    """(min, max) uint8 CUDA tensors (H, W) of the clipped window."""
+    import torch
+    ptr, H, W, pitch = _image(image, W)
+    mn = torch.empty((H, W), dtype=torch.uint8, device=image.device)
+    mx = torch.empty((H, W), dtype=torch.uint8, device=image.device)
+    _check("window_minmax", _load().window_minmax(ptr, H, W, pitch, h, w, mn.data_ptr(), mx.data_ptr(),
+                                                  _stream(stream)))
+    return mn, mx
+
+
+def binarize_bernsen(image, h: int, w: int, contrast_limit: int = 15, out=None, W: int | None = None,
+                     stream=None):
+    """Bernsen: midrange threshold where the window's contrast reaches the
+    limit, else the whole window is one class (dark iff its midrange <= 127.5)."""
+    ptr, H, W, pitch = _image(image, W)
+    out, op = _out(out, H, W, image.device)
+    _check("binarize_bernsen", _load().binarize_bernsen(ptr, H, W, pitch, h, w, contrast_limit,
+                                                        out.data_ptr(), op, _stream(stream)))
+    return out
 
 
 def last_fp64_fallbacks(stream=None) -> int:

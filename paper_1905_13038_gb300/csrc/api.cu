@@ -404,6 +404,45 @@ bz_status binarize_precision_report_ext(int32_t method, const uint8_t *image, in
     return run_ext(method, image, H, W, in_pitch, h, w, params, MODE_REPORT, o, stream);
 }
 
+bz_status window_minmax(const uint8_t *image, int64_t H, int64_t W, int64_t in_pitch, int32_t h,
+                        int32_t w, uint8_t *mn, uint8_t *mx, void *stream)
+{
+    bz_status st = check_image(image, H, W, in_pitch, h, w);
+    if (st != BZ_OK)
+        return st;
+    if (!mn || !mx)
+        return BZ_EINVAL;
+    const size_t img_bytes = (size_t)((H - 1) * in_pitch + W);
+    const size_t HW = (size_t)(H * W);
+    if (ranges_overlap(image, img_bytes, mn, HW) || ranges_overlap(image, img_bytes, mx, HW) ||
+        ranges_overlap(mn, HW, mx, HW))
+        return BZ_EOVERLAP;
+    Image g{image, H, W, in_pitch};
+    return launch_minmax(g, make_window(h, w), 0, mn, mx, nullptr, 0, (cudaStream_t)stream) ==
+                   cudaSuccess
+               ? BZ_OK
+               : BZ_ECUDA;
+}
+
+bz_status binarize_bernsen(const uint8_t *image, int64_t H, int64_t W, int64_t in_pitch,
+                           int32_t h, int32_t w, int32_t contrast_limit, uint8_t *out,
+                           int64_t out_pitch, void *stream)
+{
+    bz_status st = check_image(image, H, W, in_pitch, h, w);
+    if (st != BZ_OK)
+        return st;
+    st = check_out(image, H, W, in_pitch, out, out_pitch);
+    if (st != BZ_OK)
+        return st;
+    if (contrast_limit < 0 || contrast_limit > 256)
+        return BZ_EINVAL;
+    Image g{image, H, W, in_pitch};
+    return launch_minmax(g, make_window(h, w), contrast_limit, nullptr, nullptr, out, out_pitch,
+                         (cudaStream_t)stream) == cudaSuccess
+               ? BZ_OK
+               : BZ_ECUDA;
+}
+
 int64_t bz_last_fp64_fallbacks(void *stream)
 {
     int dev = 0;

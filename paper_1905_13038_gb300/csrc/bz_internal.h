@@ -39,6 +39,11 @@ cudaError_t launch_global_finalize(const GStats *gs, unsigned long long N, doubl
 cudaError_t launch_window_ext(int mode, const Image &g, const Window &win, const ThreshExt &T,
                               const Outputs &o, cudaStream_t stream);
 
+// Window extrema (dense mn, mx planes) or, when bits != null, Bernsen's
+// packed decision (k_minmax.cu).
+cudaError_t launch_minmax(const Image &g, const Window &win, int32_t contrast_limit, uint8_t *mn,
+                          uint8_t *mx, uint8_t *bits, int64_t out_pitch, cudaStream_t stream);
+
 cudaError_t launch_quantile(const Image &g, const Window &win, int32_t q_num, int32_t q_den,
                             int32_t offset, uint8_t *out, int64_t out_pitch, uint8_t *Q,
                             cudaStream_t stream);

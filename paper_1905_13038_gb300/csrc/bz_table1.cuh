@@ -17,10 +17,11 @@ enum Method : int {
     METHOD_PHANSALKAR = 7,
 };
 
-// Exact image-wide sums, produced by k_global_stats.  L starts at 0xFFFFFFFF,
-// the sums at 0.
+// Exact image-wide sums, produced by k_global_stats from an all-zero start:
+// the minimum is kept as Linv = 255 - L, a maximum, so that one memset
+// initialises everything.
 struct GStats {
-    unsigned int L;
+    unsigned int Linv;
     unsigned int pad;
     unsigned long long sum, sumsq;
 };
@@ -52,7 +53,7 @@ __device__ __forceinline__ double u128_to_double_rn(unsigned long long hi, unsig
 __device__ __forceinline__ Global global_lms(const GStats &G, unsigned long long N)
 {
     Global r;
-    r.L = __uint2double_rn(G.L);
+    r.L = __uint2double_rn(255u - G.Linv);
     const double Nd = __ull2double_rn(N);
     r.M = __ddiv_rn(__ull2double_rn(G.sum), Nd);
     const unsigned long long ph = __umul64hi(N, G.sumsq), pl = N * G.sumsq;

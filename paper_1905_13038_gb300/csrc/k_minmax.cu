@@ -1,0 +1,295 @@
+// Local minimum and maximum of the clipped window (Sec. 3.4: Bernsen's
+// midrange and the local contrast), and Bernsen binarization.
+//
+// The paper keeps the extrema recursively with deques.  A deque is a
+// sequential, data-dependent structure; on the GPU the same Theta(1)-per-
+// pixel bound comes from splitting every window at a fixed row (van Herk /
+// Gil-Werman): a CTA owns a tile of TW output columns x TR output rows and
+//  1. vertical: for a segment of rows [a, b) with b - a <= h every window
+//     (i-o, i+u] contains row c = a + u, so its extremum is ext(suffix
+//     extremum of rows i-o+1 .. c, prefix extremum of rows c+1 .. i+u).  One
+//     backward sweep of h rows stores the suffixes, one forward sweep of
+//     b - a - 1 rows combines them with the running prefix.  Four columns
+//     are packed per 32-bit word (byte-wise vmin/vmax).
+//  2. horizontal: on each row of vertical extrema (in shared memory) the
+//     extremum over 2^k consecutive columns is built by K = floor(log2 w)
+//     doubling steps, and the window's extremum is ext(M_K[start],
+//     M_K[start + w - 2^K]) (two overlapping blocks cover the window).
+// Pixels outside the image take no part: they read as 0xFF for the minimum
+// and 0x00 for the maximum.
+#include "bz_internal.h"
+
+namespace bz {
+
+constexpr int kMmThreads = 128;            // 4 warps
+constexpr int kMmTileCols = 512;           // TW
+constexpr int kMmTileRows = 32;            // TR
+constexpr int kMmMaxWords = 3;             // vertical words per thread (NWd <= 384)
+
+enum MmOut : int { MM_EXTREMA = 0, MM_BERNSEN = 1 };
+
+// Words of one extended row: 4 columns each, from xa = floor4(x0 - (l-1))
+// through x0 + TW - 1 + r, plus 34 words of padding for the shifted reads.
+__host__ __device__ inline int mm_words(int w)
+{
+    return (kMmTileCols + w - 1 + 3) / 4 + 1;
+}
+__host__ __device__ inline int mm_pitch_words(int w)
+{
+    return mm_words(w) + 34;
+}
+
+template <bool VEC4>
+__device__ __forceinline__ uint32_t mm_load(const Image &g, int64_t row, int64_t xw)
+{
+    const uint8_t *rp = g.img + row * g.pitch;
+    if (VEC4 && xw >= 0 && xw + 4 <= g.W)
+        return __ldg(reinterpret_cast<const uint32_t *>(rp + xw));
+    uint32_t v = 0;
+#pragma unroll
+    for (int b = 0; b < 4; b++) {
+        const int64_t c = xw + b;
+        if (c >= 0 && c < g.W)
+            v |= (uint32_t)rp[c] << (8 * b);
+    }
+    return v;
+}
+
+// Bytes [byte, byte+4) of a shared-memory row of words.
+__device__ __forceinline__ uint32_t mm_bytes(const uint32_t *row, int byte)
+{
+    const int q = byte >> 2, s = byte & 3;
+    return __funnelshift_r(row[q], row[q + 1], 8 * s);
+}
+
+template <int OUT, bool VEC4>
+__global__ void __launch_bounds__(kMmThreads)
+    k_minmax(Image g, Window win, int32_t contrast_limit, uint8_t *mn_out, uint8_t *mx_out,
+             uint8_t *bits, int64_t out_pitch, int64_t tiles_x)
+{
+    extern __shared__ uint32_t mm_smem[];
+    const int NWd = mm_words(win.w), NWP = mm_pitch_words(win.w);
+    uint32_t *Vmin = mm_smem;                        // [TR][NWP]
+    uint32_t *Vmax = mm_smem + kMmTileRows * NWP;    // [TR][NWP]
+
+    const int64_t tx = (int64_t)blockIdx.x % tiles_x, ty = (int64_t)blockIdx.x / tiles_x;
+    const int64_t x0 = tx * kMmTileCols, y0 = ty * kMmTileRows;
+    const int64_t y1 = y0 + kMmTileRows < g.H ? y0 + kMmTileRows : g.H;
+    const int l = win.l, r = win.r, o = win.o, u = win.u, h = win.h, w = win.w;
+    const int64_t xs = x0 - (l - 1);
+    const int64_t xa = xs >= 0 ? (xs & ~(int64_t)3) : -((-xs + 3) & ~(int64_t)3);
+    const int delta = (int)(xs - xa);
+    const int tid = threadIdx.x;
+
+    // padding words: neutral
+    for (int q = NWd + tid; q < NWP; q += kMmThreads)
+        for (int i = 0; i < kMmTileRows; i++) {
+            Vmin[i * NWP + q] = 0xFFFFFFFFu;
+            Vmax[i * NWP + q] = 0u;
+        }
+
+    // ---- 1. vertical extrema, per word column ----
+    uint32_t oob[kMmMaxWords];
+    int64_t xw[kMmMaxWords];
+    bool act[kMmMaxWords];
+#pragma unroll
+    for (int m = 0; m < kMmMaxWords; m++) {
+        const int q = tid + m * kMmThreads;
+        act[m] = q < NWd;
+        xw[m] = xa + 4 * (int64_t)q;
+        uint32_t mk = 0;
+#pragma unroll
+        for (int b = 0; b < 4; b++) {
+            const int64_t c = xw[m] + b;
+            if (c < 0 || c >= g.W)
+                mk |= 0xFFu << (8 * b);
+        }
+        oob[m] = mk;
+    }
+    for (int64_t a = y0; a < y1; a += h) {
+        const int64_t b = a + h < y1 ? a + h : y1;
+        const int64_t c = a + u;
+        // backward sweep: suffix extrema of rows s .. c, stored for the
+        // window starts s = i-o+1, i in [a, b)
+        uint32_t smin[kMmMaxWords], smax[kMmMaxWords];
+#pragma unroll
+        for (int m = 0; m < kMmMaxWords; m++) {
+            smin[m] = 0xFFFFFFFFu;
+            smax[m] = 0u;
+        }
+        for (int64_t s = c; s >= a - o + 1; s--) {
+            if (s >= 0 && s < g.H) {
+#pragma unroll
+                for (int m = 0; m < kMmMaxWords; m++) {
+                    if (act[m]) {
+                        const uint32_t v = mm_load<VEC4>(g, s, xw[m]);
+                        smin[m] = __vminu4(smin[m], v | oob[m]);
+                        smax[m] = __vmaxu4(smax[m], v & ~oob[m]);
+                    }
+                }
+            }
+            const int64_t i = s + o - 1;  // the output row whose window starts at s
+            if (i >= a && i < b) {
+#pragma unroll
+                for (int m = 0; m < kMmMaxWords; m++) {
+                    if (act[m]) {
+                        const int q = tid + m * kMmThreads;
+                        Vmin[(i - y0) * NWP + q] = smin[m];
+                        Vmax[(i - y0) * NWP + q] = smax[m];
+                    }
+                }
+            }
+        }
+        // forward sweep: prefix extrema of rows c+1 .. i+u
+        uint32_t pmin[kMmMaxWords], pmax[kMmMaxWords];
+#pragma unroll
+        for (int m = 0; m < kMmMaxWords; m++) {
+            pmin[m] = 0xFFFFFFFFu;
+            pmax[m] = 0u;
+        }
+        for (int64_t i = a + 1; i < b; i++) {
+            const int64_t q_row = i + u;
+#pragma unroll
+            for (int m = 0; m < kMmMaxWords; m++) {
+                if (act[m]) {
+                    if (q_row < g.H) {
+                        const uint32_t v = mm_load<VEC4>(g, q_row, xw[m]);
+                        pmin[m] = __vminu4(pmin[m], v | oob[m]);
+                        pmax[m] = __vmaxu4(pmax[m], v & ~oob[m]);
+                    }
+                    const int q = tid + m * kMmThreads;
+                    const int64_t x = (i - y0) * NWP + q;
+                    Vmin[x] = __vminu4(Vmin[x], pmin[m]);
+                    Vmax[x] = __vmaxu4(Vmax[x], pmax[m]);
+                }
+            }
+        }
+    }
+    __syncthreads();
+
+    // ---- 2. horizontal extrema by doubling, one warp per row ----
+    const int warp = tid >> 5, lane = tid & 31;
+    int K = 0;
+    while ((2 << K) <= w)
+        K++;
+    const int rows = (int)(y1 - y0);
+    for (int i = warp; i < rows; i += kMmThreads / 32) {
+        uint32_t *rmin = Vmin + i * NWP, *rmax = Vmax + i * NWP;
+        for (int k = 1; k <= K; k++) {
+            const int sh = 1 << (k - 1);  // bytes
+            uint32_t nmin[10], nmax[10];  // NWd <= 10 * 32
+#pragma unroll
+            for (int m = 0; m < 10; m++) {
+                const int q = lane + 32 * m;
+                if (q < NWd) {
+                    nmin[m] = __vminu4(rmin[q], mm_bytes(rmin, 4 * q + sh));
+                    nmax[m] = __vmaxu4(rmax[q], mm_bytes(rmax, 4 * q + sh));
+                }
+            }
+            __syncwarp();
+#pragma unroll
+            for (int m = 0; m < 10; m++) {
+                const int q = lane + 32 * m;
+                if (q < NWd) {
+                    rmin[q] = nmin[m];
+                    rmax[q] = nmax[m];
+                }
+            }
+            __syncwarp();
+        }
+        // window extremum of output column x0 + 4p + e: bytes at start
+        // 4p + delta and 4p + delta + w - 2^K
+        const int64_t row = y0 + i;
+        const int second = w - (1 << K);
+        if (OUT == MM_EXTREMA) {
+            for (int p = lane; p < kMmTileCols / 4; p += 32) {
+                const int64_t j0 = x0 + 4 * p;
+                if (j0 >= g.W)
+                    break;
+                const uint32_t lo = __vminu4(mm_bytes(rmin, 4 * p + delta),
+                                             mm_bytes(rmin, 4 * p + delta + second));
+                const uint32_t hi = __vmaxu4(mm_bytes(rmax, 4 * p + delta),
+                                             mm_bytes(rmax, 4 * p + delta + second));
+#pragma unroll
+                for (int e = 0; e < 4; e++) {
+                    if (j0 + e < g.W) {
+                        mn_out[row * g.W + j0 + e] = (uint8_t)(lo >> (8 * e));
+                        mx_out[row * g.W + j0 + e] = (uint8_t)(hi >> (8 * e));
+                    }
+                }
+            }
+        } else {
+            for (int p = lane; p < kMmTileCols / 8; p += 32) {
+                const int64_t j0 = x0 + 8 * p;
+                if (j0 >= g.W)
+                    break;
+                uint32_t byte = 0;
+#pragma unroll
+                for (int half = 0; half < 2; half++) {
+                    const int pw = 2 * p + half;
+                    const uint32_t lo = __vminu4(mm_bytes(rmin, 4 * pw + delta),
+                                                 mm_bytes(rmin, 4 * pw + delta + second));
+                    const uint32_t hi = __vmaxu4(mm_bytes(rmax, 4 * pw + delta),
+                                                 mm_bytes(rmax, 4 * pw + delta + second));
+                    const uint32_t I4 = mm_load<VEC4>(g, row, j0 + 4 * half);
+#pragma unroll
+                    for (int e = 0; e < 4; e++) {
+                        const int32_t I = (int32_t)((I4 >> (8 * e)) & 0xFFu);
+                        const int32_t mn = (int32_t)((lo >> (8 * e)) & 0xFFu);
+                        const int32_t mx = (int32_t)((hi >> (8 * e)) & 0xFFu);
+                        const uint32_t bit = (mx - mn >= contrast_limit) ? (2 * I > mn + mx)
+                                                                          : (mn + mx > 255);
+                        byte |= bit << (4 * half + e);
+                    }
+                }
+                if (j0 + 8 > g.W)
+                    byte &= (1u << (g.W - j0)) - 1u;  // padding bits are 0
+                bits[row * out_pitch + (j0 >> 3)] = (uint8_t)byte;
+            }
+        }
+    }
+}
+
+template <int OUT, bool VEC4>
+static cudaError_t launch_mm_t(const Image &g, const Window &win, int32_t contrast_limit,
+                               uint8_t *mn, uint8_t *mx, uint8_t *bits, int64_t out_pitch,
+                               cudaStream_t stream)
+{
+    // the shared-memory opt-in (largest window), once per device
+    static unsigned long long configured = 0;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return e;
+    const size_t smem = (size_t)2 * kMmTileRows * mm_pitch_words(511) * sizeof(uint32_t);
+    if (dev >= 64 || !(configured >> dev & 1ull)) {
+        e = cudaFuncSetAttribute(k_minmax<OUT, VEC4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess)
+            return e;
+        if (dev < 64)
+            configured |= 1ull << dev;
+    }
+    const size_t need = (size_t)2 * kMmTileRows * mm_pitch_words(win.w) * sizeof(uint32_t);
+    const int64_t tiles_x = (g.W + kMmTileCols - 1) / kMmTileCols;
+    const int64_t tiles = tiles_x * ((g.H + kMmTileRows - 1) / kMmTileRows);
+    if (tiles > 2147483647LL)
+        return cudaErrorInvalidValue;
+    k_minmax<OUT, VEC4><<<(unsigned)tiles, kMmThreads, need, stream>>>(g, win, contrast_limit, mn, mx,
+                                                                       bits, out_pitch, tiles_x);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_minmax(const Image &g, const Window &win, int32_t contrast_limit, uint8_t *mn,
+                          uint8_t *mx, uint8_t *bits, int64_t out_pitch, cudaStream_t stream)
+{
+    const bool vec4 = ((uintptr_t)g.img % 4 == 0) && (g.pitch % 4 == 0);
+    if (bits)
+        return vec4 ? launch_mm_t<MM_BERNSEN, true>(g, win, contrast_limit, mn, mx, bits, out_pitch, stream)
+                    : launch_mm_t<MM_BERNSEN, false>(g, win, contrast_limit, mn, mx, bits, out_pitch,
+                                                     stream);
+    return vec4 ? launch_mm_t<MM_EXTREMA, true>(g, win, contrast_limit, mn, mx, bits, out_pitch, stream)
+                : launch_mm_t<MM_EXTREMA, false>(g, win, contrast_limit, mn, mx, bits, out_pitch, stream);
+}
+
+}  // namespace bz

@@ -84,7 +84,7 @@ __global__ void __launch_bounds__(kGsThreads) k_global_stats(Image g, GStats *gs
             t2 += sh2[q];
             tm = shm[q] < tm ? shm[q] : tm;
         }
-        atomicMin(&gs->L, tm);
+        atomicMax(&gs->Linv, 255u - tm);
         atomicAdd(&gs->sum, t1);
         atomicAdd(&gs->sumsq, t2);
     }
@@ -93,9 +93,6 @@ __global__ void __launch_bounds__(kGsThreads) k_global_stats(Image g, GStats *gs
 cudaError_t launch_global_stats(const Image &g, GStats *gs, cudaStream_t stream)
 {
     cudaError_t e = cudaMemsetAsync(gs, 0, sizeof(GStats), stream);
-    if (e != cudaSuccess)
-        return e;
-    e = cudaMemsetAsync(&gs->L, 0xFF, sizeof(unsigned int), stream);
     if (e != cudaSuccess)
         return e;
     const int64_t cpr = (g.W + 15) / 16;

@@ -28,7 +28,8 @@ def test_header_declares_expected_entry_points():
               "bz_server_submit", "bz_server_wait", "bz_server_cancel", "bz_server_destroy",
               "bz_status_string", "bz_last_fp64_fallbacks", "binarize_wolf", "binarize_feng",
               "binarize_rais", "binarize_nick", "binarize_phansalkar", "global_stats",
-              "binarize_precision_report_ext", "binarize_batch_noalloc"]:
+              "binarize_precision_report_ext", "binarize_batch_noalloc", "window_minmax",
+              "binarize_bernsen"]:
         assert n in names, n
 
 
