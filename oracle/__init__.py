@@ -74,6 +74,8 @@ def _load():
         "oracle_window_minmax_deque": ([P, i64, i64, i64, i32, i32, P, P], ctypes.c_int),
         "oracle_binarize_bernsen": ([P, i64, i64, i64, i32, i32, i32, P, P, i64], ctypes.c_int),
         "oracle_window_minmax_at": ([P, i64, i64, i64, i32, i32, P, P, i64, P, P], None),
+        "oracle_haar_bruteforce": ([P, i64, i64, i64, P, P, i32, P, P, i32, P], ctypes.c_int),
+        "oracle_haar_integral": ([P, i64, i64, i64, P, P, i32, P, P, i32, P], ctypes.c_int),
         "oracle_threshold_ext_array": ([i32, P, P, P, i64, P, P, P], None),
         "oracle_binarize_ext": ([i32, P, i64, i64, i64, i32, i32, P, P, P, i64], ctypes.c_int),
     }
@@ -343,3 +345,22 @@ def binarize_bernsen(img: np.ndarray, h: int, w: int, contrast_limit: int = 15, 
                                            bits.ctypes.data, packed.ctypes.data, out_pitch),
            "binarize_bernsen")
     return bits, packed
+
+
+# --------------------------------------------------------- Haar-like sums --
+def haar(img: np.ndarray, rows, cols, route: str = "integral", W: int | None = None) -> np.ndarray:
+    """Separable piecewise-constant window sum, int32 (H, W).  rows / cols:
+    lists of (length, weight) segments of the window's rows / columns
+    (h = sum of row lengths, w = sum of column lengths, placed as in
+    Algorithm 1).  route: 'integral' (four lookups per rectangle) or
+    'bruteforce' (direct loops)."""
+    img, H, W, pitch = _img(img, W)
+    rl = np.ascontiguousarray([r[0] for r in rows], np.int32)
+    rw = np.ascontiguousarray([r[1] for r in rows], np.int32)
+    cl = np.ascontiguousarray([c[0] for c in cols], np.int32)
+    cw = np.ascontiguousarray([c[1] for c in cols], np.int32)
+    out = np.empty((H, W), np.int32)
+    fn = getattr(_load(), f"oracle_haar_{route}")
+    _check(fn(img.ctypes.data, H, W, pitch, rl.ctypes.data, rw.ctypes.data, len(rows), cl.ctypes.data,
+              cw.ctypes.data, len(cols), out.ctypes.data), "haar")
+    return out

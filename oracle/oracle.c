@@ -1062,3 +1062,122 @@ void oracle_window_minmax_at(const uint8_t *img, int64_t H, int64_t W,
         mx[x] = (uint8_t)hi;
     }
 }
+
+/* ------------------------------------------------------------------------ */
+/* (xi) Haar-like features (Sec. 3.4: the recursive sums serve any sum over  */
+/*      rectangles).  A feature is a sum over Algorithm 1's h x w window with */
+/*      a separable, piecewise-constant weight f(a) g(b): the rows of the     */
+/*      window are cut into n_row segments (length, weight), the columns into */
+/*      n_col segments.  Two segments of opposite weight in one direction and */
+/*      one in the other give Viola and Jones's two-rectangle features, three */
+/*      give the three-rectangle ones, two by two the four-rectangle one.     */
+/*      Out-of-image pixels are 0, as for the window sums.                    */
+/* ------------------------------------------------------------------------ */
+static int haar_profile(const int32_t *len, const int32_t *wt, int32_t nseg,
+                        int32_t total, int32_t *prof)
+{
+    int32_t pos = 0;
+    for (int32_t s = 0; s < nseg; s++) {
+        if (len[s] < 1)
+            return 1;
+        for (int32_t q = 0; q < len[s]; q++) {
+            if (pos >= total)
+                return 1;
+            prof[pos++] = wt[s];
+        }
+    }
+    return pos == total ? 0 : 1;
+}
+
+/* Definition: the weighted sum over the window, by direct loops. */
+int oracle_haar_bruteforce(const uint8_t *img, int64_t H, int64_t W, int64_t pitch,
+                           const int32_t *row_len, const int32_t *row_wt, int32_t n_row,
+                           const int32_t *col_len, const int32_t *col_wt, int32_t n_col,
+                           int32_t *out)
+{
+    int32_t h = 0, w = 0;
+    for (int32_t s = 0; s < n_row; s++)
+        h += row_len[s];
+    for (int32_t s = 0; s < n_col; s++)
+        w += col_len[s];
+    if (check_args(H, W, pitch, h, w))
+        return 1;
+    int32_t *f = (int32_t *)malloc((size_t)h * sizeof(int32_t));
+    int32_t *g = (int32_t *)malloc((size_t)w * sizeof(int32_t));
+    if (!f || !g || haar_profile(row_len, row_wt, n_row, h, f) ||
+        haar_profile(col_len, col_wt, n_col, w, g)) {
+        free(f);
+        free(g);
+        return 1;
+    }
+    int32_t l, r, o, u;
+    oracle_window_params(h, w, &l, &r, &o, &u);
+    for (int64_t i = 0; i < H; i++)
+        for (int64_t j = 0; j < W; j++) {
+            int64_t acc = 0;
+            for (int32_t a = 0; a < h; a++)
+                for (int32_t b = 0; b < w; b++)
+                    acc += (int64_t)f[a] * g[b] *
+                           (int64_t)px(img, H, W, pitch, i - o + 1 + a, j - l + 1 + b);
+            out[i * W + j] = (int32_t)acc;
+        }
+    free(f);
+    free(g);
+    return 0;
+}
+
+/* Viola and Jones's route: every rectangle (row segment x column segment)
+ * summed by four lookups in the Sec. 2 integral image, times the product of
+ * the two weights. */
+int oracle_haar_integral(const uint8_t *img, int64_t H, int64_t W, int64_t pitch,
+                         const int32_t *row_len, const int32_t *row_wt, int32_t n_row,
+                         const int32_t *col_len, const int32_t *col_wt, int32_t n_col,
+                         int32_t *out)
+{
+    int32_t h = 0, w = 0;
+    for (int32_t s = 0; s < n_row; s++)
+        h += row_len[s];
+    for (int32_t s = 0; s < n_col; s++)
+        w += col_len[s];
+    if (check_args(H, W, pitch, h, w) || n_row < 1 || n_col < 1)
+        return 1;
+    for (int32_t s = 0; s < n_row; s++)
+        if (row_len[s] < 1)
+            return 1;
+    for (int32_t s = 0; s < n_col; s++)
+        if (col_len[s] < 1)
+            return 1;
+    int64_t *J = (int64_t *)malloc((size_t)(H * W) * sizeof(int64_t));
+    if (!J)
+        return 2;
+    for (int64_t i = 0; i < H; i++) {
+        int64_t rowsum = 0;
+        for (int64_t j = 0; j < W; j++) {
+            rowsum += img[i * pitch + j];
+            J[i * W + j] = rowsum + (i > 0 ? J[(i - 1) * W + j] : 0);
+        }
+    }
+    int32_t l, r, o, u;
+    oracle_window_params(h, w, &l, &r, &o, &u);
+    for (int64_t i = 0; i < H; i++)
+        for (int64_t j = 0; j < W; j++) {
+            int64_t acc = 0, a0 = i - o; /* rows (a0 + start, a0 + end] */
+            int32_t rs = 0;
+            for (int32_t p = 0; p < n_row; p++) {
+                int32_t cs = 0;
+                for (int32_t q = 0; q < n_col; q++) {
+                    /* rows (i-o+rs, i-o+rs+len], columns (j-l+cs, j-l+cs+len] */
+                    int64_t r0 = a0 + rs, r1 = a0 + rs + row_len[p];
+                    int64_t c0 = j - l + cs, c1 = j - l + cs + col_len[q];
+                    int64_t s = J_at(J, H, W, r1, c1) - J_at(J, H, W, r0, c1) -
+                                J_at(J, H, W, r1, c0) + J_at(J, H, W, r0, c0);
+                    acc += (int64_t)row_wt[p] * col_wt[q] * s;
+                    cs += col_len[q];
+                }
+                rs += row_len[p];
+            }
+            out[i * W + j] = (int32_t)acc;
+        }
+    free(J);
+    return 0;
+}

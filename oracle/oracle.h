@@ -105,4 +105,12 @@ void oracle_window_minmax_at(const uint8_t *img, int64_t H, int64_t W,
                              int64_t pitch, int32_t h, int32_t w,
                              const int64_t *ii, const int64_t *jj, int64_t count,
                              uint8_t *mn, uint8_t *mx);
+int oracle_haar_bruteforce(const uint8_t *img, int64_t H, int64_t W, int64_t pitch,
+                           const int32_t *row_len, const int32_t *row_wt, int32_t n_row,
+                           const int32_t *col_len, const int32_t *col_wt, int32_t n_col,
+                           int32_t *out);
+int oracle_haar_integral(const uint8_t *img, int64_t H, int64_t W, int64_t pitch,
+                         const int32_t *row_len, const int32_t *row_wt, int32_t n_row,
+                         const int32_t *col_len, const int32_t *col_wt, int32_t n_col,
+                         int32_t *out);
 #endif
