@@ -308,6 +308,38 @@ def extra_minmax(bz, imgs, outs, dev, stream, windows=((15, 15), (31, 31), (63, 
     return res
 
 
+def extra_haar(bz, imgs, dev, stream):
+    """Haar-like window sums (int32 map) on the 4096 x 3072 page, graph-timed
+    over the rotating buffers; 5 algorithmic bytes per pixel (1 read, 4
+    written)."""
+    import torch
+    out = torch.empty((H, W), dtype=torch.int32, device=dev)
+    res = {}
+    for name, (h, w) in (("edge_h", (24, 24)), ("line_h", (24, 24)), ("diag", (24, 24)),
+                         ("edge_h", (96, 96))):
+        rows, cols = bz.HAAR_FEATURES[name](h, w)
+        calls = [lambda b=(r * 7 + 3) % N_BUFFERS: bz.haar_feature(imgs[b], rows, cols, out=out,
+                                                                   stream=stream) for r in range(8)]
+        ms = graph_ms(calls, dev, stream)
+        res[f"{name}_{h}x{w}"] = {"ms": round(ms, 4), "gpix_s": round(H * W / (ms * 1e-3) / 1e9, 2)}
+    return res
+
+
+def extra_inplace(bz, imgs, dev, stream, bands=(0, 1024)):
+    """In-place Sauvola 31 x 31 over the 4096 x 3072 page (graph-timed; each
+    call overwrites its buffer's first 512 bytes per row, so later calls see
+    a different image but the same work)."""
+    res = {}
+    for band in bands:
+        calls = [lambda b=(r * 7 + 3) % N_BUFFERS: bz.binarize_inplace(0, imgs[b], 31, 31, band_rows=band,
+                                                                       stream=stream) for r in range(8)]
+        ms = graph_ms(calls, dev, stream)
+        res[f"band_{band or 'default'}"] = {
+            "ms": round(ms, 4), "gpix_s": round(H * W / (ms * 1e-3) / 1e9, 2),
+            "scratch_bytes": bz.inplace_scratch_bytes(H, W, 31, band)}
+    return res
+
+
 def extra_serve(bz, synth, dev, pages, n_req=1500, seed=5):
     """Served path: requests over pre-staged device images (crops of the batch
     pages, area log-uniform 0.1-8.7 Mpix, aspect 1:sqrt(2) portrait or
@@ -510,9 +542,14 @@ def main():
     if rank == 0:
         extras["table1_4096x3072_fp64"] = extra_table1(bz, imgs, outs, dev, stream)
         extras["bernsen_4096x3072"] = extra_minmax(bz, imgs, outs, dev, stream)
+        extras["haar_4096x3072"] = extra_haar(bz, imgs, dev, stream)
         extras["quantile_2048x2048"] = extra_quantile(bz, synth, dev, stream)
         extras["batch_256"] = extra_batch(bz, synth, dev, stream)
         extras["serve"] = extra_serve(bz, synth, dev, extra_batch.pages)
+        extras["inplace_sauvola_31x31"] = extra_inplace(bz, imgs, dev, stream)
+        for t in imgs:  # the in-place row overwrote the pages
+            t.copy_(pinned, non_blocking=True)
+        torch.cuda.synchronize(dev)
 
     # end to end through the C ABI with host buffers
     e2e_steps = max(2, min(args.steps, 10))

@@ -142,6 +142,30 @@ bz_status binarize_precision_report(int32_t method, const uint8_t *image,
 int64_t bz_last_fp64_fallbacks(void *stream);
 
 /* ---------------------------------------------------------------------- */
+/* In-place binarization (Sec. 3.2 assumptions: the algorithm can be made */
+/* in-place by keeping the gray levels that later windows still need).    */
+/* ---------------------------------------------------------------------- */
+
+/* Sauvola (method 0) or Niblack (method 1) written over the image itself:
+ * on return row i of `image` starts with its ceil(W/8) packed output bytes
+ * (same bit layout as binarize_sauvola); the bytes after them keep their
+ * gray levels.  The image is processed in bands of band_rows rows (0 picks
+ * max(o, 256)); band k goes to a library scratch of two bands
+ * (2 * band_rows * ceil(W/8) bytes, stream-ordered cudaMallocAsync) and is
+ * copied into place after band k+1 has read its rows, which needs
+ * band_rows >= o = floor((h+1)/2) (else BZ_EINVAL).  Results equal
+ * binarize_sauvola / binarize_niblack with a separate output.  Smaller
+ * bands use less memory and run more, smaller launches. */
+bz_status binarize_inplace(int32_t method, uint8_t *image, int64_t H, int64_t W,
+                           int64_t pitch, int32_t h, int32_t w, double k,
+                           double R, int64_t band_rows, bz_precision precision,
+                           void *stream);
+
+/* Scratch bytes binarize_inplace takes for these sizes (-1 if invalid), for
+ * admission under a memory budget. */
+int64_t bz_inplace_scratch_bytes(int64_t H, int64_t W, int32_t h, int64_t band_rows);
+
+/* ---------------------------------------------------------------------- */
 /* Local minimum and maximum (Sec. 3.4: Bernsen's midrange and the local  */
 /* contrast, kept recursively).  The window is Algorithm 1's, clipped to  */
 /* the image; pixels outside the image take no part (they are neither a   */
@@ -163,6 +187,31 @@ bz_status binarize_bernsen(const uint8_t *image, int64_t H, int64_t W,
                            int64_t in_pitch, int32_t h, int32_t w,
                            int32_t contrast_limit, uint8_t *out,
                            int64_t out_pitch, void *stream);
+
+/* ---------------------------------------------------------------------- */
+/* Haar-like window sums (Sec. 3.4: the recursive sums replace integral   */
+/* images for Haar-like features).  For every pixel (i, j) the sum over   */
+/* Algorithm 1's h x w window of f(a) g(b) I(i-o+1+a, j-l+1+b), where the  */
+/* window's rows are cut into n_row segments (row_len[s] rows of weight    */
+/* row_wt[s], top to bottom) and its columns into n_col segments (left to  */
+/* right); h = sum row_len, w = sum col_len.  Pixels outside the image are */
+/* 0.  Viola and Jones's features: two segments of weights +1/-1 in one    */
+/* direction (edge), three of -1/+2/-1 (line), two by two (diagonal).      */
+/* The cost per pixel depends on the number of segments, not on h or w.    */
+/* ---------------------------------------------------------------------- */
+typedef struct {
+    int32_t n_row, n_col;          /* 1..4 each                            */
+    int32_t row_len[4], row_wt[4]; /* lengths >= 1, weights in [-127, 127] */
+    int32_t col_len[4], col_wt[4];
+} bz_haar;
+
+/* out: dense H x W int32 device array (caller-owned, not overlapping the
+ * image).  Limits: 1 <= h, w <= 511 and 255 h w max|row_wt| max|col_wt|
+ * < 2^31 (so the result is exact); otherwise BZ_EINVAL.  `feature` is a
+ * host pointer, read during the call. */
+bz_status haar_feature(const uint8_t *image, int64_t H, int64_t W,
+                       int64_t in_pitch, const bz_haar *feature, int32_t *out,
+                       void *stream);
 
 /* ---------------------------------------------------------------------- */
 /* The other Table 1 methods (Sec. 3.4: one changed condition on the same */

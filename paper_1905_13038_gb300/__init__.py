@@ -25,7 +25,8 @@ __all__ = [
     "Server", "status_string",
     "WOLF", "FENG", "RAIS", "NICK", "PHANSALKAR", "binarize_wolf", "binarize_feng", "binarize_rais",
     "binarize_nick", "binarize_phansalkar", "global_stats", "binarize_precision_report_ext",
-    "window_minmax", "binarize_bernsen",
+    "window_minmax", "binarize_bernsen", "haar_feature", "HAAR_FEATURES", "binarize_inplace",
+    "inplace_scratch_bytes",
 ]
 
 FP64, FP32, FP64_DIRECT = 0, 1, 2
@@ -63,6 +64,12 @@ class _JobC(ctypes.Structure):
                 ("q_den", ctypes.c_int32), ("offset", ctypes.c_int32)]
 
 
+class _HaarC(ctypes.Structure):
+    _fields_ = [("n_row", ctypes.c_int32), ("n_col", ctypes.c_int32),
+                ("row_len", ctypes.c_int32 * 4), ("row_wt", ctypes.c_int32 * 4),
+                ("col_len", ctypes.c_int32 * 4), ("col_wt", ctypes.c_int32 * 4)]
+
+
 def _load():
     global _lib
     if _lib is not None:
@@ -90,6 +97,9 @@ def _load():
         "global_stats": ([P, i64, i64, i64, P, P, P], st),
         "window_minmax": ([P, i64, i64, i64, i32, i32, P, P, P], st),
         "binarize_bernsen": ([P, i64, i64, i64, i32, i32, i32, P, i64, P], st),
+        "haar_feature": ([P, i64, i64, i64, ctypes.POINTER(_HaarC), P, P], st),
+        "binarize_inplace": ([i32, P, i64, i64, i64, i32, i32, f64, f64, i64, st, P], st),
+        "bz_inplace_scratch_bytes": ([i64, i64, i32, i64], i64),
         "binarize_precision_report_ext": ([i32, P, i64, i64, i64, i32, i32, P, P, P, P], st),
         "binarize_batch": ([ctypes.POINTER(_JobC), i32, st, P], st),
         "binarize_batch_noalloc": ([ctypes.POINTER(_JobC), i32, st, P], st),
@@ -307,6 +317,51 @@ def binarize_bernsen(image, h: int, w: int, contrast_limit: int = 15, out=None, 
     _check("binarize_bernsen", _load().binarize_bernsen(ptr, H, W, pitch, h, w, contrast_limit,
                                                         out.data_ptr(), op, _stream(stream)))
     return out
+
+
+# Viola and Jones's feature shapes as (row segments, column segments) of an
+# h x w window: two rectangles (edge), three (line), four (diagonal).
+HAAR_FEATURES = {
+    "edge_h": lambda h, w: ([(h, 1)], [(w // 2, 1), (w - w // 2, -1)]),
+    "edge_v": lambda h, w: ([(h // 2, 1), (h - h // 2, -1)], [(w, 1)]),
+    "line_h": lambda h, w: ([(h, 1)], [(w // 3, -1), (w - 2 * (w // 3), 2), (w // 3, -1)]),
+    "line_v": lambda h, w: ([(h // 3, -1), (h - 2 * (h // 3), 2), (h // 3, -1)], [(w, 1)]),
+    "diag": lambda h, w: ([(h // 2, 1), (h - h // 2, -1)], [(w // 2, 1), (w - w // 2, -1)]),
+}
+
+
+def haar_feature(image, rows, cols, out=None, W: int | None = None, stream=None):
+    """int32 CUDA tensor (H, W): sum over the window of f(a) g(b) I, rows / cols
+    = lists of (length, weight) segments (see HAAR_FEATURES for presets)."""
+    import torch
+    ptr, H, W, pitch = _image(image, W)
+    if out is None:
+        out = torch.empty((H, W), dtype=torch.int32, device=image.device)
+    spec = _HaarC()
+    spec.n_row, spec.n_col = len(rows), len(cols)
+    if not (1 <= len(rows) <= 4 and 1 <= len(cols) <= 4):
+        raise ValueError("1 to 4 segments per direction")
+    for k, (n, wt) in enumerate(rows):
+        spec.row_len[k], spec.row_wt[k] = n, wt
+    for k, (n, wt) in enumerate(cols):
+        spec.col_len[k], spec.col_wt[k] = n, wt
+    _check("haar_feature", _load().haar_feature(ptr, H, W, pitch, ctypes.byref(spec), out.data_ptr(),
+                                                _stream(stream)))
+    return out
+
+
+def binarize_inplace(method: int, image, h: int, w: int, k: float = 0.5, R: float = 128.0,
+                     band_rows: int = 0, precision="fp64", W: int | None = None, stream=None):
+    """Sauvola / Niblack written over `image`: each row then starts with its
+    ceil(W/8) packed output bytes.  Returns the image tensor."""
+    ptr, H, W, pitch = _image(image, W)
+    _check("binarize_inplace", _load().binarize_inplace(method, ptr, H, W, pitch, h, w, k, R, band_rows,
+                                                        _PREC[precision], _stream(stream)))
+    return image
+
+
+def inplace_scratch_bytes(H: int, W: int, h: int, band_rows: int = 0) -> int:
+    return int(_load().bz_inplace_scratch_bytes(H, W, h, band_rows))
 
 
 def last_fp64_fallbacks(stream=None) -> int:

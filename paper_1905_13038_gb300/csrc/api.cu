@@ -1,5 +1,6 @@
 // C ABI entry points: argument validation, overlap checks, dispatch.
 #include <math.h>
+#include <stdlib.h>
 #include <mutex>
 
 #include "bz_internal.h"
@@ -441,6 +442,155 @@ bz_status binarize_bernsen(const uint8_t *image, int64_t H, int64_t W, int64_t i
                          (cudaStream_t)stream) == cudaSuccess
                ? BZ_OK
                : BZ_ECUDA;
+}
+
+bz_status haar_feature(const uint8_t *image, int64_t H, int64_t W, int64_t in_pitch,
+                       const bz_haar *feature, int32_t *out, void *stream)
+{
+    if (!feature || !out)
+        return BZ_EINVAL;
+    const bz_haar &F = *feature;
+    if (F.n_row < 1 || F.n_row > 4 || F.n_col < 1 || F.n_col > 4)
+        return BZ_EINVAL;
+    int32_t h = 0, w = 0, fmax = 0, gmax = 0;
+    for (int s = 0; s < F.n_row; s++) {
+        if (F.row_len[s] < 1 || F.row_len[s] > 511 || F.row_wt[s] < -127 || F.row_wt[s] > 127)
+            return BZ_EINVAL;
+        h += F.row_len[s];
+        fmax = abs(F.row_wt[s]) > fmax ? abs(F.row_wt[s]) : fmax;
+    }
+    for (int s = 0; s < F.n_col; s++) {
+        if (F.col_len[s] < 1 || F.col_len[s] > 511 || F.col_wt[s] < -127 || F.col_wt[s] > 127)
+            return BZ_EINVAL;
+        w += F.col_len[s];
+        gmax = abs(F.col_wt[s]) > gmax ? abs(F.col_wt[s]) : gmax;
+    }
+    bz_status st = check_image(image, H, W, in_pitch, h, w);
+    if (st != BZ_OK)
+        return st;
+    // |feature| <= 255 h w max|f| max|g| must stay below 2^31
+    if (255.0 * h * w * fmax * gmax > 2147483647.0)
+        return BZ_EINVAL;
+    const size_t img_bytes = (size_t)((H - 1) * in_pitch + W);
+    if (ranges_overlap(image, img_bytes, out, (size_t)(H * W) * sizeof(int32_t)))
+        return BZ_EOVERLAP;
+    HaarDev hd{};
+    hd.n_rs = F.n_row;
+    for (int s = 0; s < F.n_row; s++) {
+        hd.rs_len[s] = F.row_len[s];
+        hd.rs_wt[s] = F.row_wt[s];
+    }
+    // taps at the segment boundaries: coefficient f(a-1) - f(a), f = 0 outside
+    int a = 0;
+    for (int s = 0; s <= F.n_row; s++) {
+        const int before = s > 0 ? F.row_wt[s - 1] : 0, after = s < F.n_row ? F.row_wt[s] : 0;
+        if (before != after) {
+            hd.rt_a[hd.n_rt] = a;
+            hd.rt_c[hd.n_rt] = before - after;
+            hd.n_rt++;
+        }
+        if (s < F.n_row)
+            a += F.row_len[s];
+    }
+    int b = 0;
+    for (int s = 0; s <= F.n_col; s++) {
+        const int before = s > 0 ? F.col_wt[s - 1] : 0, after = s < F.n_col ? F.col_wt[s] : 0;
+        if (before != after) {
+            hd.ct_b[hd.n_ct] = b;
+            hd.ct_c[hd.n_ct] = before - after;
+            hd.n_ct++;
+        }
+        if (s < F.n_col)
+            b += F.col_len[s];
+    }
+    Image g{image, H, W, in_pitch};
+    return launch_haar(g, make_window(h, w), hd, out, (cudaStream_t)stream) == cudaSuccess
+               ? BZ_OK
+               : BZ_ECUDA;
+}
+
+bz_status binarize_inplace(int32_t method, uint8_t *image, int64_t H, int64_t W, int64_t pitch,
+                           int32_t h, int32_t w, double k, double R, int64_t band_rows,
+                           bz_precision precision, void *stream)
+{
+    bz_status st = check_image(image, H, W, pitch, h, w);
+    if (st != BZ_OK)
+        return st;
+    if ((method != 0 && method != 1) || !finite_params(method, k, R))
+        return BZ_EINVAL;
+    int mode;
+    switch (precision) {
+    case BZ_FP64: mode = MODE_FP64; break;
+    case BZ_FP32: mode = MODE_FP32; break;
+    case BZ_FP64_DIRECT: mode = MODE_FP64_DIRECT; break;
+    default: return BZ_EINVAL;
+    }
+    const Window win = make_window(h, w);
+    const int64_t B = band_rows == 0 ? (win.o > 256 ? win.o : 256) : band_rows;
+    if (B < win.o)
+        return BZ_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t cw = (W + 7) / 8;
+    Image g{image, H, W, pitch};
+    Thresh T = make_thresh(method, k, method == 0 ? R : 128.0);
+    unsigned long long *fb = nullptr;
+    if (mode == MODE_FP64) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess)
+            return BZ_ECUDA;
+        fb = fallback_counter(dev);
+        if (fb && cudaMemsetAsync(fb, 0, sizeof(unsigned long long), s) != cudaSuccess)
+            return BZ_ECUDA;
+    }
+    const int64_t band = B < H ? B : H;
+    uint8_t *scratch = nullptr;
+    if (cudaMallocAsync((void **)&scratch, (size_t)(2 * band * cw), s) != cudaSuccess)
+        return BZ_ENOMEM;
+    // Band k is binarized into scratch slot k % 2 while the image still holds
+    // every gray level its windows need; band k-1 is copied into place only
+    // after band k has run.  Band k+1 reads rows >= start(k+1) - o + 1, which
+    // lie in band k or later because B >= o, so it never sees an overwritten
+    // row.
+    int64_t prev_row0 = -1, prev_rows = 0;
+    int slot = 0;
+    for (int64_t r0 = 0; r0 < H && st == BZ_OK; r0 += band, slot ^= 1) {
+        const int64_t r1 = r0 + band < H ? r0 + band : H;
+        Outputs o{};
+        o.bits = scratch + (int64_t)slot * band * cw;
+        o.out_pitch = cw;
+        o.out_row0 = r0;
+        o.fallbacks = fb;
+        if (launch_window_rows(mode, g, win, T, o, r0, r1, s) != cudaSuccess)
+            st = BZ_ECUDA;
+        else if (prev_row0 >= 0 &&
+                 cudaMemcpy2DAsync(image + prev_row0 * pitch, (size_t)pitch,
+                                   scratch + (int64_t)(slot ^ 1) * band * cw, (size_t)cw,
+                                   (size_t)cw, (size_t)prev_rows, cudaMemcpyDeviceToDevice,
+                                   s) != cudaSuccess)
+            st = BZ_ECUDA;
+        prev_row0 = r0;
+        prev_rows = r1 - r0;
+    }
+    if (st == BZ_OK &&
+        cudaMemcpy2DAsync(image + prev_row0 * pitch, (size_t)pitch,
+                          scratch + (int64_t)(slot ^ 1) * band * cw, (size_t)cw, (size_t)cw,
+                          (size_t)prev_rows, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        st = BZ_ECUDA;
+    if (cudaFreeAsync(scratch, s) != cudaSuccess)
+        st = BZ_ECUDA;
+    return st;
+}
+
+int64_t bz_inplace_scratch_bytes(int64_t H, int64_t W, int32_t h, int64_t band_rows)
+{
+    if (H < 1 || W < 1 || h < 1 || h > 511)
+        return -1;
+    const int64_t o = (h + 1) / 2;
+    const int64_t B = band_rows == 0 ? (o > 256 ? o : 256) : band_rows;
+    if (B < o)
+        return -1;
+    const int64_t band = B < H ? B : H;
+    return 2 * band * ((W + 7) / 8);
 }
 
 int64_t bz_last_fp64_fallbacks(void *stream)

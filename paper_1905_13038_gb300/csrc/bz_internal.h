@@ -29,6 +29,10 @@ int64_t window_tile_rows(int64_t H, int64_t W, int h, int w);
 // Launches of the window path; mode is a bz::Mode.
 cudaError_t launch_window(int mode, const Image &g, const Window &win, const Thresh &T,
                           const Outputs &o, cudaStream_t stream);
+// The same over the output rows [row0, row1) only (windows still see the
+// whole image).
+cudaError_t launch_window_rows(int mode, const Image &g, const Window &win, const Thresh &T,
+                               const Outputs &o, int64_t row0, int64_t row1, cudaStream_t stream);
 
 // The other Table 1 methods (k_table1.cu).  prm = {k, R, alpha1, k1, k2,
 // gamma, p, q}.
@@ -38,6 +42,17 @@ cudaError_t launch_global_finalize(const GStats *gs, unsigned long long N, doubl
                                    uint64_t *sums, cudaStream_t stream);
 cudaError_t launch_window_ext(int mode, const Image &g, const Window &win, const ThreshExt &T,
                               const Outputs &o, cudaStream_t stream);
+
+// Haar-like window sums (k_haar.cu): the row profile's segments (warm-up)
+// and the row and column taps c_a = f(a-1) - f(a), c'_B = g(B-1) - g(B).
+struct HaarDev {
+    int n_rs, n_rt, n_ct;
+    int rs_len[4], rs_wt[4];
+    int rt_a[5], rt_c[5];
+    int ct_b[5], ct_c[5];
+};
+cudaError_t launch_haar(const Image &g, const Window &win, const HaarDev &hd, int32_t *out,
+                        cudaStream_t stream);
 
 // Window extrema (dense mn, mx planes) or, when bits != null, Bernsen's
 // packed decision (k_minmax.cu).

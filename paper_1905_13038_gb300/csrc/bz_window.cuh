@@ -67,6 +67,7 @@ struct ThreshExt : Thresh {
 struct Outputs {
     uint8_t *bits;        // packed output (binarize modes)
     int64_t out_pitch;
+    int64_t out_row0;     // image row i is output row i - out_row0
     uint32_t *S1;         // MODE_SUMS (each may be null)
     uint64_t *S2;
     uint32_t *n;
@@ -664,7 +665,7 @@ __device__ __forceinline__ void window_rows(const Image &g, const Window &win, c
         if (MODE != MODE_REPORT && j0 < W) {
             if (!INTERIOR && j0 + 8 > W)
                 byte &= (1u << (W - j0)) - 1u;  // padding bits are 0
-            o.bits[i * o.out_pitch + (j0 >> 3)] = (uint8_t)byte;
+            o.bits[(i - o.out_row0) * o.out_pitch + (j0 >> 3)] = (uint8_t)byte;
         }
     }
 
@@ -888,7 +889,7 @@ __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &w
             }
             nfb += __popc(undecided);
         }
-        o.bits[i * o.out_pitch + (j0 >> 3)] = (uint8_t)byte;
+        o.bits[(i - o.out_row0) * o.out_pitch + (j0 >> 3)] = (uint8_t)byte;
     };
 
     auto centre = [&](int64_t i) { return __ldg(reinterpret_cast<const uint2 *>(g.img + i * g.pitch + j0)); };

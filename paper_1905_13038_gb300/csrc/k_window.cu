@@ -13,7 +13,7 @@ constexpr int kWarpsPerBlock = 4;
 template <int MODE, bool VEC, typename S2T>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4)
     k_window(Image g, Window win, Thresh T, Outputs o, int64_t tiles_x, int64_t tiles_total,
-             int64_t tile_h)
+             int64_t tile_h, int64_t row0, int64_t row1)
 {
     __shared__ uint4 slots[kWarpsPerBlock][256];  // 4 KB per warp (pipelined path)
     const int lane = threadIdx.x & 31;
@@ -21,8 +21,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4)
     const int64_t stride = (int64_t)gridDim.x * kWarpsPerBlock;
     for (int64_t t = wid; t < tiles_total; t += stride) {
         const int64_t tx = t % tiles_x, ty = t / tiles_x;
-        const int64_t x0 = tx * kTileCols, y0 = ty * tile_h;
-        const int64_t y1 = y0 + tile_h < g.H ? y0 + tile_h : g.H;
+        const int64_t x0 = tx * kTileCols, y0 = row0 + ty * tile_h;
+        const int64_t y1 = y0 + tile_h < row1 ? y0 + tile_h : row1;
         window_tile<MODE, VEC, S2T, true>(g, win, T, o, x0, y0, y1, lane, slots[threadIdx.x >> 5]);
     }
 }
@@ -86,44 +86,52 @@ int64_t window_tile_rows(int64_t H, int64_t W, int h, int w)
 
 template <int MODE, bool VEC, typename S2T>
 static cudaError_t launch_t(const Image &g, const Window &win, const Thresh &T, const Outputs &o,
-                            cudaStream_t stream)
+                            int64_t row0, int64_t row1, cudaStream_t stream)
 {
-    const int64_t tile_h = window_tile_rows(g.H, g.W, win.h, win.w);
+    const int64_t tile_h = window_tile_rows(row1 - row0, g.W, win.h, win.w);
     const int64_t tiles_x = (g.W + kTileCols - 1) / kTileCols;
-    const int64_t tiles_y = (g.H + tile_h - 1) / tile_h;
+    const int64_t tiles_y = (row1 - row0 + tile_h - 1) / tile_h;
     const int64_t tiles = tiles_x * tiles_y;
     int64_t blocks = (tiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
     if (blocks > 2147483647LL)
         blocks = 2147483647LL;
     k_window<MODE, VEC, S2T><<<(unsigned)blocks, 32 * kWarpsPerBlock, 0, stream>>>(
-        g, win, T, o, tiles_x, tiles, tile_h);
+        g, win, T, o, tiles_x, tiles, tile_h, row0, row1);
     return cudaGetLastError();
 }
 
 template <int MODE>
 static cudaError_t launch_m(const Image &g, const Window &win, const Thresh &T, const Outputs &o,
-                            cudaStream_t stream)
+                            int64_t row0, int64_t row1, cudaStream_t stream)
 {
     const bool vec = ((uintptr_t)g.img % 8 == 0) && (g.pitch % 8 == 0);
     const bool wide = (int64_t)win.h * win.w > 66051;  // S2 may reach 2^32
     if (vec)
-        return wide ? launch_t<MODE, true, unsigned long long>(g, win, T, o, stream)
-                    : launch_t<MODE, true, uint32_t>(g, win, T, o, stream);
-    return wide ? launch_t<MODE, false, unsigned long long>(g, win, T, o, stream)
-                : launch_t<MODE, false, uint32_t>(g, win, T, o, stream);
+        return wide ? launch_t<MODE, true, unsigned long long>(g, win, T, o, row0, row1, stream)
+                    : launch_t<MODE, true, uint32_t>(g, win, T, o, row0, row1, stream);
+    return wide ? launch_t<MODE, false, unsigned long long>(g, win, T, o, row0, row1, stream)
+                : launch_t<MODE, false, uint32_t>(g, win, T, o, row0, row1, stream);
+}
+
+cudaError_t launch_window_rows(int mode, const Image &g, const Window &win, const Thresh &T,
+                               const Outputs &o, int64_t row0, int64_t row1, cudaStream_t stream)
+{
+    if (row0 < 0 || row1 > g.H || row0 >= row1)
+        return cudaErrorInvalidValue;
+    switch (mode) {
+    case MODE_FP64: return launch_m<MODE_FP64>(g, win, T, o, row0, row1, stream);
+    case MODE_FP32: return launch_m<MODE_FP32>(g, win, T, o, row0, row1, stream);
+    case MODE_FP64_DIRECT: return launch_m<MODE_FP64_DIRECT>(g, win, T, o, row0, row1, stream);
+    case MODE_SUMS: return launch_m<MODE_SUMS>(g, win, T, o, row0, row1, stream);
+    case MODE_REPORT: return launch_m<MODE_REPORT>(g, win, T, o, row0, row1, stream);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_window(int mode, const Image &g, const Window &win, const Thresh &T,
                           const Outputs &o, cudaStream_t stream)
 {
-    switch (mode) {
-    case MODE_FP64: return launch_m<MODE_FP64>(g, win, T, o, stream);
-    case MODE_FP32: return launch_m<MODE_FP32>(g, win, T, o, stream);
-    case MODE_FP64_DIRECT: return launch_m<MODE_FP64_DIRECT>(g, win, T, o, stream);
-    case MODE_SUMS: return launch_m<MODE_SUMS>(g, win, T, o, stream);
-    case MODE_REPORT: return launch_m<MODE_REPORT>(g, win, T, o, stream);
-    default: return cudaErrorInvalidValue;
-    }
+    return launch_window_rows(mode, g, win, T, o, 0, g.H, stream);
 }
 
 }  // namespace bz
