@@ -29,6 +29,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -37,6 +39,11 @@ WINDOWS = [(15, 15), (63, 63), (255, 255), (31, 127)]
 K_SAUVOLA, R_SAUVOLA = 0.5, 128.0
 N_BUFFERS = 32
 BYTES_PER_PIXEL = 1.0 + 1.0 / 8.0  # read the image once, write one bit
+# Algorithmic ALU work per pixel (integer and FP32 lane operations): add and
+# subtract at both window edges for S1 and S2 in both directions (8), the
+# exact V = n S2 - S1^2 (4), and the Sauvola threshold and compare (10).
+ALU_OPS_PER_PIXEL = 22
+ALU_LANES_PER_SM = 128  # FP32/INT32 lanes per SM per clock
 
 
 def parse():
@@ -145,6 +152,30 @@ def cpu_baseline(img, budget_s=15.0):
                       f"row-band OpenMP oracle, {dt:.2f} s"}
 
 
+def cpu_oracle_rows(page, rows=384):
+    """The oracle beside the GPU rows that have no CPU baseline of their own:
+    single-threaded oracle routines on the first `rows` rows of the page
+    (a bounded sample, a few seconds in all), in Gpix/s."""
+    import oracle
+    img = np.ascontiguousarray(page[:rows])
+    px = img.shape[0] * img.shape[1]
+    res = {}
+
+    def timed(name, fn):
+        t0 = time.perf_counter()
+        fn()
+        res[name] = round(px / (time.perf_counter() - t0) / 1e9, 4)
+
+    timed("wolf_31x31", lambda: oracle.binarize_ext(oracle.WOLF, img, 31, 31, oracle.params()))
+    timed("phansalkar_31x31", lambda: oracle.binarize_ext(oracle.PHANSALKAR, img, 31, 31,
+                                                          oracle.params(k=0.25, R=127.5)))
+    timed("bernsen_31x31", lambda: oracle.binarize_bernsen(img, 31, 31, 15))
+    timed("haar_edge_h_24x24", lambda: oracle.haar(img, [(24, 1)], [(12, 1), (12, -1)]))
+    timed("quantile_31x31_median", lambda: oracle.binarize_quantile(img, 31, 31, 1, 2, 8, threads=1))
+    return {"unit": "Gpix/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {rows} rows of the {W}x{H} page, one thread", "rows": res}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -198,6 +229,20 @@ def measured_traffic():
         return None
 
 
+def alu_roofline(launch_ms, clocks, dev):
+    """Secondary roofline: algorithmic ALU operations per launch (22 per
+    pixel) per second, against SMs x 128 lanes x the median SM clock seen
+    during the timed region (the kernel is issue-bound, not HBM-bound)."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2070.0
+    peak = sms * ALU_LANES_PER_SM * mhz * 1e6 / 1e12  # Tops/s
+    achieved = ALU_OPS_PER_PIXEL * H * W / (launch_ms * 1e-3) / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+            "frac": achieved / peak, "ops_per_pixel": ALU_OPS_PER_PIXEL,
+            "note": f"{sms} SMs x {ALU_LANES_PER_SM} lanes x {mhz:.0f} MHz (median under load)"}
+
+
 def max_over_ranks(value: float, device) -> float:
     """Maximum of a per-rank float over the process group (identity when not
     distributed).  Replicas share nothing else: no collective touches the
@@ -234,8 +279,14 @@ def extra_quantile(bz, synth, dev, stream):
     for (h, w) in ((31, 31), (101, 101)):
         for (qn, qd) in ((1, 2), (1, 10)):
             ms = time_events(lambda: bz.binarize_quantile(img, h, w, qn, qd, 8, out=out, stream=stream), 3, stream)
-            res[f"{h}x{w}_q{qn}/{qd}"] = {"ms": round(ms, 3), "gpix_s": round(2048 * 2048 / (ms * 1e-3) / 1e9, 2)}
+            res[f"{h}x{w}_q{qn}/{qd}"] = {"ms": round(ms, 3), "gpix_s": round(2048 * 2048 / (ms * 1e-3) / 1e9, 2),
+                                          "hbm_frac": hbm_frac(1.125, 2048 * 2048, ms)}
     return res
+
+
+def hbm_frac(bytes_per_px, px, ms):
+    """Algorithmic bytes per second over the measured HBM peak."""
+    return round(bytes_per_px * px / (ms * 1e-3) / 1e9 / peaks()[0], 4)
 
 
 def graph_ms(calls, dev, stream, replays=3):
@@ -263,6 +314,72 @@ def graph_ms(calls, dev, stream, replays=3):
     return a.elapsed_time(b) / (replays * len(calls))
 
 
+def extra_config2(bz, imgs, outs, dev, stream):
+    """The 4096 x 3072 page with Sauvola (k = 0.5, R = 128) and Niblack
+    (k = -0.2) at every window, BZ_FP64 and BZ_FP32 (graph-timed over the
+    rotating buffers), and the FP32-vs-FP64 flips and largest |t32 - t64| of
+    one launch (binarize_precision_report)."""
+    res = {}
+    for name, method, k in (("sauvola", 0, K_SAUVOLA), ("niblack", 1, -0.2)):
+        for prec in ("fp64", "fp32"):
+            row = {}
+            for (h, w) in WINDOWS:
+                if method == 0:
+                    fn = lambda b, h=h, w=w, prec=prec: bz.binarize_sauvola(
+                        imgs[b], h, w, k, R_SAUVOLA, out=outs[b], precision=prec, stream=stream)
+                else:
+                    fn = lambda b, h=h, w=w, prec=prec: bz.binarize_niblack(
+                        imgs[b], h, w, k, out=outs[b], precision=prec, stream=stream)
+                calls = [lambda b=(r * 7 + 3) % N_BUFFERS, fn=fn: fn(b) for r in range(8)]
+                ms = graph_ms(calls, dev, stream)
+                cell = {"ms": round(ms, 4), "gpix_s": round(H * W / (ms * 1e-3) / 1e9, 2),
+                        "hbm_frac": hbm_frac(BYTES_PER_PIXEL, H * W, ms)}
+                if prec == "fp32":
+                    flips, maxdt = bz.binarize_precision_report(method, imgs[0], h, w, k, R_SAUVOLA,
+                                                                stream=stream)
+                    cell["flips"] = flips
+                    cell["max_abs_dt"] = maxdt
+                row[f"{h}x{w}"] = cell
+            res[f"{name}_{prec}"] = row
+    return res
+
+
+def extra_config1(bz, synth, dev, stream, reps=50):
+    """The 512 x 384 page, Sauvola 31 x 31, BZ_FP64: one launch's device
+    latency (CUDA events, median of reps) and the end-to-end latency of one
+    call with host buffers (pinned H2D, launch, D2H, synchronise; host clock,
+    median)."""
+    import torch
+    page = synth.single_page()
+    ph, pw = page.shape
+    pinned = torch.from_numpy(page).pin_memory()
+    host_out = torch.empty((ph, (pw + 7) // 8), dtype=torch.uint8).pin_memory()
+    d_img = torch.empty((ph, pw), dtype=torch.uint8, device=dev)
+    d_out = torch.empty((ph, (pw + 7) // 8), dtype=torch.uint8, device=dev)
+    d_img.copy_(pinned)
+    dev_us, e2e_us = [], []
+    with torch.cuda.stream(stream):
+        for r in range(reps + 3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            bz.binarize_sauvola(d_img, 31, 31, K_SAUVOLA, R_SAUVOLA, out=d_out, stream=stream)
+            b.record(stream)
+            b.synchronize()
+            if r >= 3:
+                dev_us.append(a.elapsed_time(b) * 1e3)
+        for r in range(reps + 3):
+            t0 = time.perf_counter()
+            d_img.copy_(pinned, non_blocking=True)
+            bz.binarize_sauvola(d_img, 31, 31, K_SAUVOLA, R_SAUVOLA, out=d_out, stream=stream)
+            host_out.copy_(d_out, non_blocking=True)
+            stream.synchronize()
+            if r >= 3:
+                e2e_us.append((time.perf_counter() - t0) * 1e6)
+    return {"workload": f"{pw}x{ph} page, Sauvola 31x31, fp64", "device_latency_us": round(statistics.median(dev_us), 2),
+            "e2e_latency_us": round(statistics.median(e2e_us), 2),
+            "hbm_bound_us": round(BYTES_PER_PIXEL * ph * pw / (peaks()[0] * 1e9) * 1e6, 3)}
+
+
 def extra_table1(bz, imgs, outs, dev, stream, windows=((15, 15), (31, 31), (63, 63))):
     """The other Table 1 methods on the 4096 x 3072 page (BZ_FP64, the same
     rotating buffers, calls captured in a CUDA graph): per call the
@@ -286,6 +403,7 @@ def extra_table1(bz, imgs, outs, dev, stream, windows=((15, 15), (31, 31), (63, 
             with torch.cuda.stream(stream):
                 fn(imgs[0], h, w, outs[0])
             row[f"{h}x{w}"] = {"ms": round(ms, 4), "gpix_s": round(H * W / (ms * 1e-3) / 1e9, 2),
+                               "hbm_frac": hbm_frac(2.125, H * W, ms),
                                "fp64_fallbacks": bz.last_fp64_fallbacks(stream)}
         res[name] = row
     stats = torch.empty(3, dtype=torch.float64, device=dev)
@@ -304,7 +422,8 @@ def extra_minmax(bz, imgs, outs, dev, stream, windows=((15, 15), (31, 31), (63, 
         calls = [lambda b=(r * 7 + 3) % N_BUFFERS, h=h, w=w: bz.binarize_bernsen(
             imgs[b], h, w, 15, out=outs[b], stream=stream) for r in range(8)]
         ms = graph_ms(calls, dev, stream)
-        res[f"{h}x{w}"] = {"ms": round(ms, 4), "gpix_s": round(H * W / (ms * 1e-3) / 1e9, 2)}
+        res[f"{h}x{w}"] = {"ms": round(ms, 4), "gpix_s": round(H * W / (ms * 1e-3) / 1e9, 2),
+                           "hbm_frac": hbm_frac(1.125, H * W, ms)}
     return res
 
 
@@ -321,7 +440,8 @@ def extra_haar(bz, imgs, dev, stream):
         calls = [lambda b=(r * 7 + 3) % N_BUFFERS: bz.haar_feature(imgs[b], rows, cols, out=out,
                                                                    stream=stream) for r in range(8)]
         ms = graph_ms(calls, dev, stream)
-        res[f"{name}_{h}x{w}"] = {"ms": round(ms, 4), "gpix_s": round(H * W / (ms * 1e-3) / 1e9, 2)}
+        res[f"{name}_{h}x{w}"] = {"ms": round(ms, 4), "gpix_s": round(H * W / (ms * 1e-3) / 1e9, 2),
+                                  "hbm_frac": hbm_frac(5.0, H * W, ms)}
     return res
 
 
@@ -340,29 +460,35 @@ def extra_inplace(bz, imgs, dev, stream, bands=(0, 1024)):
     return res
 
 
-def extra_serve(bz, synth, dev, pages, n_req=1500, seed=5):
-    """Served path: requests over pre-staged device images (crops of the batch
-    pages, area log-uniform 0.1-8.7 Mpix, aspect 1:sqrt(2) portrait or
-    landscape, method uniform over Sauvola/Niblack/median, odd window uniform
-    in [15, 255]) arriving as a Poisson process.  The saturation rate is
-    measured first (all requests submitted at once); then the rates 0.5x and
-    0.9x of it.  Latency = submit -> bz_server_wait returns."""
+def extra_serve(bz, synth, dev, n_req=2000, seed=5, rates=(0.1, 0.3, 0.5, 0.7, 0.9, 1.0, 1.2)):
+    """Served path: requests over pre-staged device images (crops of two
+    portrait 3366 x 4760 and two landscape 4760 x 3366 pages, area log-uniform 0.1-16 Mpix, aspect 1:sqrt(2)
+    portrait or landscape, method uniform over Sauvola/Niblack/median, odd
+    window uniform in [15, 255]) arriving as a Poisson process.  The
+    saturation rate is measured first (all requests submitted at once), then
+    Poisson arrivals at the given multiples of it.  Latency = submit ->
+    bz_server_wait returns."""
     import concurrent.futures as cf
     import numpy as np
     import torch
     rng = np.random.default_rng(seed)
-    PH, PW = pages[0].shape
+    portrait = [torch.from_numpy(synth.document(4760, 3366, synth.BASE_SEED + 7 + 1000 * p, stains=3)).to(dev)
+                for p in range(2)]
+    landscape = [torch.from_numpy(synth.document(3366, 4760, synth.BASE_SEED + 9 + 1000 * p, stains=3)).to(dev)
+                 for p in range(2)]
     jobs = []
     px_total = 0
     for q in range(n_req):
-        area = 0.1e6 * (8.7e6 / 0.1e6) ** rng.random()
+        area = 0.1e6 * (16e6 / 0.1e6) ** rng.random()
         if rng.random() < 0.5:
             H = int(round((area * 2 ** 0.5) ** 0.5)); W = int(round(area / H))
         else:
             W = int(round((area * 2 ** 0.5) ** 0.5)); H = int(round(area / W))
+        src = (portrait if H >= W else landscape)[q % 2]
+        PH, PW = src.shape
         H, W = max(1, min(H, PH)), max(1, min(W, PW))
         win = int(rng.integers(7, 128)) * 2 + 1
-        img = pages[q % len(pages)][:H, :W]
+        img = src[:H, :W]
         m = int(rng.integers(0, 3))
         if m == 0:
             jobs.append(bz.Job(img, bz.SAUVOLA, win, win, k=0.5, R=128.0))
@@ -409,7 +535,7 @@ def extra_serve(bz, synth, dev, pages, n_req=1500, seed=5):
     sat = run(0)  # everything at once: saturation throughput
     sat_rate = n_req / (px_total / (sat["gpix_s"] * 1e9))
     res = {"requests": n_req, "mpix_total": round(px_total / 1e6, 1), "saturation": sat}
-    for f in (0.5, 0.9):
+    for f in rates:
         res[f"load_{f}"] = run(f * sat_rate)
     pool.shutdown()
     return res
@@ -435,6 +561,16 @@ def extra_batch(bz, synth, dev, stream, count=256):
             jobs.append(bz.Job(img, bz.NIBLACK, sp["h"], sp["w"], k=-0.2))
         px += sp["H"] * sp["W"]
     ms_batch = time_events(lambda: bz.binarize_batch(jobs, stream=stream), 3, stream)
+    # FP32 batch against the FP64 batch: differing output bits
+    jobs32 = [bz.Job(j.image, j.c.method, j.c.h, j.c.w, k=j.c.k, R=j.c.R) for j in jobs]
+    bz.binarize_batch(jobs32, precision="fp32", stream=stream)
+    ms_batch32 = time_events(lambda: bz.binarize_batch(jobs32, precision="fp32", stream=stream), 3, stream)
+    torch.cuda.synchronize()
+    flips = 0
+    for a, b in zip(jobs, jobs32):
+        wb = (a.c.W + 7) // 8
+        x = torch.bitwise_xor(a.out[:, :wb], b.out[:, :wb])
+        flips += int(sum(int(((x >> s) & 1).sum()) for s in range(8)))
 
     def per_image():
         for j in jobs:
@@ -446,6 +582,8 @@ def extra_batch(bz, synth, dev, stream, count=256):
     extra_batch.pages = pages
     return {"images": count, "mpix": round(px / 1e6, 1),
             "batched_graph": {"ms": round(ms_batch, 3), "gpix_s": round(px / (ms_batch * 1e-3) / 1e9, 2)},
+            "batched_graph_fp32": {"ms": round(ms_batch32, 3), "gpix_s": round(px / (ms_batch32 * 1e-3) / 1e9, 2),
+                                   "flips_vs_fp64": flips},
             "per_image_launches": {"ms": round(ms_single, 3), "gpix_s": round(px / (ms_single * 1e-3) / 1e9, 2)}}
 
 
@@ -540,12 +678,14 @@ def main():
     fb = bz.last_fp64_fallbacks(stream)
     extras = {}
     if rank == 0:
+        extras["config1_512x384"] = extra_config1(bz, synth, dev, stream)
+        extras["config2_4096x3072"] = extra_config2(bz, imgs, outs, dev, stream)
         extras["table1_4096x3072_fp64"] = extra_table1(bz, imgs, outs, dev, stream)
         extras["bernsen_4096x3072"] = extra_minmax(bz, imgs, outs, dev, stream)
         extras["haar_4096x3072"] = extra_haar(bz, imgs, dev, stream)
         extras["quantile_2048x2048"] = extra_quantile(bz, synth, dev, stream)
         extras["batch_256"] = extra_batch(bz, synth, dev, stream)
-        extras["serve"] = extra_serve(bz, synth, dev, extra_batch.pages)
+        extras["serve"] = extra_serve(bz, synth, dev)
         extras["inplace_sauvola_31x31"] = extra_inplace(bz, imgs, dev, stream)
         for t in imgs:  # the in-place row overwrote the pages
             t.copy_(pinned, non_blocking=True)
@@ -580,6 +720,7 @@ def main():
             "roofline": {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm, "unit": "GB/s",
                          "frac": achieved_gbs / hbm, "traffic": measured_traffic(),
                          "note": f"peak {peak_kind}; algorithmic 1.125 B/px x {H * W} px per launch"},
+            "alu_roofline": alu_roofline(launch_ms, clk.summary(), dev),
             "gpu_launches": launches,
             "clocks": clk.summary(),
             "e2e": {"value": e2e_value, "unit": "Gpix/s", "h2d_bytes_per_step": H * W,
@@ -590,6 +731,7 @@ def main():
         }
         if world == 1:
             line["cpu_baseline"] = cpu_baseline(page)
+            line["cpu_oracle_other_rows"] = cpu_oracle_rows(page)
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -9,10 +9,34 @@
 // The two rows are staged in shared memory once per block.  The rank-rho
 // value Q is tracked incrementally: `below` counts window pixels < Q and Q
 // moves up/down until below < rho <= below + hist[Q].
+//
+// A histogram update is a shared-memory read-modify-write whose next update
+// may hit the same bin, so one at a time they form a latency chain.  The
+// updates are therefore applied four at a time: the four counters are read
+// together, each gets the sum of the deltas of every update in the group
+// that names the same bin, and all four are written back (aliased slots
+// read the same old value and write the same new one).
 #pragma once
 #include "bz_window.cuh"
 
 namespace bz {
+
+template <typename CT, int NT>
+__device__ __forceinline__ void hist_add4(CT *hist, int tid, int x0, int x1, int x2, int x3, int d0,
+                                          int d1, int d2, int d3)
+{
+    CT *p0 = hist + x0 * NT + tid, *p1 = hist + x1 * NT + tid;
+    CT *p2 = hist + x2 * NT + tid, *p3 = hist + x3 * NT + tid;
+    const int h0 = *p0, h1 = *p1, h2 = *p2, h3 = *p3;
+    const int s0 = d0 + (x1 == x0 ? d1 : 0) + (x2 == x0 ? d2 : 0) + (x3 == x0 ? d3 : 0);
+    const int s1 = d1 + (x0 == x1 ? d0 : 0) + (x2 == x1 ? d2 : 0) + (x3 == x1 ? d3 : 0);
+    const int s2 = d2 + (x0 == x2 ? d0 : 0) + (x1 == x2 ? d1 : 0) + (x3 == x2 ? d3 : 0);
+    const int s3 = d3 + (x0 == x3 ? d0 : 0) + (x1 == x3 ? d1 : 0) + (x2 == x3 ? d2 : 0);
+    *p0 = (CT)(h0 + s0);
+    *p1 = (CT)(h1 + s1);
+    *p2 = (CT)(h2 + s2);
+    *p3 = (CT)(h3 + s3);
+}
 
 // One block (NT threads) computes output columns [x0, x0+NT) x rows [y0, y1).
 // smem: 256*NT counters of type CT followed by two staging rows.
@@ -59,7 +83,11 @@ __device__ __forceinline__ void quantile_tile(const Image &g, const Window &win,
         __syncthreads();
         stage(rin, a);
         __syncthreads();
-        for (int c = c_lo; c <= c_hi; c++)
+        int c = c_lo;
+        for (; c + 3 <= c_hi; c += 4)
+            hist_add4<CT, NT>(hist, tid, rin[tid + c], rin[tid + c + 1], rin[tid + c + 2],
+                              rin[tid + c + 3], 1, 1, 1, 1);
+        for (; c <= c_hi; c++)
             hist[(int)rin[tid + c] * NT + tid] += 1;
     }
 
@@ -78,19 +106,21 @@ __device__ __forceinline__ void quantile_tile(const Image &g, const Window &win,
             stage(rin, ra);
             stage(rout, rb);
             __syncthreads();
-            if (ra < g.H) {
-                for (int c = c_lo; c <= c_hi; c++) {
-                    const int x = rin[tid + c];
-                    hist[x * NT + tid] += 1;
-                    below += (x < Q);
-                }
+            // entering pixels +1, leaving pixels -1; a row outside the
+            // image is staged as zeros and contributes with delta 0
+            const int din = ra < g.H ? 1 : 0, dout = rb >= 0 ? -1 : 0;
+            int c = c_lo;
+            for (; c + 1 <= c_hi; c += 2) {
+                const int a0 = rin[tid + c], b0 = rout[tid + c];
+                const int a1 = rin[tid + c + 1], b1 = rout[tid + c + 1];
+                hist_add4<CT, NT>(hist, tid, a0, b0, a1, b1, din, dout, din, dout);
+                below += din * ((a0 < Q) + (a1 < Q)) + dout * ((b0 < Q) + (b1 < Q));
             }
-            if (rb >= 0) {
-                for (int c = c_lo; c <= c_hi; c++) {
-                    const int x = rout[tid + c];
-                    hist[x * NT + tid] -= 1;
-                    below -= (x < Q);
-                }
+            if (c <= c_hi) {
+                const int a0 = rin[tid + c], b0 = rout[tid + c];
+                hist[a0 * NT + tid] += din;
+                hist[b0 * NT + tid] += dout;
+                below += din * (a0 < Q) + dout * (b0 < Q);
             }
         }
         const int64_t rows = (i + u < g.H - 1 ? i + u : g.H - 1) - (i - oo > -1 ? i - oo : -1);
