@@ -28,6 +28,7 @@ namespace bz {
 
 constexpr int kColsPerLane = 8;
 constexpr int kTileCols = 32 * kColsPerLane;  // 256
+constexpr int kWarmRows = 8;                   // warm-up rows per batch (WARMB)
 
 enum Mode : int { MODE_FP64 = 0, MODE_FP32 = 1, MODE_FP64_DIRECT = 2, MODE_SUMS = 3, MODE_REPORT = 4 };
 
@@ -360,7 +361,7 @@ __device__ __forceinline__ void ext_row8(const ExtF &F, const ThreshExt &T, cons
 // INTERIOR: every lane's byte streams and outputs lie inside the row, the
 // image and pitch allow aligned 8-byte loads, and every output column has
 // the full window width w (warp-uniform; decided by window_tile).
-template <int MODE, bool VEC, bool INTERIOR, typename S2T, bool EXT = false>
+template <int MODE, bool VEC, bool INTERIOR, typename S2T, bool EXT = false, bool WARMB = false>
 __device__ __forceinline__ void window_rows(const Image &g, const Window &win, const Thresh &T,
                                             const Outputs &o, int64_t x0, int64_t y0, int64_t y1,
                                             int lane)
@@ -447,6 +448,30 @@ __device__ __forceinline__ void window_rows(const Image &g, const Window &win, c
         if (a_hi > H - 1)
             a_hi = H - 1;
         const uint2 Z = make_uint2(0u, 0u);
+        if (WARMB) {
+            // latency-bound launches (few, short tiles): the loads of
+            // kWarmRows rows are issued before any is accumulated
+            for (int64_t a = a_lo; a <= a_hi; a += kWarmRows) {
+                uint2 Ar[kWarmRows], Br[kWarmRows];
+                uint32_t w1r[kWarmRows], w2r[kWarmRows];
+#pragma unroll
+                for (int q = 0; q < kWarmRows; q++) {
+                    Ar[q] = Br[q] = Z;
+                    w1r[q] = w2r[q] = 0u;
+                    if (a + q <= a_hi) {  // warp-uniform
+                        load_row(a + q, Ar[q], Br[q]);
+                        anchor_row(a + q, w1r[q], w2r[q]);
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < kWarmRows; q++) {
+                    warm8(Ar[q], Br[q], E1, E2);
+                    a1p += w1r[q];
+                    a2p += w2r[q];
+                }
+            }
+            a_hi = a_lo - 1;  // done: skip the one-row loop below
+        }
         // one row of look-ahead: the loads of row a+1 are in flight while row
         // a is accumulated
         uint2 A = Z, B = Z;
@@ -700,7 +725,7 @@ __device__ __forceinline__ void window_rows(const Image &g, const Window &win, c
 // scan's latency chain with the threshold arithmetic.  Rows outside the image
 // are handled without branches (safe row pointer + zero mask).
 // smem: 4096 bytes per warp.
-template <int MODE>
+template <int MODE, bool WARMB = false>
 __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &win, const Thresh &T,
                                                  const Outputs &o, int64_t x0, int64_t y0,
                                                  int64_t y1, int lane, uint4 *slots)
@@ -751,6 +776,30 @@ __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &w
         if (a_hi > H - 1)
             a_hi = H - 1;
         const uint2 Z = make_uint2(0u, 0u);
+        if (WARMB) {
+            for (int64_t a = a_lo; a <= a_hi; a += kWarmRows) {
+                uint2 Ar[kWarmRows], Br[kWarmRows];
+                uint32_t w1r[kWarmRows], w2r[kWarmRows];
+#pragma unroll
+                for (int q = 0; q < kWarmRows; q++) {
+                    Ar[q] = Br[q] = Z;
+                    w1r[q] = w2r[q] = 0u;
+                    if (a + q <= a_hi) {  // warp-uniform
+                        const uint8_t *rp = g.img + (a + q) * g.pitch;
+                        Ar[q] = ld8_w3(rp + colA, kA, selA);
+                        Br[q] = ld8_w3(rp + colB, kB, selB);
+                        anchor_row(rp, w1r[q], w2r[q]);
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < kWarmRows; q++) {
+                    warm8(Ar[q], Br[q], E1, E2);
+                    a1p += w1r[q];
+                    a2p += w2r[q];
+                }
+            }
+            a_hi = a_lo - 1;
+        }
         uint2 A = Z, B = Z;
         uint32_t w1 = 0, w2 = 0;
         if (a_lo <= a_hi) {
@@ -921,7 +970,7 @@ __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &w
 // One warp computes the tile of columns [x0, x0+256) x rows [y0, y1).
 // PIPE: the caller provides 4 KB of shared memory per warp (`slots`) for the
 // pipelined interior path.
-template <int MODE, bool VEC, typename S2T, bool PIPE>
+template <int MODE, bool VEC, typename S2T, bool PIPE, bool WARMB = false>
 __device__ __forceinline__ void window_tile(const Image &g, const Window &win, const Thresh &T,
                                             const Outputs &o, int64_t x0, int64_t y0, int64_t y1,
                                             int lane, uint4 *slots)
@@ -933,11 +982,11 @@ __device__ __forceinline__ void window_tile(const Image &g, const Window &win, c
         // the pipelined path loads the anchor window as one word per lane
         const bool one_word = win.w + ((4 - (win.l & 3)) & 3) <= 128;
         if (PIPE && (MODE == MODE_FP64 || MODE == MODE_FP32) && sizeof(S2T) == 4 && one_word)
-            window_rows_pipe<MODE>(g, win, T, o, x0, y0, y1, lane, slots);
+            window_rows_pipe<MODE, WARMB>(g, win, T, o, x0, y0, y1, lane, slots);
         else
-            window_rows<MODE, VEC, true, S2T>(g, win, T, o, x0, y0, y1, lane);
+            window_rows<MODE, VEC, true, S2T, false, WARMB>(g, win, T, o, x0, y0, y1, lane);
     } else {
-        window_rows<MODE, VEC, false, S2T>(g, win, T, o, x0, y0, y1, lane);
+        window_rows<MODE, VEC, false, S2T, false, WARMB>(g, win, T, o, x0, y0, y1, lane);
     }
 }
 

@@ -21,21 +21,29 @@ static cudaError_t launch_q(const Image &g, const Window &win, int32_t q_num, in
                             int32_t offset, uint8_t *out, int64_t out_pitch, uint8_t *Q,
                             cudaStream_t stream)
 {
-    int64_t tile_h = 2 * (int64_t)win.h;
-    if (tile_h < 64)
-        tile_h = 64;
-    const int64_t tiles_x = (g.W + NT - 1) / NT;
-    // keep >= ~2 blocks per SM when the image allows it
-    while (tile_h > 32 && tiles_x * ((g.H + tile_h - 1) / tile_h) < 2 * 152)
-        tile_h /= 2;
-    if (tile_h > g.H)
-        tile_h = g.H;
-    const int64_t tiles_y = (g.H + tile_h - 1) / tile_h;
     const size_t smem = quantile_smem_bytes<NT>(sizeof(CT), win.w);
     cudaError_t e = cudaFuncSetAttribute(k_quantile<CT, NT>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
+    // One wave: as many row bands as the resident-block slots allow for the
+    // column strips (the histograms in shared memory cap residency at a few
+    // blocks per SM, so a second, partial wave would leave most SMs idle).
+    int dev = 0, sms = 152, per_sm = 1;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_quantile<CT, NT>, NT, smem) !=
+            cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    const int64_t tiles_x = (g.W + NT - 1) / NT;
+    int64_t bands = ((int64_t)sms * per_sm) / tiles_x;
+    if (bands < 1)
+        bands = 1;
+    int64_t tile_h = (g.H + bands - 1) / bands;
+    if (tile_h < 1)
+        tile_h = 1;
+    const int64_t tiles_y = (g.H + tile_h - 1) / tile_h;
     k_quantile<CT, NT><<<(unsigned)(tiles_x * tiles_y), NT, smem, stream>>>(
         g, win, q_num, q_den, offset, out, out_pitch, Q, tiles_x, tile_h);
     return cudaGetLastError();

@@ -9,9 +9,10 @@
 namespace bz {
 
 constexpr int kWarpsPerBlock = 4;
+constexpr int kBlocksPerSM = 4;  // 128 registers per thread
 
-template <int MODE, bool VEC, typename S2T>
-__global__ void __launch_bounds__(32 * kWarpsPerBlock, 4)
+template <int MODE, bool VEC, typename S2T, bool WARMB>
+__global__ void __launch_bounds__(32 * kWarpsPerBlock, kBlocksPerSM)
     k_window(Image g, Window win, Thresh T, Outputs o, int64_t tiles_x, int64_t tiles_total,
              int64_t tile_h, int64_t row0, int64_t row1)
 {
@@ -23,7 +24,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, 4)
         const int64_t tx = t % tiles_x, ty = t / tiles_x;
         const int64_t x0 = tx * kTileCols, y0 = row0 + ty * tile_h;
         const int64_t y1 = y0 + tile_h < row1 ? y0 + tile_h : row1;
-        window_tile<MODE, VEC, S2T, true>(g, win, T, o, x0, y0, y1, lane, slots[threadIdx.x >> 5]);
+        window_tile<MODE, VEC, S2T, true, WARMB>(g, win, T, o, x0, y0, y1, lane,
+                                                  slots[threadIdx.x >> 5]);
     }
 }
 
@@ -67,24 +69,35 @@ Thresh make_thresh(int method, double k, double R)
 
 int64_t window_tile_rows(int64_t H, int64_t W, int h, int w)
 {
-    (void)W;
-    (void)w;
     (void)h;
-    // Measured on GB300 (4096 x 3072 page): a warm-up row costs a fraction of
-    // a full row, so short tiles win by giving every SM enough warps; 24 rows
-    // was best or within 5 % of best for windows from 15 x 15 to 255 x 255.
-    // BZ_TILE_ROWS overrides it (tuning).
+    (void)w;
+    // One wave of warp tiles: the shortest tiles for which every tile of the
+    // image is resident at once (SMs x 4 blocks x 4 warps).  Measured on
+    // GB300: on the 4096 x 3072 page this gives 21 rows (8 % faster than 24,
+    // while 20 rows spills into a second wave); on small pages it gives
+    // 1-4 rows, which halves the latency (the launch is latency-bound and
+    // every warp's work shrinks).  BZ_TILE_ROWS overrides it (tuning).
     static const int64_t env = [] {
         const char *e = getenv("BZ_TILE_ROWS");
         return e ? (int64_t)atoll(e) : (int64_t)0;
     }();
-    int64_t th = env > 0 ? env : 24;
-    if (th > H)
-        th = H;
+    if (env > 0)
+        return env < H ? env : H;
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t tiles_x = (W + kTileCols - 1) / kTileCols;
+    const int64_t warps = (int64_t)sms * kBlocksPerSM * kWarpsPerBlock;
+    int64_t bands = warps / tiles_x;
+    if (bands < 1)
+        bands = 1;
+    int64_t th = (H + bands - 1) / bands;
+    if (th < 1)
+        th = 1;
     return th;
 }
 
-template <int MODE, bool VEC, typename S2T>
+template <int MODE, bool VEC, typename S2T, bool WARMB>
 static cudaError_t launch_t(const Image &g, const Window &win, const Thresh &T, const Outputs &o,
                             int64_t row0, int64_t row1, cudaStream_t stream)
 {
@@ -95,7 +108,7 @@ static cudaError_t launch_t(const Image &g, const Window &win, const Thresh &T, 
     int64_t blocks = (tiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
     if (blocks > 2147483647LL)
         blocks = 2147483647LL;
-    k_window<MODE, VEC, S2T><<<(unsigned)blocks, 32 * kWarpsPerBlock, 0, stream>>>(
+    k_window<MODE, VEC, S2T, WARMB><<<(unsigned)blocks, 32 * kWarpsPerBlock, 0, stream>>>(
         g, win, T, o, tiles_x, tiles, tile_h, row0, row1);
     return cudaGetLastError();
 }
@@ -106,11 +119,23 @@ static cudaError_t launch_m(const Image &g, const Window &win, const Thresh &T, 
 {
     const bool vec = ((uintptr_t)g.img % 8 == 0) && (g.pitch % 8 == 0);
     const bool wide = (int64_t)win.h * win.w > 66051;  // S2 may reach 2^32
+    // short tiles (a small image): the launch is latency-bound, so the
+    // warm-up issues its loads in batches (binarize modes only)
+    const bool warmb = (MODE == MODE_FP64 || MODE == MODE_FP32) &&
+                       window_tile_rows(row1 - row0, g.W, win.h, win.w) <= 4;
+    constexpr bool kB = (MODE == MODE_FP64 || MODE == MODE_FP32);
+    if (warmb) {
+        if (vec)
+            return wide ? launch_t<MODE, true, unsigned long long, kB>(g, win, T, o, row0, row1, stream)
+                        : launch_t<MODE, true, uint32_t, kB>(g, win, T, o, row0, row1, stream);
+        return wide ? launch_t<MODE, false, unsigned long long, kB>(g, win, T, o, row0, row1, stream)
+                    : launch_t<MODE, false, uint32_t, kB>(g, win, T, o, row0, row1, stream);
+    }
     if (vec)
-        return wide ? launch_t<MODE, true, unsigned long long>(g, win, T, o, row0, row1, stream)
-                    : launch_t<MODE, true, uint32_t>(g, win, T, o, row0, row1, stream);
-    return wide ? launch_t<MODE, false, unsigned long long>(g, win, T, o, row0, row1, stream)
-                : launch_t<MODE, false, uint32_t>(g, win, T, o, row0, row1, stream);
+        return wide ? launch_t<MODE, true, unsigned long long, false>(g, win, T, o, row0, row1, stream)
+                    : launch_t<MODE, true, uint32_t, false>(g, win, T, o, row0, row1, stream);
+    return wide ? launch_t<MODE, false, unsigned long long, false>(g, win, T, o, row0, row1, stream)
+                : launch_t<MODE, false, uint32_t, false>(g, win, T, o, row0, row1, stream);
 }
 
 cudaError_t launch_window_rows(int mode, const Image &g, const Window &win, const Thresh &T,
