@@ -15,47 +15,67 @@ constexpr int kWarpsPerBlockExt = 4;
 // sum of squares with DP4A and its minimum with byte-wise vmin, then the
 // block reduces and adds to *gs with one atomic per quantity.
 template <bool VEC16>
+__device__ __forceinline__ void gs_chunk(const Image &g, int64_t c, int64_t chunks_per_row,
+                                         uint32_t (&wd)[4], uint32_t &mn)
+{
+    const int64_t i = c / chunks_per_row;
+    const int64_t j = (c - i * chunks_per_row) * 16;
+    const uint8_t *p = g.img + i * g.pitch + j;
+    if (VEC16 && j + 16 <= g.W) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(p));
+        wd[0] = v.x;
+        wd[1] = v.y;
+        wd[2] = v.z;
+        wd[3] = v.w;
+        mn = __vminu4(mn, __vminu4(__vminu4(v.x, v.y), __vminu4(v.z, v.w)));
+        return;
+    }
+    uint32_t lo4[4] = {0u, 0u, 0u, 0u}, hi4[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+    for (int b = 0; b < 16; b++) {
+        const bool in = j + b < g.W;
+        const uint32_t v = in ? (uint32_t)p[b] : 0u;
+        lo4[b >> 2] |= v << (8 * (b & 3));
+        hi4[b >> 2] |= (in ? v : 0xFFu) << (8 * (b & 3));  // 0xFF: neutral for min
+    }
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        wd[q] = lo4[q];
+        mn = __vminu4(mn, hi4[q]);
+    }
+}
+
+// One pass over the image: each thread takes 16-byte chunks of rows
+// (grid-stride over H x ceil(W/16) chunks, four chunks loaded before any is
+// summed), accumulates the chunk's sum and sum of squares with DP4A and its
+// minimum with byte-wise vmin, then the block reduces and adds to *gs with
+// one atomic per quantity.
+template <bool VEC16>
 __global__ void __launch_bounds__(kGsThreads) k_global_stats(Image g, GStats *gs, int64_t chunks_per_row,
                                                               int64_t chunks)
 {
     unsigned long long s1 = 0, s2 = 0;
     uint32_t mn = 0xFFFFFFFFu;  // byte-wise minimum of four lanes of bytes
     const int64_t stride = (int64_t)gridDim.x * kGsThreads;
-    for (int64_t c = (int64_t)blockIdx.x * kGsThreads + threadIdx.x; c < chunks; c += stride) {
-        const int64_t i = c / chunks_per_row;
-        const int64_t j = (c - i * chunks_per_row) * 16;
-        const uint8_t *p = g.img + i * g.pitch + j;
-        uint32_t wd[4];
-        if (VEC16 && j + 16 <= g.W) {
-            const uint4 v = __ldg(reinterpret_cast<const uint4 *>(p));
-            wd[0] = v.x;
-            wd[1] = v.y;
-            wd[2] = v.z;
-            wd[3] = v.w;
-            mn = __vminu4(mn, __vminu4(__vminu4(v.x, v.y), __vminu4(v.z, v.w)));
-        } else {
-            uint32_t lo4[4] = {0u, 0u, 0u, 0u}, hi4[4] = {0u, 0u, 0u, 0u};
+    for (int64_t c = (int64_t)blockIdx.x * kGsThreads + threadIdx.x; c < chunks; c += 4 * stride) {
+        uint32_t wd[4][4];
 #pragma unroll
-            for (int b = 0; b < 16; b++) {
-                const bool in = j + b < g.W;
-                const uint32_t v = in ? (uint32_t)p[b] : 0u;
-                lo4[b >> 2] |= v << (8 * (b & 3));
-                hi4[b >> 2] |= (in ? v : 0xFFu) << (8 * (b & 3));  // 0xFF: neutral for min
-            }
+        for (int k = 0; k < 4; k++) {
+            wd[k][0] = wd[k][1] = wd[k][2] = wd[k][3] = 0u;
+            if (c + k * stride < chunks)
+                gs_chunk<VEC16>(g, c + k * stride, chunks_per_row, wd[k], mn);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            uint32_t a1 = 0, a2 = 0;
 #pragma unroll
             for (int q = 0; q < 4; q++) {
-                wd[q] = lo4[q];
-                mn = __vminu4(mn, hi4[q]);
+                a1 = __dp4a(wd[k][q], 0x01010101u, a1);
+                a2 = __dp4a(wd[k][q], wd[k][q], a2);
             }
+            s1 += a1;
+            s2 += a2;
         }
-        uint32_t a1 = 0, a2 = 0;
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-            a1 = __dp4a(wd[q], 0x01010101u, a1);
-            a2 = __dp4a(wd[q], wd[q], a2);
-        }
-        s1 += a1;
-        s2 += a2;
     }
     // minimum of the four bytes
     mn = __vminu4(mn, mn >> 16);
