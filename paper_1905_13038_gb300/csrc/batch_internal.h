@@ -45,7 +45,9 @@ struct BatchSlot {
     void *h_table = nullptr;
     cudaStream_t cap_stream = nullptr;
     cudaEvent_t done = nullptr;
-    cudaGraphExec_t exec[3] = {nullptr, nullptr, nullptr};
+    // one graph per precision x quantile variant (2 * mode + v; v = 1: the
+    // batch's quantile jobs all fit 16-bit counters)
+    cudaGraphExec_t exec[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
     unsigned long long *fallbacks = nullptr;
     ~BatchSlot();
     void release();
