@@ -419,6 +419,20 @@ __device__ __forceinline__ void window_rows(const Image &g, const Window &win, c
         keep &= 0xFFFFFFFFu << (8 * (int)(ac0 - c4));
     if (c4 + 4 > aend)
         keep = (c4 >= aend) ? 0u : (keep & (0xFFFFFFFFu >> (8 * (int)(c4 + 4 - aend))));
+    // interior anchors wider than 32 words: up to 5 words per lane (w <= 511)
+    // with their masks fixed for the whole tile
+    constexpr int kAW = 5;
+    uint32_t keepk[kAW];
+#pragma unroll
+    for (int k = 0; k < kAW; k++) {
+        const int64_t ck = c4 + 128 * k;
+        uint32_t m = 0xFFFFFFFFu;
+        if (ck < ac0)
+            m &= 0xFFFFFFFFu << (8 * (int)(ac0 - ck));
+        if (ck + 4 > aend)
+            m = (ck >= aend) ? 0u : (m & (0xFFFFFFFFu >> (8 * (int)(ck + 4 - aend))));
+        keepk[k] = m;
+    }
     auto anchor_row = [&](int64_t row, uint32_t &s1, uint32_t &s2) {
         const uint8_t *rp = g.img + row * g.pitch;
         if (one_word) {
@@ -426,6 +440,18 @@ __device__ __forceinline__ void window_rows(const Image &g, const Window &win, c
                 const uint32_t wd = __ldg(reinterpret_cast<const uint32_t *>(rp + c4)) & keep;
                 s1 = __dp4a(wd, 0x01010101u, s1);
                 s2 = __dp4a(wd, wd, s2);
+            }
+        } else if (INTERIOR) {
+            // every word lies inside the row (the tile is interior), so only
+            // the words past the anchor are skipped
+#pragma unroll
+            for (int k = 0; k < kAW; k++) {
+                if (c4 + 128 * k < aend) {
+                    const uint32_t wd =
+                        __ldg(reinterpret_cast<const uint32_t *>(rp + c4 + 128 * k)) & keepk[k];
+                    s1 = __dp4a(wd, 0x01010101u, s1);
+                    s2 = __dp4a(wd, wd, s2);
+                }
             }
         } else {
             anchor_words<VEC>(rp, a4, ac0, aend, W, lane, s1, s2);
