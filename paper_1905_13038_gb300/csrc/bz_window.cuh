@@ -356,6 +356,32 @@ __device__ __forceinline__ void ext_row8(const ExtF &F, const ThreshExt &T, cons
     }
 }
 
+// Warm-up from stripe sums: `st` holds (C, D) = (sum I, sum I^2) of every
+// column over the window rows of this tile's first row (the stripe
+// pre-pass), so E_j = C_{j+r} - C_{j-l} directly and the anchor is the sum of
+// C and D over the anchor columns [ac0, aend).  Columns outside [0, W) are 0.
+__device__ __forceinline__ void warm_from_stripes(const uint2 *st, int64_t W, int64_t colA,
+                                                  int64_t colB, int64_t ac0, int64_t aend, int lane,
+                                                  int32_t *E1, uint32_t *E2, uint32_t &a1p,
+                                                  uint32_t &a2p)
+{
+#pragma unroll
+    for (int m = 0; m < kColsPerLane; m++) {
+        const int64_t xa = colA + m, xb = colB + m;
+        const uint2 ca = (xa >= 0 && xa < W) ? __ldg(st + xa) : make_uint2(0u, 0u);
+        const uint2 cb = (xb >= 0 && xb < W) ? __ldg(st + xb) : make_uint2(0u, 0u);
+        E1[m] = (int32_t)(ca.x - cb.x);
+        E2[m] = ca.y - cb.y;
+    }
+    for (int64_t x = ac0 + lane; x < aend; x += 32) {
+        if (x >= 0 && x < W) {
+            const uint2 c = __ldg(st + x);
+            a1p += c.x;
+            a2p += c.y;
+        }
+    }
+}
+
 // S2T: uint32_t when h*w <= 66051 (S2 < 2^32), else unsigned long long.
 // EXT: the Table 1 thresholds other than Sauvola and Niblack (T.method).
 // INTERIOR: every lane's byte streams and outputs lie inside the row, the
@@ -364,7 +390,7 @@ __device__ __forceinline__ void ext_row8(const ExtF &F, const ThreshExt &T, cons
 template <int MODE, bool VEC, bool INTERIOR, typename S2T, bool EXT = false, bool WARMB = false>
 __device__ __forceinline__ void window_rows(const Image &g, const Window &win, const Thresh &T,
                                             const Outputs &o, int64_t x0, int64_t y0, int64_t y1,
-                                            int lane)
+                                            int lane, const uint2 *stripe = nullptr)
 {
     const int64_t W = g.W, H = g.H;
     const int64_t j0 = x0 + (int64_t)kColsPerLane * lane;
@@ -467,7 +493,9 @@ __device__ __forceinline__ void window_rows(const Image &g, const Window &win, c
         E2[m] = 0;
     }
     uint32_t a1p = 0, a2p = 0;
-    {
+    if (stripe) {
+        warm_from_stripes(stripe, W, colA, colB, ac0, aend, lane, E1, E2, a1p, a2p);
+    } else {
         int64_t a_lo = y0 - oo + 1, a_hi = y0 + u;
         if (a_lo < 0)
             a_lo = 0;
@@ -754,7 +782,8 @@ __device__ __forceinline__ void window_rows(const Image &g, const Window &win, c
 template <int MODE, bool WARMB = false>
 __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &win, const Thresh &T,
                                                  const Outputs &o, int64_t x0, int64_t y0,
-                                                 int64_t y1, int lane, uint4 *slots)
+                                                 int64_t y1, int lane, uint4 *slots,
+                                                 const uint2 *stripe = nullptr)
 {
     typedef uint32_t S2T;
     const int64_t H = g.H;
@@ -795,7 +824,9 @@ __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &w
         E2[m] = 0;
     }
     uint32_t a1p = 0, a2p = 0;
-    {
+    if (stripe) {
+        warm_from_stripes(stripe, g.W, colA, colB, ac0, aend, lane, E1, E2, a1p, a2p);
+    } else {
         int64_t a_lo = y0 - oo + 1, a_hi = y0 + u;
         if (a_lo < 0)
             a_lo = 0;
@@ -999,7 +1030,7 @@ __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &w
 template <int MODE, bool VEC, typename S2T, bool PIPE, bool WARMB = false>
 __device__ __forceinline__ void window_tile(const Image &g, const Window &win, const Thresh &T,
                                             const Outputs &o, int64_t x0, int64_t y0, int64_t y1,
-                                            int lane, uint4 *slots)
+                                            int lane, uint4 *slots, const uint2 *stripe = nullptr)
 {
     // interior: left edge stream of lane 0 and right edge stream of lane 31
     // inside the row, and the whole tile left of the last column
@@ -1008,11 +1039,11 @@ __device__ __forceinline__ void window_tile(const Image &g, const Window &win, c
         // the pipelined path loads the anchor window as one word per lane
         const bool one_word = win.w + ((4 - (win.l & 3)) & 3) <= 128;
         if (PIPE && (MODE == MODE_FP64 || MODE == MODE_FP32) && sizeof(S2T) == 4 && one_word)
-            window_rows_pipe<MODE, WARMB>(g, win, T, o, x0, y0, y1, lane, slots);
+            window_rows_pipe<MODE, WARMB>(g, win, T, o, x0, y0, y1, lane, slots, stripe);
         else
-            window_rows<MODE, VEC, true, S2T, false, WARMB>(g, win, T, o, x0, y0, y1, lane);
+            window_rows<MODE, VEC, true, S2T, false, WARMB>(g, win, T, o, x0, y0, y1, lane, stripe);
     } else {
-        window_rows<MODE, VEC, false, S2T, false, WARMB>(g, win, T, o, x0, y0, y1, lane);
+        window_rows<MODE, VEC, false, S2T, false, WARMB>(g, win, T, o, x0, y0, y1, lane, stripe);
     }
 }
 

@@ -14,7 +14,7 @@ constexpr int kBlocksPerSM = 4;  // 128 registers per thread
 template <int MODE, bool VEC, typename S2T, bool WARMB>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock, kBlocksPerSM)
     k_window(Image g, Window win, Thresh T, Outputs o, int64_t tiles_x, int64_t tiles_total,
-             int64_t tile_h, int64_t row0, int64_t row1)
+             int64_t tile_h, int64_t row0, int64_t row1, const uint2 *stripes)
 {
     __shared__ uint4 slots[kWarpsPerBlock][256];  // 4 KB per warp (pipelined path)
     const int lane = threadIdx.x & 31;
@@ -25,7 +25,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, kBlocksPerSM)
         const int64_t x0 = tx * kTileCols, y0 = row0 + ty * tile_h;
         const int64_t y1 = y0 + tile_h < row1 ? y0 + tile_h : row1;
         window_tile<MODE, VEC, S2T, true, WARMB>(g, win, T, o, x0, y0, y1, lane,
-                                                  slots[threadIdx.x >> 5]);
+                                                  slots[threadIdx.x >> 5],
+                                                  stripes ? stripes + ty * g.W : nullptr);
     }
 }
 
@@ -65,6 +66,110 @@ Thresh make_thresh(int method, double k, double R)
     T.eps = kEpsF32;
     T.delta64 = (float)(mag * 1.01) + 1e-30f;
     return T;
+}
+
+// Stripe pre-pass.  A tile's warm-up re-reads the h window rows above its
+// first output row, so each image row is warmed ~h / tile_h times; for tall
+// windows that dominates.  This kernel computes, once per column, the column
+// sums C = sum I and D = sum I^2 over the window rows of every tile's first
+// row (the Sec. 3.1 stripe identity, slid down the column), so that a tile
+// starts from them (warm_from_stripes).  One thread owns 4 columns and
+// kStripeGroup consecutive tile starts: it sums the h rows of the first,
+// then slides tile_h rows at a time (one row in, one row out) to the next.
+constexpr int kStripeThreads = 128;
+constexpr int kStripeGroup = 4;
+
+template <bool VEC4>
+__device__ __forceinline__ uint32_t stripe_word(const Image &g, int64_t row, int64_t x)
+{
+    const uint8_t *rp = g.img + row * g.pitch;
+    if (VEC4 && x + 4 <= g.W)
+        return __ldg(reinterpret_cast<const uint32_t *>(rp + x));
+    uint32_t v = 0;
+#pragma unroll
+    for (int b = 0; b < 4; b++)
+        if (x + b < g.W)
+            v |= (uint32_t)rp[x + b] << (8 * b);
+    return v;
+}
+
+__device__ __forceinline__ void stripe_acc(uint32_t (&C)[4], uint32_t (&D)[4], uint32_t wd, int sign)
+{
+#pragma unroll
+    for (int b = 0; b < 4; b++) {
+        const uint32_t v = (wd >> (8 * b)) & 0xFFu;
+        C[b] += (uint32_t)sign * v;
+        D[b] += (uint32_t)sign * v * v;
+    }
+}
+
+template <bool VEC4>
+__global__ void __launch_bounds__(kStripeThreads)
+    k_stripes(Image g, int o, int u, int64_t row0, int64_t tile_h, int64_t S, int64_t words,
+              uint2 *out)
+{
+    const int64_t t = (int64_t)blockIdx.x * kStripeThreads + threadIdx.x;
+    const int64_t q = t % words, s0 = (t / words) * kStripeGroup;
+    if (s0 >= S)
+        return;
+    const int64_t s1 = s0 + kStripeGroup < S ? s0 + kStripeGroup : S;
+    const int64_t x = 4 * q;
+    uint32_t C[4] = {0u, 0u, 0u, 0u}, D[4] = {0u, 0u, 0u, 0u};
+    auto store = [&](int64_t s) {
+#pragma unroll
+        for (int b = 0; b < 4; b++)
+            if (x + b < g.W)
+                out[s * g.W + x + b] = make_uint2(C[b], D[b]);
+    };
+    // window rows (y - o, y + u] of the first tile start y, eight loads at a time
+    const int64_t y = row0 + s0 * tile_h;
+    int64_t a_lo = y - o + 1, a_hi = y + u;
+    if (a_lo < 0)
+        a_lo = 0;
+    if (a_hi > g.H - 1)
+        a_hi = g.H - 1;
+    for (int64_t a = a_lo; a <= a_hi; a += 8) {
+        uint32_t wd[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++)
+            wd[k] = a + k <= a_hi ? stripe_word<VEC4>(g, a + k, x) : 0u;
+#pragma unroll
+        for (int k = 0; k < 8; k++)
+            stripe_acc(C, D, wd[k], 1);
+    }
+    store(s0);
+    // slide to the next tile starts: rows y' + u enter, rows y' - o leave
+    for (int64_t s = s0 + 1; s < s1; s++) {
+        const int64_t ys = row0 + s * tile_h;
+        for (int64_t yy = ys - tile_h + 1; yy <= ys; yy += 4) {
+            uint32_t win_[4], wout[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const int64_t r = yy + k;
+                win_[k] = (r <= ys && r + u < g.H) ? stripe_word<VEC4>(g, r + u, x) : 0u;
+                wout[k] = (r <= ys && r - o >= 0) ? stripe_word<VEC4>(g, r - o, x) : 0u;
+            }
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                stripe_acc(C, D, win_[k], 1);
+                stripe_acc(C, D, wout[k], -1);
+            }
+        }
+        store(s);
+    }
+}
+
+// Windows at least this tall start their tiles from the stripe pre-pass
+// (measured on GB300; BZ_STRIPES=0/1 forces it off/on).
+static bool use_stripes(int h)
+{
+    static const int env = [] {
+        const char *e = getenv("BZ_STRIPES");
+        return e ? atoi(e) : -1;
+    }();
+    if (env >= 0)
+        return env != 0;
+    return h >= 48;
 }
 
 int64_t window_tile_rows(int64_t H, int64_t W, int h, int w)
@@ -108,9 +213,31 @@ static cudaError_t launch_t(const Image &g, const Window &win, const Thresh &T, 
     int64_t blocks = (tiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
     if (blocks > 2147483647LL)
         blocks = 2147483647LL;
+    uint2 *stripes = nullptr;
+    if (use_stripes(win.h) && tiles_y > 1) {
+        const size_t bytes = (size_t)tiles_y * (size_t)g.W * sizeof(uint2);
+        if (cudaMallocAsync((void **)&stripes, bytes, stream) != cudaSuccess) {
+            cudaGetLastError();  // no scratch: the tiles warm up themselves
+            stripes = nullptr;
+        } else {
+            const int64_t words = (g.W + 3) / 4;
+            const int64_t threads = words * ((tiles_y + kStripeGroup - 1) / kStripeGroup);
+            const int64_t sblocks = (threads + kStripeThreads - 1) / kStripeThreads;
+            const bool vec4 = ((uintptr_t)g.img % 4 == 0) && (g.pitch % 4 == 0);
+            if (vec4)
+                k_stripes<true><<<(unsigned)sblocks, kStripeThreads, 0, stream>>>(
+                    g, win.o, win.u, row0, tile_h, tiles_y, words, stripes);
+            else
+                k_stripes<false><<<(unsigned)sblocks, kStripeThreads, 0, stream>>>(
+                    g, win.o, win.u, row0, tile_h, tiles_y, words, stripes);
+        }
+    }
     k_window<MODE, VEC, S2T, WARMB><<<(unsigned)blocks, 32 * kWarpsPerBlock, 0, stream>>>(
-        g, win, T, o, tiles_x, tiles, tile_h, row0, row1);
-    return cudaGetLastError();
+        g, win, T, o, tiles_x, tiles, tile_h, row0, row1, stripes);
+    cudaError_t e = cudaGetLastError();
+    if (stripes && cudaFreeAsync(stripes, stream) != cudaSuccess && e == cudaSuccess)
+        e = cudaGetLastError();
+    return e;
 }
 
 template <int MODE>
