@@ -74,7 +74,9 @@ def peaks():
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+    """nvidia-smi clocks and throttle reasons, sampled every 100 ms while the
+    benchmark graph runs: right before, during and right after the timed
+    replay (which alone lasts only milliseconds)."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -645,13 +647,25 @@ def main():
 
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    def load_until_samples(clk, more, limit_s):
+        # untimed replays of the same graph until the sampler has reported
+        # `more` new samples, so that the clock samples bracket the timed
+        # region under the same load (nvidia-smi needs ~0.1 s to start)
+        n0, t_end = len(clk.lines), time.time() + limit_s
+        with torch.cuda.stream(stream):
+            while len(clk.lines) < n0 + more and time.time() < t_end:
+                graph.replay()
+                stream.synchronize()
+
     with ClockSampler(local if world > 1 else 0) as clk:
+        load_until_samples(clk, 2, 3.0)
         barrier()
         with torch.cuda.stream(stream):
             e0.record(stream)
             graph.replay()  # replays on the current stream: `stream`
             e1.record(stream)
         barrier()
+        load_until_samples(clk, 1, 1.0)
     ms = max_over_ranks(e0.elapsed_time(e1), dev)
     px_step = len(WINDOWS) * H * W
     value = world * px_step * args.steps / (ms * 1e-3) / 1e9

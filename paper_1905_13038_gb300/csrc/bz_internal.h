@@ -26,6 +26,13 @@ Thresh make_thresh(int method, double k, double R);
 // Rows of a warp tile for the window path (autotuned heuristics).
 int64_t window_tile_rows(int64_t H, int64_t W, int h, int w);
 
+// Stripe pre-pass on `stream` for windows of 48 rows or more: (C, D) column
+// sums at every tile start row0 + s * tile_h, s < tiles_y, in a stream-ordered
+// scratch of tiles_y * W uint2 that the caller frees on the stream after the
+// window kernel; nullptr when not used or not available.
+uint2 *launch_stripes(const Image &g, const Window &win, int64_t row0, int64_t tile_h,
+                      int64_t tiles_y, cudaStream_t stream);
+
 // Launches of the window path; mode is a bz::Mode.
 cudaError_t launch_window(int mode, const Image &g, const Window &win, const Thresh &T,
                           const Outputs &o, cudaStream_t stream);

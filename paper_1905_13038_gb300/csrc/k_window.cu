@@ -74,10 +74,10 @@ Thresh make_thresh(int method, double k, double R)
 // sums C = sum I and D = sum I^2 over the window rows of every tile's first
 // row (the Sec. 3.1 stripe identity, slid down the column), so that a tile
 // starts from them (warm_from_stripes).  One thread owns 4 columns and
-// kStripeGroup consecutive tile starts: it sums the h rows of the first,
+// `group` consecutive tile starts: it sums the h rows of the first,
 // then slides tile_h rows at a time (one row in, one row out) to the next.
 constexpr int kStripeThreads = 128;
-constexpr int kStripeGroup = 4;
+constexpr int kStripeBatch = 16;  // rows whose loads are issued together
 
 template <bool VEC4>
 __device__ __forceinline__ uint32_t stripe_word(const Image &g, int64_t row, int64_t x)
@@ -106,13 +106,13 @@ __device__ __forceinline__ void stripe_acc(uint32_t (&C)[4], uint32_t (&D)[4], u
 template <bool VEC4>
 __global__ void __launch_bounds__(kStripeThreads)
     k_stripes(Image g, int o, int u, int64_t row0, int64_t tile_h, int64_t S, int64_t words,
-              uint2 *out)
+              int group, uint2 *out)
 {
     const int64_t t = (int64_t)blockIdx.x * kStripeThreads + threadIdx.x;
-    const int64_t q = t % words, s0 = (t / words) * kStripeGroup;
+    const int64_t q = t % words, s0 = (t / words) * group;
     if (s0 >= S)
         return;
-    const int64_t s1 = s0 + kStripeGroup < S ? s0 + kStripeGroup : S;
+    const int64_t s1 = s0 + group < S ? s0 + group : S;
     const int64_t x = 4 * q;
     uint32_t C[4] = {0u, 0u, 0u, 0u}, D[4] = {0u, 0u, 0u, 0u};
     auto store = [&](int64_t s) {
@@ -128,35 +128,46 @@ __global__ void __launch_bounds__(kStripeThreads)
         a_lo = 0;
     if (a_hi > g.H - 1)
         a_hi = g.H - 1;
-    for (int64_t a = a_lo; a <= a_hi; a += 8) {
-        uint32_t wd[8];
+    for (int64_t a = a_lo; a <= a_hi; a += kStripeBatch) {
+        uint32_t wd[kStripeBatch];
 #pragma unroll
-        for (int k = 0; k < 8; k++)
+        for (int k = 0; k < kStripeBatch; k++)
             wd[k] = a + k <= a_hi ? stripe_word<VEC4>(g, a + k, x) : 0u;
 #pragma unroll
-        for (int k = 0; k < 8; k++)
+        for (int k = 0; k < kStripeBatch; k++)
             stripe_acc(C, D, wd[k], 1);
     }
     store(s0);
     // slide to the next tile starts: rows y' + u enter, rows y' - o leave
     for (int64_t s = s0 + 1; s < s1; s++) {
         const int64_t ys = row0 + s * tile_h;
-        for (int64_t yy = ys - tile_h + 1; yy <= ys; yy += 4) {
-            uint32_t win_[4], wout[4];
+        for (int64_t yy = ys - tile_h + 1; yy <= ys; yy += kStripeBatch / 2) {
+            uint32_t win_[kStripeBatch / 2], wout[kStripeBatch / 2];
 #pragma unroll
-            for (int k = 0; k < 4; k++) {
+            for (int k = 0; k < kStripeBatch / 2; k++) {
                 const int64_t r = yy + k;
                 win_[k] = (r <= ys && r + u < g.H) ? stripe_word<VEC4>(g, r + u, x) : 0u;
                 wout[k] = (r <= ys && r - o >= 0) ? stripe_word<VEC4>(g, r - o, x) : 0u;
             }
 #pragma unroll
-            for (int k = 0; k < 4; k++) {
+            for (int k = 0; k < kStripeBatch / 2; k++) {
                 stripe_acc(C, D, win_[k], 1);
                 stripe_acc(C, D, wout[k], -1);
             }
         }
         store(s);
     }
+}
+
+// Tile starts per pre-pass thread: fewer means more threads (latency
+// hiding) but more repeated h-row sums (BZ_STRIPE_GROUP overrides: tuning).
+static int stripe_group()
+{
+    static const int env = [] {
+        const char *e = getenv("BZ_STRIPE_GROUP");
+        return e ? atoi(e) : 0;
+    }();
+    return env > 0 ? env : 2;
 }
 
 // Windows at least this tall start their tiles from the stripe pre-pass
@@ -170,6 +181,35 @@ static bool use_stripes(int h)
     if (env >= 0)
         return env != 0;
     return h >= 48;
+}
+
+uint2 *launch_stripes(const Image &g, const Window &win, int64_t row0, int64_t tile_h,
+                      int64_t tiles_y, cudaStream_t stream)
+{
+    if (!use_stripes(win.h) || tiles_y <= 1)
+        return nullptr;
+    uint2 *stripes = nullptr;
+    const size_t bytes = (size_t)tiles_y * (size_t)g.W * sizeof(uint2);
+    if (cudaMallocAsync((void **)&stripes, bytes, stream) != cudaSuccess) {
+        cudaGetLastError();  // no scratch: the tiles warm up themselves
+        return nullptr;
+    }
+    const int64_t words = (g.W + 3) / 4;
+    const int group = stripe_group();
+    const int64_t threads = words * ((tiles_y + group - 1) / group);
+    const int64_t sblocks = (threads + kStripeThreads - 1) / kStripeThreads;
+    const bool vec4 = ((uintptr_t)g.img % 4 == 0) && (g.pitch % 4 == 0);
+    if (vec4)
+        k_stripes<true><<<(unsigned)sblocks, kStripeThreads, 0, stream>>>(
+            g, win.o, win.u, row0, tile_h, tiles_y, words, group, stripes);
+    else
+        k_stripes<false><<<(unsigned)sblocks, kStripeThreads, 0, stream>>>(
+            g, win.o, win.u, row0, tile_h, tiles_y, words, group, stripes);
+    if (cudaGetLastError() != cudaSuccess) {
+        cudaFreeAsync(stripes, stream);
+        return nullptr;
+    }
+    return stripes;
 }
 
 int64_t window_tile_rows(int64_t H, int64_t W, int h, int w)
@@ -213,25 +253,7 @@ static cudaError_t launch_t(const Image &g, const Window &win, const Thresh &T, 
     int64_t blocks = (tiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
     if (blocks > 2147483647LL)
         blocks = 2147483647LL;
-    uint2 *stripes = nullptr;
-    if (use_stripes(win.h) && tiles_y > 1) {
-        const size_t bytes = (size_t)tiles_y * (size_t)g.W * sizeof(uint2);
-        if (cudaMallocAsync((void **)&stripes, bytes, stream) != cudaSuccess) {
-            cudaGetLastError();  // no scratch: the tiles warm up themselves
-            stripes = nullptr;
-        } else {
-            const int64_t words = (g.W + 3) / 4;
-            const int64_t threads = words * ((tiles_y + kStripeGroup - 1) / kStripeGroup);
-            const int64_t sblocks = (threads + kStripeThreads - 1) / kStripeThreads;
-            const bool vec4 = ((uintptr_t)g.img % 4 == 0) && (g.pitch % 4 == 0);
-            if (vec4)
-                k_stripes<true><<<(unsigned)sblocks, kStripeThreads, 0, stream>>>(
-                    g, win.o, win.u, row0, tile_h, tiles_y, words, stripes);
-            else
-                k_stripes<false><<<(unsigned)sblocks, kStripeThreads, 0, stream>>>(
-                    g, win.o, win.u, row0, tile_h, tiles_y, words, stripes);
-        }
-    }
+    uint2 *stripes = launch_stripes(g, win, row0, tile_h, tiles_y, stream);
     k_window<MODE, VEC, S2T, WARMB><<<(unsigned)blocks, 32 * kWarpsPerBlock, 0, stream>>>(
         g, win, T, o, tiles_x, tiles, tile_h, row0, row1, stripes);
     cudaError_t e = cudaGetLastError();
