@@ -210,9 +210,11 @@ def binarize_precision_report(method: int, image, h: int, w: int, k: float, R: f
     ptr, H, W, pitch = _image(image, W)
     flips = torch.zeros(1, dtype=torch.int64, device=image.device)
     maxdt = torch.zeros(1, dtype=torch.float64, device=image.device)
+    torch.cuda.synchronize(image.device)  # the zeros are in place before `stream` runs
     _check("binarize_precision_report",
            _load().binarize_precision_report(method, ptr, H, W, pitch, h, w, k, R, flips.data_ptr(),
                                              maxdt.data_ptr(), _stream(stream)))
+    torch.cuda.synchronize(image.device)  # ... and the report is complete before reading
     return int(flips.item()), float(maxdt.item())
 
 
@@ -291,9 +293,11 @@ def binarize_precision_report_ext(method: int, image, h: int, w: int, params, W:
     prm = (ctypes.c_double * 8)(*[float(x) for x in params])
     flips = torch.zeros(1, dtype=torch.int64, device=image.device)
     maxdt = torch.zeros(1, dtype=torch.float64, device=image.device)
+    torch.cuda.synchronize(image.device)
     _check("binarize_precision_report_ext",
            _load().binarize_precision_report_ext(method, ptr, H, W, pitch, h, w, prm, flips.data_ptr(),
                                                  maxdt.data_ptr(), _stream(stream)))
+    torch.cuda.synchronize(image.device)
     return int(flips.item()), float(maxdt.item())
 
 

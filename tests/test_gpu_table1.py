@@ -172,7 +172,7 @@ def test_precision_report_ext_counts_fp32_flips(method):
     a = unpack(o32.cpu().numpy(), 1000)
     b = unpack(o64.cpu().numpy(), 1000)
     assert flips == int((a != b).sum())
-    assert 0.0 <= maxdt <= 2e-3
+    assert 0.0 < maxdt <= 2e-3
 
 
 def test_table1_rejects_bad_parameters():
