@@ -709,21 +709,53 @@ def main():
             t.copy_(pinned, non_blocking=True)
         torch.cuda.synchronize(dev)
 
-    # end to end through the C ABI with host buffers
+    # end to end through the C ABI with host buffers: every step copies the
+    # page from pinned host memory and the four outputs back.  Uploads and
+    # downloads run on their own streams, double-buffered, so that step s+1's
+    # upload and step s-1's downloads overlap step s's binarizations (a
+    # streaming pipeline; an upload never queues behind a download).
     e2e_steps = max(2, min(args.steps, 10))
-    host_out = torch.empty((len(WINDOWS), H, (W + 7) // 8), dtype=torch.uint8).pin_memory()
-    dimg = imgs[0]
+    host_out = [torch.empty((len(WINDOWS), H, (W + 7) // 8), dtype=torch.uint8).pin_memory()
+                for _ in range(2)]
+    d_img = [imgs[0], imgs[1]]
+    d_out = [[outs[2 + 4 * b + wi] for wi in range(len(WINDOWS))] for b in range(2)]
+    up_s = torch.cuda.Stream(device=dev)
+    down_s = torch.cuda.Stream(device=dev)
+    up = [torch.cuda.Event() for _ in range(2)]      # upload of buffer b done
+    done = [torch.cuda.Event() for _ in range(2)]    # binarizations of buffer b done
+    down = [torch.cuda.Event() for _ in range(2)]    # downloads of buffer b done
     e2 = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
     barrier()
-    with torch.cuda.stream(stream):
-        e2[0].record(stream)
-        for s in range(e2e_steps):
-            dimg.copy_(pinned, non_blocking=True)
+    e2[0].record(up_s)
+    down_s.wait_event(e2[0])
+
+    def upload(s_):
+        b = s_ % 2
+        with torch.cuda.stream(up_s):
+            if s_ >= 2:
+                up_s.wait_event(done[b])  # the image buffer is free again
+            d_img[b].copy_(pinned, non_blocking=True)
+            up[b].record(up_s)
+
+    upload(0)
+    for s_ in range(e2e_steps):
+        b = s_ % 2
+        if s_ + 1 < e2e_steps:
+            upload(s_ + 1)
+        with torch.cuda.stream(stream):
+            stream.wait_event(up[b])
+            if s_ >= 2:
+                stream.wait_event(down[b])  # the outputs of step s-2 are home
             for wi, (h, w) in enumerate(WINDOWS):
-                bz.binarize_sauvola(dimg, h, w, K_SAUVOLA, R_SAUVOLA, out=outs[wi], precision=prec,
-                                    stream=stream)
-                host_out[wi].copy_(outs[wi], non_blocking=True)
-        e2[1].record(stream)
+                bz.binarize_sauvola(d_img[b], h, w, K_SAUVOLA, R_SAUVOLA, out=d_out[b][wi],
+                                    precision=prec, stream=stream)
+            done[b].record(stream)
+        with torch.cuda.stream(down_s):
+            down_s.wait_event(done[b])
+            for wi in range(len(WINDOWS)):
+                host_out[b][wi].copy_(d_out[b][wi], non_blocking=True)
+            down[b].record(down_s)
+    e2[1].record(down_s)
     barrier()
     e2e_ms = max_over_ranks(e2[0].elapsed_time(e2[1]), dev)
     e2e_value = world * px_step * e2e_steps / (e2e_ms * 1e-3) / 1e9

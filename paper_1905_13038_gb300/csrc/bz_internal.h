@@ -26,6 +26,12 @@ Thresh make_thresh(int method, double k, double R);
 // Rows of a warp tile for the window path (autotuned heuristics).
 int64_t window_tile_rows(int64_t H, int64_t W, int h, int w);
 
+// Small pages, windows up to 63 x 63 (k_small.cu): shared-memory tiles
+// instead of latency-bound warp tiles.
+bool small_path_applies(int mode, const Image &g, const Window &win, int64_t row0, int64_t row1);
+cudaError_t launch_small(int mode, const Image &g, const Window &win, const Thresh &T,
+                         const Outputs &o, int64_t row0, int64_t row1, cudaStream_t stream);
+
 // Stripe pre-pass on `stream` for windows of 48 rows or more: (C, D) column
 // sums at every tile start row0 + s * tile_h, s < tiles_y, in a stream-ordered
 // scratch of tiles_y * W uint2 that the caller frees on the stream after the

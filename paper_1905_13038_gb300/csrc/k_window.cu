@@ -159,6 +159,75 @@ __global__ void __launch_bounds__(kStripeThreads)
     }
 }
 
+// Chunked form of the same pre-pass.  With p_k = row0 - o + 1 + k tile_h, the
+// window rows of tile start s are [p_s, p_s + h) = chunks s .. s+m-1 plus the
+// first h - m tile_h rows of chunk s+m (m = floor(h / tile_h)).  Phase 1 sums
+// every chunk (Q_k) and its first h - m tile_h rows (R_k) in parallel, each
+// image row read once per column; phase 2 slides a window of m chunk sums down
+// each column: C(s) = sum_{k=s}^{s+m-1} Q_k + R_{s+m}.
+template <bool VEC4>
+__global__ void __launch_bounds__(kStripeThreads)
+    k_stripe_chunks(Image g, int64_t p0, int64_t tile_h, int hm, int64_t K, int64_t words,
+                    uint4 *QR)
+{
+    const int64_t t = (int64_t)blockIdx.x * kStripeThreads + threadIdx.x;
+    const int64_t q = t % words, k = t / words;
+    if (k >= K)
+        return;
+    const int64_t x = 4 * q;
+    uint32_t C[4] = {0u, 0u, 0u, 0u}, D[4] = {0u, 0u, 0u, 0u};
+    uint32_t RC[4] = {0u, 0u, 0u, 0u}, RD[4] = {0u, 0u, 0u, 0u};
+    const int64_t pk = p0 + k * tile_h;
+    for (int64_t a = 0; a < tile_h; a += kStripeBatch) {
+        uint32_t wd[kStripeBatch];
+#pragma unroll
+        for (int j = 0; j < kStripeBatch; j++) {
+            const int64_t r = pk + a + j;
+            wd[j] = (a + j < tile_h && r >= 0 && r < g.H) ? stripe_word<VEC4>(g, r, x) : 0u;
+        }
+#pragma unroll
+        for (int j = 0; j < kStripeBatch; j++) {
+            if (a + j == hm) {  // R: the sums of the first hm rows
+#pragma unroll
+                for (int b = 0; b < 4; b++) {
+                    RC[b] = C[b];
+                    RD[b] = D[b];
+                }
+            }
+            stripe_acc(C, D, wd[j], 1);
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < 4; b++)
+        if (x + b < g.W)
+            QR[k * g.W + x + b] = make_uint4(C[b], D[b], RC[b], RD[b]);
+}
+
+__global__ void __launch_bounds__(kStripeThreads)
+    k_stripe_slide(int64_t W, int64_t S, int m, int group, const uint4 *QR, uint2 *out)
+{
+    const int64_t t = (int64_t)blockIdx.x * kStripeThreads + threadIdx.x;
+    const int64_t x = t % W, s0 = (t / W) * group;
+    if (s0 >= S)
+        return;
+    const int64_t s1 = s0 + group < S ? s0 + group : S;
+    uint32_t c = 0, d = 0;
+    for (int k = 0; k < m; k++) {
+        const uint4 v = __ldg(QR + (s0 + k) * W + x);
+        c += v.x;
+        d += v.y;
+    }
+    for (int64_t s = s0; s < s1; s++) {
+        if (s > s0) {
+            const uint4 vin = __ldg(QR + (s + m - 1) * W + x), vout = __ldg(QR + (s - 1) * W + x);
+            c += vin.x - vout.x;
+            d += vin.y - vout.y;
+        }
+        const uint4 r = __ldg(QR + (s + m) * W + x);
+        out[s * W + x] = make_uint2(c + r.z, d + r.w);
+    }
+}
+
 // Tile starts per pre-pass thread: fewer means more threads (latency
 // hiding) but more repeated h-row sums (BZ_STRIPE_GROUP overrides: tuning).
 static int stripe_group()
@@ -188,23 +257,49 @@ uint2 *launch_stripes(const Image &g, const Window &win, int64_t row0, int64_t t
 {
     if (!use_stripes(win.h) || tiles_y <= 1)
         return nullptr;
+    // chunked form when the window spans at least four tile heights (measured
+    // on GB300: 255 x 255 86 vs 105 us; at 63 x 63, three tile heights, the
+    // per-group slide is 2 us faster).  BZ_STRIPE_MODE=0/1 forces one (tuning).
+    static const int env_mode = [] {
+        const char *e = getenv("BZ_STRIPE_MODE");
+        return e ? atoi(e) : -1;
+    }();
+    const int m = (int)(win.h / tile_h), hm = (int)(win.h - (int64_t)m * tile_h);
+    const int mode = env_mode >= 0 ? env_mode : (m >= 4 ? 1 : 0);
+    const bool vec4 = ((uintptr_t)g.img % 4 == 0) && (g.pitch % 4 == 0);
+    const int64_t words = (g.W + 3) / 4;
+    const size_t sbytes = ((size_t)tiles_y * (size_t)g.W * sizeof(uint2) + 15) & ~(size_t)15;
+    const int64_t K = tiles_y + m + 1;  // chunks s .. s+m for every tile start
+    const size_t qbytes = mode ? (size_t)K * (size_t)g.W * sizeof(uint4) : 0;
     uint2 *stripes = nullptr;
-    const size_t bytes = (size_t)tiles_y * (size_t)g.W * sizeof(uint2);
-    if (cudaMallocAsync((void **)&stripes, bytes, stream) != cudaSuccess) {
+    if (cudaMallocAsync((void **)&stripes, sbytes + qbytes, stream) != cudaSuccess) {
         cudaGetLastError();  // no scratch: the tiles warm up themselves
         return nullptr;
     }
-    const int64_t words = (g.W + 3) / 4;
     const int group = stripe_group();
-    const int64_t threads = words * ((tiles_y + group - 1) / group);
-    const int64_t sblocks = (threads + kStripeThreads - 1) / kStripeThreads;
-    const bool vec4 = ((uintptr_t)g.img % 4 == 0) && (g.pitch % 4 == 0);
-    if (vec4)
-        k_stripes<true><<<(unsigned)sblocks, kStripeThreads, 0, stream>>>(
-            g, win.o, win.u, row0, tile_h, tiles_y, words, group, stripes);
-    else
-        k_stripes<false><<<(unsigned)sblocks, kStripeThreads, 0, stream>>>(
-            g, win.o, win.u, row0, tile_h, tiles_y, words, group, stripes);
+    if (mode) {
+        uint4 *QR = reinterpret_cast<uint4 *>(reinterpret_cast<unsigned char *>(stripes) + sbytes);
+        const int64_t p0 = row0 - win.o + 1;
+        const int64_t b1 = (words * K + kStripeThreads - 1) / kStripeThreads;
+        if (vec4)
+            k_stripe_chunks<true><<<(unsigned)b1, kStripeThreads, 0, stream>>>(g, p0, tile_h, hm, K,
+                                                                               words, QR);
+        else
+            k_stripe_chunks<false><<<(unsigned)b1, kStripeThreads, 0, stream>>>(g, p0, tile_h, hm, K,
+                                                                                words, QR);
+        const int sg = 8;  // tile starts per sliding thread
+        const int64_t b2 = (g.W * ((tiles_y + sg - 1) / sg) + kStripeThreads - 1) / kStripeThreads;
+        k_stripe_slide<<<(unsigned)b2, kStripeThreads, 0, stream>>>(g.W, tiles_y, m, sg, QR, stripes);
+    } else {
+        const int64_t threads = words * ((tiles_y + group - 1) / group);
+        const int64_t sblocks = (threads + kStripeThreads - 1) / kStripeThreads;
+        if (vec4)
+            k_stripes<true><<<(unsigned)sblocks, kStripeThreads, 0, stream>>>(
+                g, win.o, win.u, row0, tile_h, tiles_y, words, group, stripes);
+        else
+            k_stripes<false><<<(unsigned)sblocks, kStripeThreads, 0, stream>>>(
+                g, win.o, win.u, row0, tile_h, tiles_y, words, group, stripes);
+    }
     if (cudaGetLastError() != cudaSuccess) {
         cudaFreeAsync(stripes, stream);
         return nullptr;
@@ -266,6 +361,8 @@ template <int MODE>
 static cudaError_t launch_m(const Image &g, const Window &win, const Thresh &T, const Outputs &o,
                             int64_t row0, int64_t row1, cudaStream_t stream)
 {
+    if (small_path_applies(MODE, g, win, row0, row1))
+        return launch_small(MODE, g, win, T, o, row0, row1, stream);
     const bool vec = ((uintptr_t)g.img % 8 == 0) && (g.pitch % 8 == 0);
     const bool wide = (int64_t)win.h * win.w > 66051;  // S2 may reach 2^32
     // short tiles (a small image): the launch is latency-bound, so the
