@@ -25,6 +25,7 @@ constexpr int kMmThreads = 128;            // 4 warps
 constexpr int kMmTileCols = 512;           // TW
 constexpr int kMmTileRows = 32;            // TR
 constexpr int kMmMaxWords = 3;             // vertical words per thread (NWd <= 384)
+constexpr int kMmBatch = 8;                // rows loaded together in the vertical sweeps
 
 enum MmOut : int { MM_EXTREMA = 0, MM_BERNSEN = 1 };
 
@@ -117,25 +118,38 @@ __global__ void __launch_bounds__(kMmThreads)
             smin[m] = 0xFFFFFFFFu;
             smax[m] = 0u;
         }
-        for (int64_t s = c; s >= a - o + 1; s--) {
-            if (s >= 0 && s < g.H) {
+        // (rows are loaded kMmBatch at a time so that their latencies overlap)
+        for (int64_t s0 = c; s0 >= a - o + 1; s0 -= kMmBatch) {
+            uint32_t v[kMmBatch][kMmMaxWords];
 #pragma unroll
-                for (int m = 0; m < kMmMaxWords; m++) {
-                    if (act[m]) {
-                        const uint32_t v = mm_load<VEC4>(g, s, xw[m]);
-                        smin[m] = __vminu4(smin[m], v | oob[m]);
-                        smax[m] = __vmaxu4(smax[m], v & ~oob[m]);
+            for (int k = 0; k < kMmBatch; k++) {
+                const int64_t s = s0 - k;
+                const bool in = s >= a - o + 1 && s >= 0 && s < g.H;
+#pragma unroll
+                for (int m = 0; m < kMmMaxWords; m++)
+                    v[k][m] = (in && act[m]) ? mm_load<VEC4>(g, s, xw[m]) : 0u;
+            }
+#pragma unroll
+            for (int k = 0; k < kMmBatch; k++) {
+                const int64_t s = s0 - k;
+                if (s < a - o + 1)
+                    break;
+                if (s >= 0 && s < g.H) {
+#pragma unroll
+                    for (int m = 0; m < kMmMaxWords; m++) {
+                        smin[m] = __vminu4(smin[m], v[k][m] | oob[m]);
+                        smax[m] = __vmaxu4(smax[m], v[k][m] & ~oob[m]);
                     }
                 }
-            }
-            const int64_t i = s + o - 1;  // the output row whose window starts at s
-            if (i >= a && i < b) {
+                const int64_t i = s + o - 1;  // the output row whose window starts at s
+                if (i >= a && i < b) {
 #pragma unroll
-                for (int m = 0; m < kMmMaxWords; m++) {
-                    if (act[m]) {
-                        const int q = tid + m * kMmThreads;
-                        Vmin[(i - y0) * NWP + q] = smin[m];
-                        Vmax[(i - y0) * NWP + q] = smax[m];
+                    for (int m = 0; m < kMmMaxWords; m++) {
+                        if (act[m]) {
+                            const int q = tid + m * kMmThreads;
+                            Vmin[(i - y0) * NWP + q] = smin[m];
+                            Vmax[(i - y0) * NWP + q] = smax[m];
+                        }
                     }
                 }
             }
@@ -147,20 +161,33 @@ __global__ void __launch_bounds__(kMmThreads)
             pmin[m] = 0xFFFFFFFFu;
             pmax[m] = 0u;
         }
-        for (int64_t i = a + 1; i < b; i++) {
-            const int64_t q_row = i + u;
+        for (int64_t i0 = a + 1; i0 < b; i0 += kMmBatch) {
+            uint32_t v[kMmBatch][kMmMaxWords];
 #pragma unroll
-            for (int m = 0; m < kMmMaxWords; m++) {
-                if (act[m]) {
-                    if (q_row < g.H) {
-                        const uint32_t v = mm_load<VEC4>(g, q_row, xw[m]);
-                        pmin[m] = __vminu4(pmin[m], v | oob[m]);
-                        pmax[m] = __vmaxu4(pmax[m], v & ~oob[m]);
+            for (int k = 0; k < kMmBatch; k++) {
+                const int64_t q_row = i0 + k + u;
+                const bool in = i0 + k < b && q_row < g.H;
+#pragma unroll
+                for (int m = 0; m < kMmMaxWords; m++)
+                    v[k][m] = (in && act[m]) ? mm_load<VEC4>(g, q_row, xw[m]) : 0u;
+            }
+#pragma unroll
+            for (int k = 0; k < kMmBatch; k++) {
+                const int64_t i = i0 + k;
+                if (i >= b)
+                    break;
+#pragma unroll
+                for (int m = 0; m < kMmMaxWords; m++) {
+                    if (act[m]) {
+                        if (i + u < g.H) {
+                            pmin[m] = __vminu4(pmin[m], v[k][m] | oob[m]);
+                            pmax[m] = __vmaxu4(pmax[m], v[k][m] & ~oob[m]);
+                        }
+                        const int q = tid + m * kMmThreads;
+                        const int64_t x = (i - y0) * NWP + q;
+                        Vmin[x] = __vminu4(Vmin[x], pmin[m]);
+                        Vmax[x] = __vmaxu4(Vmax[x], pmax[m]);
                     }
-                    const int q = tid + m * kMmThreads;
-                    const int64_t x = (i - y0) * NWP + q;
-                    Vmin[x] = __vminu4(Vmin[x], pmin[m]);
-                    Vmax[x] = __vmaxu4(Vmax[x], pmax[m]);
                 }
             }
         }
