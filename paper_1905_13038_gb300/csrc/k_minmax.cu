@@ -72,11 +72,14 @@ __global__ void __launch_bounds__(kMmThreads)
     const int NWd = mm_words(win.w), NWP = mm_pitch_words(win.w);
     uint32_t *Vmin = mm_smem;                        // [TR][NWP]
     uint32_t *Vmax = mm_smem + kMmTileRows * NWP;    // [TR][NWP]
+    // per-warp scratch rows for the doubling steps (ping-pong with the row)
+    uint32_t *Smin = mm_smem + 2 * kMmTileRows * NWP + (threadIdx.x >> 5) * NWP;
+    uint32_t *Smax = Smin + (kMmThreads / 32) * NWP;
 
     const int64_t tx = (int64_t)blockIdx.x % tiles_x, ty = (int64_t)blockIdx.x / tiles_x;
     const int64_t x0 = tx * kMmTileCols, y0 = ty * kMmTileRows;
     const int64_t y1 = y0 + kMmTileRows < g.H ? y0 + kMmTileRows : g.H;
-    const int l = win.l, r = win.r, o = win.o, u = win.u, h = win.h, w = win.w;
+    const int l = win.l, o = win.o, u = win.u, h = win.h, w = win.w;
     const int64_t xs = x0 - (l - 1);
     const int64_t xa = xs >= 0 ? (xs & ~(int64_t)3) : -((-xs + 3) & ~(int64_t)3);
     const int delta = (int)(xs - xa);
@@ -88,6 +91,10 @@ __global__ void __launch_bounds__(kMmThreads)
             Vmin[i * NWP + q] = 0xFFFFFFFFu;
             Vmax[i * NWP + q] = 0u;
         }
+    for (int q = NWd + (threadIdx.x & 31); q < NWP; q += 32) {
+        Smin[q] = 0xFFFFFFFFu;
+        Smax[q] = 0u;
+    }
 
     // ---- 1. vertical extrema, per word column ----
     uint32_t oob[kMmMaxWords];
@@ -202,27 +209,20 @@ __global__ void __launch_bounds__(kMmThreads)
     const int rows = (int)(y1 - y0);
     for (int i = warp; i < rows; i += kMmThreads / 32) {
         uint32_t *rmin = Vmin + i * NWP, *rmax = Vmax + i * NWP;
+        uint32_t *tmin = Smin, *tmax = Smax;
         for (int k = 1; k <= K; k++) {
             const int sh = 1 << (k - 1);  // bytes
-            uint32_t nmin[10], nmax[10];  // NWd <= 10 * 32
-#pragma unroll
-            for (int m = 0; m < 10; m++) {
-                const int q = lane + 32 * m;
-                if (q < NWd) {
-                    nmin[m] = __vminu4(rmin[q], mm_bytes(rmin, 4 * q + sh));
-                    nmax[m] = __vmaxu4(rmax[q], mm_bytes(rmax, 4 * q + sh));
-                }
+            for (int q = lane; q < NWd; q += 32) {
+                tmin[q] = __vminu4(rmin[q], mm_bytes(rmin, 4 * q + sh));
+                tmax[q] = __vmaxu4(rmax[q], mm_bytes(rmax, 4 * q + sh));
             }
             __syncwarp();
-#pragma unroll
-            for (int m = 0; m < 10; m++) {
-                const int q = lane + 32 * m;
-                if (q < NWd) {
-                    rmin[q] = nmin[m];
-                    rmax[q] = nmax[m];
-                }
-            }
-            __syncwarp();
+            uint32_t *x = rmin;  // the new extrema become the current row
+            rmin = tmin;
+            tmin = x;
+            x = rmax;
+            rmax = tmax;
+            tmax = x;
         }
         // window extremum of output column x0 + 4p + e: bytes at start
         // 4p + delta and 4p + delta + w - 2^K
@@ -274,6 +274,7 @@ __global__ void __launch_bounds__(kMmThreads)
                 bits[row * out_pitch + (j0 >> 3)] = (uint8_t)byte;
             }
         }
+        __syncwarp();  // the scratch rows are rewritten by the next row
     }
 }
 
@@ -288,7 +289,8 @@ static cudaError_t launch_mm_t(const Image &g, const Window &win, int32_t contra
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess)
         return e;
-    const size_t smem = (size_t)2 * kMmTileRows * mm_pitch_words(511) * sizeof(uint32_t);
+    const size_t smem =
+        (size_t)(2 * kMmTileRows + 2 * (kMmThreads / 32)) * mm_pitch_words(511) * sizeof(uint32_t);
     if (dev >= 64 || !(configured >> dev & 1ull)) {
         e = cudaFuncSetAttribute(k_minmax<OUT, VEC4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
@@ -297,7 +299,8 @@ static cudaError_t launch_mm_t(const Image &g, const Window &win, int32_t contra
         if (dev < 64)
             configured |= 1ull << dev;
     }
-    const size_t need = (size_t)2 * kMmTileRows * mm_pitch_words(win.w) * sizeof(uint32_t);
+    const size_t need =
+        (size_t)(2 * kMmTileRows + 2 * (kMmThreads / 32)) * mm_pitch_words(win.w) * sizeof(uint32_t);
     const int64_t tiles_x = (g.W + kMmTileCols - 1) / kMmTileCols;
     const int64_t tiles = tiles_x * ((g.H + kMmTileRows - 1) / kMmTileRows);
     if (tiles > 2147483647LL)
