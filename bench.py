@@ -470,7 +470,8 @@ def extra_serve(bz, synth, dev, n_req=2000, seed=5, rates=(0.1, 0.3, 0.5, 0.7, 0
     window uniform in [15, 255]) arriving as a Poisson process.  The
     saturation rate is measured first (all requests submitted at once), then
     Poisson arrivals at the given multiples of it.  Latency = submit ->
-    bz_server_wait returns."""
+    bz_server_wait returns.  A second mode ingests from pinned host memory:
+    the image is uploaded per request and the output downloaded."""
     import concurrent.futures as cf
     import numpy as np
     import torch
@@ -540,6 +541,58 @@ def extra_serve(bz, synth, dev, n_req=2000, seed=5, rates=(0.1, 0.3, 0.5, 0.7, 0
     res = {"requests": n_req, "mpix_total": round(px_total / 1e6, 1), "saturation": sat}
     for f in rates:
         res[f"load_{f}"] = run(f * sat_rate)
+
+    # host ingest: the first n_host requests with their images in pinned host
+    # memory; each request copies its image to the device, is served, and
+    # copies its packed output back (latency = arrival -> output on the host)
+    n_host = min(400, n_req)
+    host_imgs = [jobs[q].image.cpu().pin_memory() for q in range(n_host)]
+    dev_imgs = [torch.empty_like(jobs[q].image, memory_format=torch.contiguous_format) for q in range(n_host)]
+    host_outs = [torch.empty(jobs[q].out.shape, dtype=torch.uint8).pin_memory() for q in range(n_host)]
+    hjobs = [bz.Job(dev_imgs[q], jobs[q].c.method, jobs[q].c.h, jobs[q].c.w, k=jobs[q].c.k, R=jobs[q].c.R,
+                    q_num=jobs[q].c.q_num, q_den=jobs[q].c.q_den, offset=jobs[q].c.offset)
+             for q in range(n_host)]
+    px_host = sum(int(j.c.H) * int(j.c.W) for j in hjobs)
+
+    def run_host(rate):
+        srv = bz.Server(hbm_budget_bytes=budget, max_slots=64)
+        t_arr = np.zeros(n_host)
+        t_done = np.zeros(n_host)
+        gaps = rng.exponential(1.0 / rate, n_host) if rate else np.zeros(n_host)
+
+        def serve(q):
+            st_ = torch.cuda.Stream(device=dev)
+            with torch.cuda.stream(st_):
+                dev_imgs[q].copy_(host_imgs[q], non_blocking=True)
+            st_.synchronize()
+            status = srv.wait(srv.submit(hjobs[q]), 120000)
+            with torch.cuda.stream(st_):
+                host_outs[q].copy_(hjobs[q].out, non_blocking=True)
+            st_.synchronize()
+            t_done[q] = time.perf_counter()
+            return status
+        futs = []
+        t0 = time.perf_counter()
+        nxt = t0
+        for q in range(n_host):
+            nxt += gaps[q]
+            while time.perf_counter() < nxt:
+                time.sleep(0.0002)
+            t_arr[q] = time.perf_counter()
+            futs.append(pool.submit(serve, q))
+        sts = [f.result() for f in futs]
+        srv.close()
+        lat = (t_done - t_arr) * 1e3
+        return {"rate_req_s": round(rate, 1) if rate else None,
+                "p50_ms": round(float(np.percentile(lat, 50)), 3),
+                "p99_ms": round(float(np.percentile(lat, 99)), 3),
+                "gpix_s": round(px_host / (t_done.max() - t0) / 1e9, 2),
+                "ok": int(sum(1 for x in sts if x == 0))}
+
+    hsat = run_host(0)
+    hrate = n_host / (px_host / (hsat["gpix_s"] * 1e9))
+    res["host_ingest"] = {"requests": n_host, "mpix_total": round(px_host / 1e6, 1), "saturation": hsat,
+                          "load_0.5": run_host(0.5 * hrate)}
     pool.shutdown()
     return res
 
