@@ -141,6 +141,30 @@ bz_status binarize_precision_report(int32_t method, const uint8_t *image,
  * stream finishes.  Diagnostic only; returns -1 when unknown. */
 int64_t bz_last_fp64_fallbacks(void *stream);
 
+/* Sauvola (method 0) or Niblack (method 1) from HOST memory: the image is
+ * uploaded, binarized and the packed output downloaded.  The call returns once
+ * the work is enqueued; every later operation on `stream` (and a synchronize
+ * of it) comes after the download, so synchronise the stream before reading
+ * out_host.  The call does not wait for work already on `stream`: the host
+ * image is read from the moment of the call.  image_host: H rows of
+ * in_pitch >= W bytes; out_host: H rows of out_pitch >= ceil(W/8) bytes; both
+ * must stay valid and the image unchanged until the stream has been
+ * synchronised, and they must not overlap.  Page-locked (pinned) host memory
+ * makes the copies asynchronous; pageable memory works but the copies then
+ * block the host.  The library runs the upload, compute and download of a
+ * device's calls on three streams of its own with two sets of device buffers
+ * used in turn (grown with cudaMalloc when a larger page arrives, after the
+ * set's previous call is done), so that a sequence of calls overlaps one
+ * call's upload and download with its neighbours' compute.  Calls from
+ * several host threads are serialised on a per-device lock while they
+ * enqueue.  CUDA failure -> BZ_ECUDA (nothing of the call is then left in
+ * flight).  Results equal binarize_sauvola / binarize_niblack. */
+bz_status binarize_host(int32_t method, const uint8_t *image_host, int64_t H,
+                        int64_t W, int64_t in_pitch, int32_t h, int32_t w,
+                        double k, double R, uint8_t *out_host,
+                        int64_t out_pitch, bz_precision precision,
+                        void *stream);
+
 /* ---------------------------------------------------------------------- */
 /* In-place binarization (Sec. 3.2 assumptions: the algorithm can be made */
 /* in-place by keeping the gray levels that later windows still need).    */

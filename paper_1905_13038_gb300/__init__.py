@@ -26,7 +26,7 @@ __all__ = [
     "WOLF", "FENG", "RAIS", "NICK", "PHANSALKAR", "binarize_wolf", "binarize_feng", "binarize_rais",
     "binarize_nick", "binarize_phansalkar", "global_stats", "binarize_precision_report_ext",
     "window_minmax", "binarize_bernsen", "haar_feature", "HAAR_FEATURES", "binarize_inplace",
-    "inplace_scratch_bytes",
+    "inplace_scratch_bytes", "binarize_host",
 ]
 
 FP64, FP32, FP64_DIRECT = 0, 1, 2
@@ -99,6 +99,7 @@ def _load():
         "binarize_bernsen": ([P, i64, i64, i64, i32, i32, i32, P, i64, P], st),
         "haar_feature": ([P, i64, i64, i64, ctypes.POINTER(_HaarC), P, P], st),
         "binarize_inplace": ([i32, P, i64, i64, i64, i32, i32, f64, f64, i64, st, P], st),
+        "binarize_host": ([i32, P, i64, i64, i64, i32, i32, f64, f64, P, i64, st, P], st),
         "bz_inplace_scratch_bytes": ([i64, i64, i32, i64], i64),
         "binarize_precision_report_ext": ([i32, P, i64, i64, i64, i32, i32, P, P, P, P], st),
         "binarize_batch": ([ctypes.POINTER(_JobC), i32, st, P], st),
@@ -362,6 +363,29 @@ def binarize_inplace(method: int, image, h: int, w: int, k: float = 0.5, R: floa
     _check("binarize_inplace", _load().binarize_inplace(method, ptr, H, W, pitch, h, w, k, R, band_rows,
                                                         _PREC[precision], _stream(stream)))
     return image
+
+
+def binarize_host(method: int, image, h: int, w: int, k: float = 0.5, R: float = 128.0, out=None,
+                  precision="fp64", W: int | None = None, stream=None, sync: bool = True):
+    """Sauvola / Niblack from host memory: `image` is a 2-D uint8 CPU tensor
+    (pinned for asynchronous copies) whose first W columns hold the image;
+    returns the packed output as a CPU uint8 tensor (H, ceil(W/8)).  With
+    sync=False the call only enqueues: synchronise `stream` before reading."""
+    import torch
+    if image.is_cuda or image.dtype != torch.uint8 or image.dim() != 2 or image.stride(1) != 1:
+        raise ValueError("image must be a 2-D uint8 CPU tensor with unit column stride")
+    H = image.shape[0]
+    pitch = image.stride(0) if H > 1 else image.shape[1]
+    W = image.shape[1] if W is None else W
+    if out is None:
+        out = torch.empty((H, (W + 7) // 8), dtype=torch.uint8, pin_memory=image.is_pinned())
+    op = out.stride(0) if out.shape[0] > 1 else out.shape[1]
+    s = _stream(stream)
+    _check("binarize_host", _load().binarize_host(method, image.data_ptr(), H, W, pitch, h, w, k, R,
+                                                  out.data_ptr(), op, _PREC[precision], s))
+    if sync:
+        torch.cuda.Stream(stream_ptr=s.value).synchronize() if s.value else torch.cuda.synchronize()
+    return out
 
 
 def inplace_scratch_bytes(H: int, W: int, h: int, band_rows: int = 0) -> int:

@@ -581,6 +581,145 @@ bz_status binarize_inplace(int32_t method, uint8_t *image, int64_t H, int64_t W,
     return st;
 }
 
+// binarize_host's per-device pipeline: an upload, a compute and a download
+// stream, and two slots used in turn, each with a device image and output
+// buffer and the events that mark its upload, compute and download done.
+// Call n uploads into slot n % 2 once that slot's previous compute has read
+// it, computes once the upload is done and the slot's previous output is
+// home, and downloads; the caller's stream waits only for the download, so
+// call n+1's upload runs during call n's compute and call n+1's compute
+// during call n's download.  Fixed buffers rather than stream-ordered
+// allocations: a pool allocation on one stream can be handed memory freed on
+// another and then wait for that stream's work.
+struct HostSlot {
+    uint8_t *img = nullptr, *out = nullptr;
+    size_t img_cap = 0, out_cap = 0;
+    cudaEvent_t up = nullptr, comp = nullptr, down = nullptr;
+};
+
+struct HostState {
+    std::mutex mu;
+    cudaStream_t up = nullptr, comp = nullptr, down = nullptr;
+    HostSlot slot[2];
+    int next = 0;
+};
+
+static HostState *host_state(int dev)
+{
+    static std::mutex mu;
+    static HostState *st[64] = {nullptr};
+    if (dev < 0 || dev >= 64)
+        return nullptr;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!st[dev]) {
+        HostState *h = new HostState();
+        bool ok = cudaStreamCreateWithFlags(&h->up, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaStreamCreateWithFlags(&h->comp, cudaStreamNonBlocking) == cudaSuccess &&
+                  cudaStreamCreateWithFlags(&h->down, cudaStreamNonBlocking) == cudaSuccess;
+        for (HostSlot &sl : h->slot)
+            ok = ok && cudaEventCreateWithFlags(&sl.up, cudaEventDisableTiming) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&sl.comp, cudaEventDisableTiming) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&sl.down, cudaEventDisableTiming) == cudaSuccess;
+        if (!ok)
+            return nullptr;  // (leaked on this rare failure; the next call retries)
+        st[dev] = h;
+    }
+    return st[dev];
+}
+
+// Grow a slot buffer to `need` bytes once its last user (marked by `last`)
+// is done.
+static bool host_grow(uint8_t *&buf, size_t &cap, size_t need, cudaEvent_t last)
+{
+    if (cap >= need)
+        return true;
+    if (cudaEventSynchronize(last) != cudaSuccess)
+        return false;
+    if (buf)
+        cudaFree(buf);
+    buf = nullptr;
+    cap = 0;
+    if (cudaMalloc((void **)&buf, need) != cudaSuccess)
+        return false;
+    cap = need;
+    return true;
+}
+
+bz_status binarize_host(int32_t method, const uint8_t *image_host, int64_t H, int64_t W,
+                        int64_t in_pitch, int32_t h, int32_t w, double k, double R,
+                        uint8_t *out_host, int64_t out_pitch, bz_precision precision, void *stream)
+{
+    bz_status st = check_image(image_host, H, W, in_pitch, h, w);
+    if (st != BZ_OK)
+        return st;
+    const int64_t cw = (W + 7) / 8;
+    if (!out_host || out_pitch < cw || out_pitch > (INT64_MAX / H))
+        return BZ_EINVAL;
+    if (ranges_overlap(image_host, (size_t)((H - 1) * in_pitch + W), out_host,
+                       (size_t)((H - 1) * out_pitch + cw)))
+        return BZ_EOVERLAP;
+    if ((method != 0 && method != 1) || !finite_params(method, k, R))
+        return BZ_EINVAL;
+    int mode;
+    switch (precision) {
+    case BZ_FP64: mode = MODE_FP64; break;
+    case BZ_FP32: mode = MODE_FP32; break;
+    case BZ_FP64_DIRECT: mode = MODE_FP64_DIRECT; break;
+    default: return BZ_EINVAL;
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess)
+        return BZ_ECUDA;
+    HostState *hs = host_state(dev);
+    if (!hs)
+        return BZ_ECUDA;
+    const Window win = make_window(h, w);
+    const Thresh T = make_thresh(method, k, method == 0 ? R : 128.0);
+    // device rows of 16-byte multiples; a host pitch that already is one (and
+    // no wider than needed) keeps the copy a single contiguous transfer
+    const int64_t dpitch = (in_pitch % 16 == 0 && in_pitch - W < 16) ? in_pitch : (W + 15) & ~(int64_t)15;
+    Outputs o{};
+    o.out_pitch = cw;
+    unsigned long long *fb = mode == MODE_FP64 ? fallback_counter(dev) : nullptr;
+    std::lock_guard<std::mutex> lk(hs->mu);
+    HostSlot &sl = hs->slot[hs->next];
+    hs->next ^= 1;
+    bool ok = host_grow(sl.img, sl.img_cap, (size_t)(H * dpitch), sl.down) &&
+              host_grow(sl.out, sl.out_cap, (size_t)(H * cw), sl.down);
+    o.bits = sl.out;
+    o.fallbacks = fb;
+    // upload once the slot's previous compute has read its image
+    ok = ok && cudaStreamWaitEvent(hs->up, sl.comp, 0) == cudaSuccess;
+    if (ok && dpitch == in_pitch)
+        ok = cudaMemcpyAsync(sl.img, image_host, (size_t)((H - 1) * in_pitch + W), cudaMemcpyHostToDevice,
+                             hs->up) == cudaSuccess;
+    else if (ok)
+        ok = cudaMemcpy2DAsync(sl.img, (size_t)dpitch, image_host, (size_t)in_pitch, (size_t)W, (size_t)H,
+                               cudaMemcpyHostToDevice, hs->up) == cudaSuccess;
+    ok = ok && cudaEventRecord(sl.up, hs->up) == cudaSuccess;
+    // compute once the upload is done and the slot's previous output is home
+    ok = ok && cudaStreamWaitEvent(hs->comp, sl.up, 0) == cudaSuccess &&
+         cudaStreamWaitEvent(hs->comp, sl.down, 0) == cudaSuccess &&
+         (!fb || cudaMemsetAsync(fb, 0, sizeof(unsigned long long), hs->comp) == cudaSuccess) &&
+         launch_window(mode, Image{sl.img, H, W, dpitch}, win, T, o, hs->comp) == cudaSuccess &&
+         cudaEventRecord(sl.comp, hs->comp) == cudaSuccess;
+    // download, and order the caller's stream after it
+    ok = ok && cudaStreamWaitEvent(hs->down, sl.comp, 0) == cudaSuccess;
+    if (ok && out_pitch == cw)
+        ok = cudaMemcpyAsync(out_host, sl.out, (size_t)(H * cw), cudaMemcpyDeviceToHost, hs->down) == cudaSuccess;
+    else if (ok)
+        ok = cudaMemcpy2DAsync(out_host, (size_t)out_pitch, sl.out, (size_t)cw, (size_t)cw, (size_t)H,
+                               cudaMemcpyDeviceToHost, hs->down) == cudaSuccess;
+    ok = ok && cudaEventRecord(sl.down, hs->down) == cudaSuccess &&
+         cudaStreamWaitEvent((cudaStream_t)stream, sl.down, 0) == cudaSuccess;
+    if (!ok) {  // leave nothing of this call in flight
+        cudaStreamSynchronize(hs->up);
+        cudaStreamSynchronize(hs->comp);
+        cudaStreamSynchronize(hs->down);
+    }
+    return ok ? BZ_OK : BZ_ECUDA;
+}
+
 int64_t bz_inplace_scratch_bytes(int64_t H, int64_t W, int32_t h, int64_t band_rows)
 {
     if (H < 1 || W < 1 || h < 1 || h > 511)

@@ -29,7 +29,8 @@ def test_header_declares_expected_entry_points():
               "bz_status_string", "bz_last_fp64_fallbacks", "binarize_wolf", "binarize_feng",
               "binarize_rais", "binarize_nick", "binarize_phansalkar", "global_stats",
               "binarize_precision_report_ext", "binarize_batch_noalloc", "window_minmax",
-              "binarize_bernsen", "haar_feature", "binarize_inplace", "bz_inplace_scratch_bytes"]:
+              "binarize_bernsen", "haar_feature", "binarize_inplace", "bz_inplace_scratch_bytes",
+              "binarize_host"]:
         assert n in names, n
 
 
