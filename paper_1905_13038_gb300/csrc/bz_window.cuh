@@ -770,6 +770,25 @@ __device__ __forceinline__ void window_rows(const Image &g, const Window &win, c
     }
 }
 
+// Edge tiles: a byte stream that starts at column c outside [0, W - 8] is
+// read from the nearest in-row 8 bytes, at cl = clamp(c, 0, W - 8), and
+// shifted by sh = cl - c bytes (clamped to +-8), so that byte m holds column
+// c + m and columns outside [0, W) read as 0.  Needs W >= 8.
+__device__ __forceinline__ void edge_clamp(int64_t c, int64_t W, int64_t &cl, int &sh)
+{
+    cl = c < 0 ? 0 : (c > W - 8 ? W - 8 : c);
+    const int64_t d = cl - c;
+    sh = d > 8 ? 8 : (d < -8 ? -8 : (int)d);
+}
+
+__device__ __forceinline__ uint2 shift8(uint2 v, int sh)
+{
+    unsigned long long x = ((unsigned long long)v.y << 32) | v.x;
+    const unsigned b = 8u * (unsigned)(sh < 0 ? -sh : sh);
+    x = b >= 64u ? 0ull : (sh > 0 ? x << b : x >> b);
+    return make_uint2((uint32_t)x, (uint32_t)(x >> 32));
+}
+
 // Interior tiles, binarize modes, 32-bit S2: a one-row software pipeline.
 // Iteration i computes the window sums of row i (slide, lane prefix, warp
 // scan) and stores them to a warp-private shared-memory slot, then evaluates
@@ -778,8 +797,12 @@ __device__ __forceinline__ void window_rows(const Image &g, const Window &win, c
 // rare FP64 near-tie path at its end, so the compiler can interleave the
 // scan's latency chain with the threshold arithmetic.  Rows outside the image
 // are handled without branches (safe row pointer + zero mask).
-// smem: 4096 bytes per warp.
-template <int MODE, bool WARMB = false>
+// EDGE: the same for the first and last tile columns (and tiles of images
+// narrower than a tile): streams that leave the row are clamped and shifted
+// (edge_clamp), the anchor window is clipped to the row, and the per-column
+// counts and their reciprocals come from a per-warp table.
+// smem: 6144 bytes per warp (two 2 KB row slots, then the 2 KB column table).
+template <int MODE, bool WARMB = false, bool EDGE = false>
 __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &win, const Thresh &T,
                                                  const Outputs &o, int64_t x0, int64_t y0,
                                                  int64_t y1, int lane, uint4 *slots,
@@ -790,17 +813,47 @@ __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &w
     const int64_t j0 = x0 + (int64_t)kColsPerLane * lane;
     const int l = win.l, r = win.r, oo = win.o, u = win.u;
     const int64_t colA = j0 + r, colB = j0 - l;
-    const int kA = (int)(colA & 3), kB = (int)(colB & 3);  // warp-uniform
+    // load columns (32-bit: the caller guarantees W <= 2^30) and, for EDGE,
+    // the byte shifts of the A, B and centre streams as three signed bytes
+    int32_t pA = (int32_t)colA, pB = (int32_t)colB, pP = (int32_t)j0;
+    uint32_t shifts = 0;
+    if (EDGE) {
+        int64_t c;
+        int sh;
+        edge_clamp(colA, g.W, c, sh);
+        pA = (int32_t)c;
+        shifts = (uint32_t)(sh & 0xFF);
+        edge_clamp(colB, g.W, c, sh);
+        pB = (int32_t)c;
+        shifts |= (uint32_t)(sh & 0xFF) << 8;
+        edge_clamp(j0, g.W, c, sh);
+        pP = (int32_t)c;
+        shifts |= (uint32_t)(sh & 0xFF) << 16;
+    }
+    auto shift_of = [&](int q) { return (int)(int8_t)(uint8_t)(shifts >> (8 * q)); };
+    const int kA = pA & 3, kB = pB & 3;  // warp-uniform unless EDGE
     const unsigned selA = (unsigned)kA * 0x1111u + 0x3210u;
     const unsigned selB = (unsigned)kB * 0x1111u + 0x3210u;
+    auto ldA = [&](const uint8_t *rp) {
+        const uint2 v = ld8_w3(rp + pA, kA, selA);
+        return EDGE ? shift8(v, shift_of(0)) : v;
+    };
+    auto ldB = [&](const uint8_t *rp) {
+        const uint2 v = ld8_w3(rp + pB, kB, selB);
+        return EDGE ? shift8(v, shift_of(1)) : v;
+    };
     const float inv_w = __frcp_rn((float)win.w);
     const float inv_h = __frcp_rn((float)win.h);
     const float inv_hw = inv_h * inv_w;
 
     // anchor words: the caller guarantees (aend - a4) <= 128, one word per
     // lane; lanes past the window read the first word and mask it to zero
-    const int64_t ac0 = x0 - l, aend = x0 + r;
-    const int64_t a4 = ac0 & ~(int64_t)3;  // ac0 >= 0 for interior tiles
+    int64_t ac0 = x0 - l, aend = x0 + r;
+    if (EDGE) {  // clip the anchor window to the row
+        ac0 = ac0 > 0 ? ac0 : 0;
+        aend = aend < g.W ? aend : g.W;
+    }
+    const int64_t a4 = ac0 & ~(int64_t)3;  // ac0 >= 0 here
     const int64_t c4 = a4 + 4 * lane;
     const bool has_word = c4 < aend;
     uint32_t keep = 0xFFFFFFFFu;
@@ -808,7 +861,7 @@ __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &w
         keep &= 0xFFFFFFFFu << (8 * (int)(ac0 - c4));
     if (c4 + 4 > aend)
         keep = (c4 >= aend) ? 0u : (keep & (0xFFFFFFFFu >> (8 * (int)(c4 + 4 - aend))));
-    const int64_t aoff = has_word ? c4 : a4;
+    const int32_t aoff = (int32_t)(has_word ? c4 : a4);
     auto anchor_row = [&](const uint8_t *rp, uint32_t &s1, uint32_t &s2) {
         const uint32_t wd = __ldg(reinterpret_cast<const uint32_t *>(rp + aoff)) & keep;
         s1 = __dp4a(wd, 0x01010101u, s1);
@@ -843,8 +896,8 @@ __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &w
                     w1r[q] = w2r[q] = 0u;
                     if (a + q <= a_hi) {  // warp-uniform
                         const uint8_t *rp = g.img + (a + q) * g.pitch;
-                        Ar[q] = ld8_w3(rp + colA, kA, selA);
-                        Br[q] = ld8_w3(rp + colB, kB, selB);
+                        Ar[q] = ldA(rp);
+                        Br[q] = ldB(rp);
                         anchor_row(rp, w1r[q], w2r[q]);
                     }
                 }
@@ -861,8 +914,8 @@ __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &w
         uint32_t w1 = 0, w2 = 0;
         if (a_lo <= a_hi) {
             const uint8_t *rp = g.img + a_lo * g.pitch;
-            A = ld8_w3(rp + colA, kA, selA);
-            B = ld8_w3(rp + colB, kB, selB);
+            A = ldA(rp);
+            B = ldB(rp);
             anchor_row(rp, w1, w2);
         }
         for (int64_t a = a_lo; a <= a_hi; a++) {
@@ -870,8 +923,8 @@ __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &w
             uint32_t v1 = 0, v2 = 0;
             if (a < a_hi) {
                 const uint8_t *rp = g.img + (a + 1) * g.pitch;
-                An = ld8_w3(rp + colA, kA, selA);
-                Bn = ld8_w3(rp + colB, kB, selB);
+                An = ldA(rp);
+                Bn = ldB(rp);
                 anchor_row(rp, v1, v2);
             }
             warm8(A, B, E1, E2);
@@ -895,8 +948,8 @@ __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &w
         const bool va = ra < H, vb = rb >= 0;
         const uint8_t *pa = g.img + (va ? ra : 0) * g.pitch;
         const uint8_t *pb = g.img + (vb ? rb : 0) * g.pitch;
-        uint2 A = ld8_w3(pa + colA, kA, selA), B = ld8_w3(pa + colB, kB, selB);
-        uint2 C = ld8_w3(pb + colA, kA, selA), D = ld8_w3(pb + colB, kB, selB);
+        uint2 A = ldA(pa), B = ldB(pa);
+        uint2 C = ldA(pb), D = ldB(pb);
         uint32_t e1 = 0, e2 = 0, x1 = 0, x2 = 0;
         anchor_row(pa, e1, e2);
         anchor_row(pb, x1, x2);
@@ -934,6 +987,24 @@ __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &w
     const bool simple = T.method == 0 && T.alpha >= 0.0f && T.beta >= 0.0f;
     unsigned long long nfb = 0;
 
+    // EDGE: column counts of this lane's 8 columns (1 past the row) and
+    // their correctly rounded reciprocals, entry m * 32 + lane; each lane
+    // reads back only its own entries.  `vmask`: the output bits inside the
+    // row.
+    uint2 *ctab = reinterpret_cast<uint2 *>(slots + 256);
+    uint32_t vmask = 0xFFu;
+    if (EDGE) {
+#pragma unroll
+        for (int m = 0; m < kColsPerLane; m++) {
+            const int64_t j = j0 + m;
+            const int64_t c = (j + r < g.W - 1 ? j + r : g.W - 1) - (j - l > -1 ? j - l : -1);
+            const uint32_t cm = j < g.W ? (uint32_t)c : 1u;
+            ctab[m * 32 + lane] = make_uint2(__float_as_uint(__frcp_rn((float)cm)), cm);
+        }
+        const int64_t left = g.W - j0;
+        vmask = left >= 8 ? 0xFFu : (left <= 0 ? 0u : (1u << (unsigned)left) - 1u);
+    }
+
     // threshold of row i from slot (i & 1) and its pixels P; stores the byte
     auto threshold_row = [&](int64_t i, uint2 P) {
         const uint4 *sl = slots + (int)(i & 1) * 128;
@@ -944,61 +1015,95 @@ __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &w
         const int64_t rows = (i + u < H - 1 ? i + u : H - 1) - (i - oo > -1 ? i - oo : -1);
         const uint32_t nrow = (uint32_t)rows;
         const uint32_t nw = nrow * (uint32_t)win.w;
-        const float inv_nw = nrow == (uint32_t)win.h ? inv_hw : __frcp_rn((float)rows) * inv_w;
-        const float inv_n2 = inv_nw * inv_nw;
-        // slack[m] = |d| - E (certified when > 0); only the row minimum is
-        // kept on the hot path, the undecided set is rebuilt when it is <= 0
+        const float inv_nw = nrow == (uint32_t)win.h ? (EDGE ? inv_h : inv_hw)
+                                                     : __frcp_rn((float)rows) * (EDGE ? 1.0f : inv_w);
+        // count and 1/count of column m: the window width (interior tiles) or
+        // the table entry (edge tiles)
+        auto count = [&](int m, uint32_t &n_m, float &inv_m) {
+            if (EDGE) {
+                const uint2 e = ctab[m * 32 + lane];
+                n_m = nrow * e.y;
+                inv_m = inv_nw * __uint_as_float(e.x);
+            } else {
+                n_m = nw;
+                inv_m = inv_nw;
+            }
+        };
+        // FP32 threshold of pixel m: returns its bit and sets `slack` =
+        // |d| - E, certified when > 0 (columns past the row count as
+        // certified).  SIMPLE: Sauvola with alpha, beta >= 0 (mag = t).
+        auto eval = [&](bool SIMPLE, int m, uint32_t S1, uint32_t S2, float &slack) -> uint32_t {
+            uint32_t n_m;
+            float inv_m;
+            count(m, n_m, inv_m);
+            const float mu = __uint2float_rn(S1) * inv_m;
+            const float var = v_float<S2T>(n_m, (uint64_t)S2, S1) * (inv_m * inv_m);
+            float t, mag;
+            if (SIMPLE) {
+                t = mu * fmaf(T.beta, sqrt_approx(var), T.alpha);
+                mag = t;
+            } else {
+                const float s = sqrt_approx(var);
+                t = fmaf(fmaf(T.beta, mu, T.gamma), s, T.alpha * mu);
+                mag = fmaf(fmaf(T.abeta, mu, T.agamma), s, T.aalpha * mu);
+            }
+            const float d = t - pixel_f(P, m);
+            slack = fabsf(d) - fmaf(T.eps, mag, T.delta64);
+            if (EDGE && !(vmask >> m & 1u))
+                slack = 1.0f;
+            return __float_as_uint(d) >> 31;
+        };
+        // hot path: the bits and the row's smallest slack only
         uint32_t byte = 0;
         float minslack = 1.0f;
-        float slack[kColsPerLane];
         if (simple) {
 #pragma unroll
             for (int m = 0; m < kColsPerLane; m++) {
-                const float mu = __uint2float_rn(S1v[m]) * inv_nw;
-                const float var = v_float<S2T>(nw, (uint64_t)S2v[m], S1v[m]) * inv_n2;
-                const float t = mu * fmaf(T.beta, sqrt_approx(var), T.alpha);
-                const float d = t - pixel_f(P, m);
-                byte |= (__float_as_uint(d) >> 31) << m;
-                if (MODE == MODE_FP64) {
-                    slack[m] = fabsf(d) - fmaf(T.eps, t, T.delta64);
-                    minslack = fminf(minslack, slack[m]);
-                }
+                float sk;
+                byte |= eval(true, m, S1v[m], S2v[m], sk) << m;
+                minslack = fminf(minslack, sk);
             }
         } else {
 #pragma unroll
             for (int m = 0; m < kColsPerLane; m++) {
-                const float mu = __uint2float_rn(S1v[m]) * inv_nw;
-                const float var = v_float<S2T>(nw, (uint64_t)S2v[m], S1v[m]) * inv_n2;
-                const float s = sqrt_approx(var);
-                const float t = fmaf(fmaf(T.beta, mu, T.gamma), s, T.alpha * mu);
-                const float d = t - pixel_f(P, m);
-                byte |= (__float_as_uint(d) >> 31) << m;
-                if (MODE == MODE_FP64) {
-                    const float mag = fmaf(fmaf(T.abeta, mu, T.agamma), s, T.aalpha * mu);
-                    slack[m] = fabsf(d) - fmaf(T.eps, mag, T.delta64);
-                    minslack = fminf(minslack, slack[m]);
-                }
+                float sk;
+                byte |= eval(false, m, S1v[m], S2v[m], sk) << m;
+                minslack = fminf(minslack, sk);
             }
         }
         if (MODE == MODE_FP64 && __any_sync(0xFFFFFFFFu, !(minslack > 0.0f)) && !(minslack > 0.0f)) {
-            uint32_t undecided = 0;
-#pragma unroll
-            for (int m = 0; m < kColsPerLane; m++)
-                undecided |= (!(slack[m] > 0.0f) ? 1u : 0u) << m;
-#pragma unroll
+            // rare path: re-read the row's sums (volatile, so that the hot
+            // path keeps no copy alive), re-evaluate the 8 pixels and decide
+            // the uncertified ones in FP64
+            const volatile uint32_t *vs = reinterpret_cast<const volatile uint32_t *>(sl);
+            byte = 0;
             for (int m = 0; m < kColsPerLane; m++) {
-                if (undecided >> m & 1u) {
-                    const uint32_t b = fp64_bit(T.method, (uint32_t)byte_at(P, m), S1v[m],
-                                                (uint64_t)S2v[m], nw, T.k, T.R);
-                    byte = (byte & ~(1u << m)) | (b << m);
+                const uint32_t S1 = vs[((m >> 2) * 32 + lane) * 4 + (m & 3)];
+                const uint32_t S2 = vs[((2 + (m >> 2)) * 32 + lane) * 4 + (m & 3)];
+                float sk;
+                uint32_t b = eval(simple, m, S1, S2, sk);
+                if (!(sk > 0.0f)) {
+                    uint32_t n_m;
+                    float inv_m;
+                    count(m, n_m, inv_m);
+                    b = fp64_bit(T.method, (uint32_t)byte_at(P, m), S1, (uint64_t)S2, n_m, T.k, T.R);
+                    nfb++;
                 }
+                byte |= b << m;
             }
-            nfb += __popc(undecided);
         }
-        o.bits[(i - o.out_row0) * o.out_pitch + (j0 >> 3)] = (uint8_t)byte;
+        if (!EDGE)
+            o.bits[(i - o.out_row0) * o.out_pitch + (j0 >> 3)] = (uint8_t)byte;
+        else if (vmask)
+            o.bits[(i - o.out_row0) * o.out_pitch + (j0 >> 3)] = (uint8_t)(byte & vmask);
     };
 
-    auto centre = [&](int64_t i) { return __ldg(reinterpret_cast<const uint2 *>(g.img + i * g.pitch + j0)); };
+    auto centre = [&](int64_t i) {
+        if (EDGE)
+            return shift8(ld8_w3(g.img + i * g.pitch + pP, pP & 3, (unsigned)(pP & 3) * 0x1111u + 0x3210u),
+                          shift_of(2));
+        return __ldg(reinterpret_cast<const uint2 *>(g.img + i * g.pitch + j0));
+    };
 
     // prologue: row y0
     sums_to_slot(y0);
@@ -1024,9 +1129,22 @@ __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &w
     }
 }
 
+// Whether the pipelined path applies to a launch (host and device): binarize
+// modes, 32-bit S2, aligned 8-byte loads, W in [8, 2^30], and an anchor
+// window [x0 - l, x0 + r) that one word per lane covers: at most 128 bytes
+// from the word boundary below x0 - l (x0 is a multiple of 256; an edge
+// tile's clipped window starts at column 0 or there, and it is no wider).
+__host__ __device__ inline bool pipe_applies(int mode, bool vec, bool s2_32, const Image &g,
+                                             const Window &win)
+{
+    return (mode == MODE_FP64 || mode == MODE_FP32) && vec && s2_32 && g.W >= 8 &&
+           g.W <= ((int64_t)1 << 30) && win.w + ((4 - (win.l & 3)) & 3) <= 128 && win.l <= kTileCols;
+}
+
 // One warp computes the tile of columns [x0, x0+256) x rows [y0, y1).
-// PIPE: the caller provides 4 KB of shared memory per warp (`slots`) for the
-// pipelined interior path.
+// PIPE: the launch satisfies pipe_applies and the caller provides 6 KB of
+// shared memory per warp (`slots`); interior and edge tiles then both take
+// the pipelined path.  Otherwise window_rows.
 template <int MODE, bool VEC, typename S2T, bool PIPE, bool WARMB = false>
 __device__ __forceinline__ void window_tile(const Image &g, const Window &win, const Thresh &T,
                                             const Outputs &o, int64_t x0, int64_t y0, int64_t y1,
@@ -1035,13 +1153,13 @@ __device__ __forceinline__ void window_tile(const Image &g, const Window &win, c
     // interior: left edge stream of lane 0 and right edge stream of lane 31
     // inside the row, and the whole tile left of the last column
     const bool interior = VEC && (x0 - win.l >= 0) && (x0 + kTileCols + win.r <= g.W);
-    if (interior) {
-        // the pipelined path loads the anchor window as one word per lane
-        const bool one_word = win.w + ((4 - (win.l & 3)) & 3) <= 128;
-        if (PIPE && (MODE == MODE_FP64 || MODE == MODE_FP32) && sizeof(S2T) == 4 && one_word)
+    if (PIPE) {
+        if (interior)
             window_rows_pipe<MODE, WARMB>(g, win, T, o, x0, y0, y1, lane, slots, stripe);
         else
-            window_rows<MODE, VEC, true, S2T, false, WARMB>(g, win, T, o, x0, y0, y1, lane, stripe);
+            window_rows_pipe<MODE, WARMB, true>(g, win, T, o, x0, y0, y1, lane, slots, stripe);
+    } else if (interior) {
+        window_rows<MODE, VEC, true, S2T, false, WARMB>(g, win, T, o, x0, y0, y1, lane, stripe);
     } else {
         window_rows<MODE, VEC, false, S2T, false, WARMB>(g, win, T, o, x0, y0, y1, lane, stripe);
     }

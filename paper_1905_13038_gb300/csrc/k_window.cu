@@ -11,22 +11,50 @@ namespace bz {
 constexpr int kWarpsPerBlock = 4;
 constexpr int kBlocksPerSM = 4;  // 128 registers per thread
 
-template <int MODE, bool VEC, typename S2T, bool WARMB>
+// The tiles of one launch.  Edge tiles (the first and last tile columns)
+// clamp their byte streams and look up per-column counts, so they take
+// longer per row; with a one-wave grid the slowest warps set the launch's
+// duration.  A balanced schedule therefore gives the two edge columns
+// shorter tiles (edge_h < tile_h rows) and lists them first (n_edge tiles,
+// alternating left and right column); the uniform schedule has n_edge = 0
+// and every column in the tile_h grid.
+struct TileSched {
+    int64_t tiles_x, tile_h, edge_h, n_edge, tiles_total, row0, row1;
+};
+
+// PIPE: every tile takes the pipelined path (the host checked pipe_applies);
+// the two variants are separate kernels so that each gets its own register
+// allocation.  `stripes` (uniform schedules only): column sums at the first
+// row of every tile row.
+template <int MODE, bool VEC, typename S2T, bool WARMB, bool PIPE>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock, kBlocksPerSM)
-    k_window(Image g, Window win, Thresh T, Outputs o, int64_t tiles_x, int64_t tiles_total,
-             int64_t tile_h, int64_t row0, int64_t row1, const uint2 *stripes)
+    k_window(Image g, Window win, Thresh T, Outputs o, TileSched S, const uint2 *stripes)
 {
-    __shared__ uint4 slots[kWarpsPerBlock][256];  // 4 KB per warp (pipelined path)
+    __shared__ uint4 slots[kWarpsPerBlock][PIPE ? 384 : 1];  // 6 KB per warp (pipelined path)
     const int lane = threadIdx.x & 31;
     const int64_t wid = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
     const int64_t stride = (int64_t)gridDim.x * kWarpsPerBlock;
-    for (int64_t t = wid; t < tiles_total; t += stride) {
-        const int64_t tx = t % tiles_x, ty = t / tiles_x;
-        const int64_t x0 = tx * kTileCols, y0 = row0 + ty * tile_h;
-        const int64_t y1 = y0 + tile_h < row1 ? y0 + tile_h : row1;
-        window_tile<MODE, VEC, S2T, true, WARMB>(g, win, T, o, x0, y0, y1, lane,
-                                                  slots[threadIdx.x >> 5],
-                                                  stripes ? stripes + ty * g.W : nullptr);
+    for (int64_t t = wid; t < S.tiles_total; t += stride) {
+        int64_t tx, y0, y1;
+        const uint2 *st = nullptr;
+        if (t < S.n_edge) {
+            tx = (t & 1) ? S.tiles_x - 1 : 0;
+            y0 = S.row0 + (t >> 1) * S.edge_h;
+            y1 = y0 + S.edge_h;
+        } else {
+            const int64_t t2 = t - S.n_edge;
+            const int64_t ncol = S.n_edge ? S.tiles_x - 2 : S.tiles_x;
+            const int64_t ty = t2 / ncol;
+            tx = (S.n_edge ? 1 : 0) + (t2 - ty * ncol);
+            y0 = S.row0 + ty * S.tile_h;
+            y1 = y0 + S.tile_h;
+            if (stripes)
+                st = stripes + ty * g.W;
+        }
+        if (y1 > S.row1)
+            y1 = S.row1;
+        window_tile<MODE, VEC, S2T, PIPE, WARMB>(g, win, T, o, tx * kTileCols, y0, y1, lane,
+                                                  slots[threadIdx.x >> 5], st);
     }
 }
 
@@ -307,6 +335,15 @@ uint2 *launch_stripes(const Image &g, const Window &win, int64_t row0, int64_t t
     return stripes;
 }
 
+// Warps resident at once on this device (one wave of k_window).
+static int64_t resident_warps()
+{
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return (int64_t)sms * kBlocksPerSM * kWarpsPerBlock;
+}
+
 int64_t window_tile_rows(int64_t H, int64_t W, int h, int w)
 {
     (void)h;
@@ -323,12 +360,8 @@ int64_t window_tile_rows(int64_t H, int64_t W, int h, int w)
     }();
     if (env > 0)
         return env < H ? env : H;
-    int dev = 0, sms = 152;
-    if (cudaGetDevice(&dev) == cudaSuccess)
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t tiles_x = (W + kTileCols - 1) / kTileCols;
-    const int64_t warps = (int64_t)sms * kBlocksPerSM * kWarpsPerBlock;
-    int64_t bands = warps / tiles_x;
+    int64_t bands = resident_warps() / tiles_x;
     if (bands < 1)
         bands = 1;
     int64_t th = (H + bands - 1) / bands;
@@ -337,20 +370,72 @@ int64_t window_tile_rows(int64_t H, int64_t W, int h, int w)
     return th;
 }
 
+// Edge-tile height as a fraction of the interior height: the measured time
+// per row of an edge tile is about 1.2x an interior row's on the pipelined
+// path and 1.3-2x on the generic path (GB300, 4096 x 3072 page).
+// BZ_EDGE_FRAC overrides it (tuning; >= 1 disables the balanced schedule).
+static double edge_fraction(bool pipe)
+{
+    static const double env = [] {
+        const char *e = getenv("BZ_EDGE_FRAC");
+        return e ? atof(e) : 0.0;
+    }();
+    if (env > 0.0)
+        return env;
+    return pipe ? 0.82 : 0.7;
+}
+
+// The tile schedule of a launch over rows [row0, row1): one-wave interior
+// tiles, and for launches without stripe warm-up and with at least three
+// tile columns, shorter edge tiles as long as the whole grid stays one wave.
+static TileSched make_sched(const Image &g, const Window &win, int64_t row0, int64_t row1, bool pipe,
+                            bool stripes)
+{
+    TileSched S;
+    const int64_t rows = row1 - row0;
+    S.tiles_x = (g.W + kTileCols - 1) / kTileCols;
+    S.tile_h = window_tile_rows(rows, g.W, win.h, win.w);
+    S.edge_h = S.tile_h;
+    S.n_edge = 0;
+    S.row0 = row0;
+    S.row1 = row1;
+    const int64_t uniform = S.tiles_x * ((rows + S.tile_h - 1) / S.tile_h);
+    S.tiles_total = uniform;
+    const double f = edge_fraction(pipe);
+    if (!stripes && S.tiles_x >= 3 && f < 1.0 && S.tile_h > 4) {
+        const int64_t cap = uniform > resident_warps() ? uniform : resident_warps();
+        int64_t eh = (int64_t)((double)S.tile_h * f + 0.5);
+        eh = eh < 1 ? 1 : eh;
+        const int64_t ne = 2 * ((rows + eh - 1) / eh);
+        const int64_t total = ne + (S.tiles_x - 2) * ((rows + S.tile_h - 1) / S.tile_h);
+        if (eh < S.tile_h && total <= cap) {
+            S.edge_h = eh;
+            S.n_edge = ne;
+            S.tiles_total = total;
+        }
+    }
+    return S;
+}
+
 template <int MODE, bool VEC, typename S2T, bool WARMB>
 static cudaError_t launch_t(const Image &g, const Window &win, const Thresh &T, const Outputs &o,
                             int64_t row0, int64_t row1, cudaStream_t stream)
 {
-    const int64_t tile_h = window_tile_rows(row1 - row0, g.W, win.h, win.w);
-    const int64_t tiles_x = (g.W + kTileCols - 1) / kTileCols;
-    const int64_t tiles_y = (row1 - row0 + tile_h - 1) / tile_h;
-    const int64_t tiles = tiles_x * tiles_y;
-    int64_t blocks = (tiles + kWarpsPerBlock - 1) / kWarpsPerBlock;
+    constexpr bool kCanPipe = VEC && (MODE == MODE_FP64 || MODE == MODE_FP32) && sizeof(S2T) == 4;
+    const bool pipe = kCanPipe && pipe_applies(MODE, VEC, sizeof(S2T) == 4, g, win);
+    const int64_t tile_h0 = window_tile_rows(row1 - row0, g.W, win.h, win.w);
+    const int64_t tiles_y0 = (row1 - row0 + tile_h0 - 1) / tile_h0;
+    uint2 *stripes = launch_stripes(g, win, row0, tile_h0, tiles_y0, stream);
+    const TileSched S = make_sched(g, win, row0, row1, pipe, stripes != nullptr);
+    int64_t blocks = (S.tiles_total + kWarpsPerBlock - 1) / kWarpsPerBlock;
     if (blocks > 2147483647LL)
         blocks = 2147483647LL;
-    uint2 *stripes = launch_stripes(g, win, row0, tile_h, tiles_y, stream);
-    k_window<MODE, VEC, S2T, WARMB><<<(unsigned)blocks, 32 * kWarpsPerBlock, 0, stream>>>(
-        g, win, T, o, tiles_x, tiles, tile_h, row0, row1, stripes);
+    if (pipe)
+        k_window<MODE, VEC, S2T, WARMB, kCanPipe><<<(unsigned)blocks, 32 * kWarpsPerBlock, 0, stream>>>(
+            g, win, T, o, S, stripes);
+    else
+        k_window<MODE, VEC, S2T, WARMB, false><<<(unsigned)blocks, 32 * kWarpsPerBlock, 0, stream>>>(
+            g, win, T, o, S, stripes);
     cudaError_t e = cudaGetLastError();
     if (stripes && cudaFreeAsync(stripes, stream) != cudaSuccess && e == cudaSuccess)
         e = cudaGetLastError();

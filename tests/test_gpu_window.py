@@ -142,6 +142,40 @@ def test_invalid_arguments_rejected():
     assert e.value.status == 1
 
 
+# Pages tall enough for the window kernel (not the small-page kernel) whose
+# first and last tile columns run the pipelined path with clamped byte
+# streams: a partial last tile, a partial last byte, W < 256, W = 8, pitch > W,
+# stripe warm-up (h >= 48) and the batched warm-up of short tiles.
+EDGE_SHAPES = [
+    # H, W, pitch, h, w
+    (3000, 1000, 1000, 15, 15),
+    (2800, 1028, 1032, 31, 31),
+    (2600, 1100, 1104, 64, 9),
+    (2500, 700, 704, 9, 125),
+    (5000, 260, 264, 15, 31),
+    (20000, 12, 16, 5, 5),
+    (20000, 8, 8, 3, 3),
+    (600, 777, 784, 31, 127),
+]
+
+
+@pytest.mark.parametrize("H,W,pitch,h,w", EDGE_SHAPES)
+def test_edge_tiles_fp64_and_fp32(H, W, pitch, h, w):
+    import paper_1905_13038_gb300 as bz
+    img = image_for(H, W, 5 * H + W + h, pitch_extra=pitch - W)
+    t, _ = to_device(img, W)
+    for method, k in ((0, 0.5), (1, -0.2)):
+        fn = bz.binarize_sauvola if method == 0 else bz.binarize_niblack
+        args = (0.5, 128.0) if method == 0 else (-0.2,)
+        _, ref = oracle.binarize(method, img, h, w, k, 128.0, W=W)
+        out = out_buffer(H, W, extra=1)
+        fn(t, h, w, *args, out=out, precision="fp64", W=W)
+        check_packed(out, ref, W)
+        o32 = fn(t, h, w, *args, precision="fp32", W=W).cpu().numpy()
+        flips = int((unpack(o32, W) != unpack(ref, W)).sum())
+        assert flips <= max(2, 1e-5 * H * W), flips
+
+
 # ------------------------------------------------------------ full size ---
 LARGE_WINDOWS = [(15, 15), (63, 63), (255, 255), (31, 127)]
 
