@@ -57,16 +57,16 @@ __global__ void __launch_bounds__(32 * kBatchWarps)
         o.fallbacks = fallbacks;
         if (J.vec) {
             if (J.wide)
-                window_tile<MODE, true, unsigned long long, false>(J.g, J.win, J.T, o, x0, y0, y1, lane,
+                window_tile<MODE, true, unsigned long long, 0>(J.g, J.win, J.T, o, x0, y0, y1, lane,
                                                             nullptr);
             else
-                window_tile<MODE, true, uint32_t, false>(J.g, J.win, J.T, o, x0, y0, y1, lane, nullptr);
+                window_tile<MODE, true, uint32_t, 0>(J.g, J.win, J.T, o, x0, y0, y1, lane, nullptr);
         } else {
             if (J.wide)
-                window_tile<MODE, false, unsigned long long, false>(J.g, J.win, J.T, o, x0, y0, y1, lane,
+                window_tile<MODE, false, unsigned long long, 0>(J.g, J.win, J.T, o, x0, y0, y1, lane,
                                                              nullptr);
             else
-                window_tile<MODE, false, uint32_t, false>(J.g, J.win, J.T, o, x0, y0, y1, lane, nullptr);
+                window_tile<MODE, false, uint32_t, 0>(J.g, J.win, J.T, o, x0, y0, y1, lane, nullptr);
         }
     }
 }

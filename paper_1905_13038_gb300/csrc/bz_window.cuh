@@ -802,7 +802,7 @@ __device__ __forceinline__ uint2 shift8(uint2 v, int sh)
 // (edge_clamp), the anchor window is clipped to the row, and the per-column
 // counts and their reciprocals come from a per-warp table.
 // smem: 6144 bytes per warp (two 2 KB row slots, then the 2 KB column table).
-template <int MODE, bool WARMB = false, bool EDGE = false>
+template <int MODE, bool WARMB = false, bool EDGE = false, int AW = 1>
 __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &win, const Thresh &T,
                                                  const Outputs &o, int64_t x0, int64_t y0,
                                                  int64_t y1, int lane, uint4 *slots,
@@ -846,26 +846,36 @@ __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &w
     const float inv_h = __frcp_rn((float)win.h);
     const float inv_hw = inv_h * inv_w;
 
-    // anchor words: the caller guarantees (aend - a4) <= 128, one word per
-    // lane; lanes past the window read the first word and mask it to zero
+    // anchor words: the caller guarantees (aend - a4) <= 128 AW, AW words
+    // per lane (lane + 32 q); lanes past the window read the first word and
+    // mask it to zero
     int64_t ac0 = x0 - l, aend = x0 + r;
     if (EDGE) {  // clip the anchor window to the row
         ac0 = ac0 > 0 ? ac0 : 0;
         aend = aend < g.W ? aend : g.W;
     }
     const int64_t a4 = ac0 & ~(int64_t)3;  // ac0 >= 0 here
-    const int64_t c4 = a4 + 4 * lane;
-    const bool has_word = c4 < aend;
-    uint32_t keep = 0xFFFFFFFFu;
-    if (c4 < ac0)
-        keep &= 0xFFFFFFFFu << (8 * (int)(ac0 - c4));
-    if (c4 + 4 > aend)
-        keep = (c4 >= aend) ? 0u : (keep & (0xFFFFFFFFu >> (8 * (int)(c4 + 4 - aend))));
-    const int32_t aoff = (int32_t)(has_word ? c4 : a4);
+    uint32_t keep[AW];
+    int32_t aoff[AW];
+#pragma unroll
+    for (int q = 0; q < AW; q++) {
+        const int64_t c4 = a4 + 4 * (lane + 32 * q);
+        const bool has_word = c4 < aend;
+        uint32_t kp = 0xFFFFFFFFu;
+        if (c4 < ac0)
+            kp &= 0xFFFFFFFFu << (8 * (int)(ac0 - c4));
+        if (c4 + 4 > aend)
+            kp = (c4 >= aend) ? 0u : (kp & (0xFFFFFFFFu >> (8 * (int)(c4 + 4 - aend))));
+        keep[q] = kp;
+        aoff[q] = (int32_t)(has_word ? c4 : a4);
+    }
     auto anchor_row = [&](const uint8_t *rp, uint32_t &s1, uint32_t &s2) {
-        const uint32_t wd = __ldg(reinterpret_cast<const uint32_t *>(rp + aoff)) & keep;
-        s1 = __dp4a(wd, 0x01010101u, s1);
-        s2 = __dp4a(wd, wd, s2);
+#pragma unroll
+        for (int q = 0; q < AW; q++) {
+            const uint32_t wd = __ldg(reinterpret_cast<const uint32_t *>(rp + aoff[q])) & keep[q];
+            s1 = __dp4a(wd, 0x01010101u, s1);
+            s2 = __dp4a(wd, wd, s2);
+        }
     };
 
     // ---- warm-up (row y0), one row of look-ahead
@@ -1131,21 +1141,25 @@ __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &w
 
 // Whether the pipelined path applies to a launch (host and device): binarize
 // modes, 32-bit S2, aligned 8-byte loads, W in [8, 2^30], and an anchor
-// window [x0 - l, x0 + r) that one word per lane covers: at most 128 bytes
+// window [x0 - l, x0 + r) that AW words per lane cover: at most 128 AW bytes
 // from the word boundary below x0 - l (x0 is a multiple of 256; an edge
 // tile's clipped window starts at column 0 or there, and it is no wider).
-__host__ __device__ inline bool pipe_applies(int mode, bool vec, bool s2_32, const Image &g,
-                                             const Window &win)
+// Returns AW (1 or 2), or 0 when the path does not apply.
+__host__ __device__ inline int pipe_words(int mode, bool vec, bool s2_32, const Image &g,
+                                          const Window &win)
 {
-    return (mode == MODE_FP64 || mode == MODE_FP32) && vec && s2_32 && g.W >= 8 &&
-           g.W <= ((int64_t)1 << 30) && win.w + ((4 - (win.l & 3)) & 3) <= 128 && win.l <= kTileCols;
+    if (!((mode == MODE_FP64 || mode == MODE_FP32) && vec && s2_32 && g.W >= 8 &&
+          g.W <= ((int64_t)1 << 30) && win.l <= kTileCols))
+        return 0;
+    const int span = win.w + ((4 - (win.l & 3)) & 3);
+    return span <= 128 ? 1 : (span <= 256 ? 2 : 0);
 }
 
 // One warp computes the tile of columns [x0, x0+256) x rows [y0, y1).
-// PIPE: the launch satisfies pipe_applies and the caller provides 6 KB of
-// shared memory per warp (`slots`); interior and edge tiles then both take
-// the pipelined path.  Otherwise window_rows.
-template <int MODE, bool VEC, typename S2T, bool PIPE, bool WARMB = false>
+// AW > 0: the launch takes the pipelined path with AW anchor words per lane
+// (pipe_words) and the caller provides 6 KB of shared memory per warp
+// (`slots`); interior and edge tiles then both take it.  AW = 0: window_rows.
+template <int MODE, bool VEC, typename S2T, int AW, bool WARMB = false>
 __device__ __forceinline__ void window_tile(const Image &g, const Window &win, const Thresh &T,
                                             const Outputs &o, int64_t x0, int64_t y0, int64_t y1,
                                             int lane, uint4 *slots, const uint2 *stripe = nullptr)
@@ -1153,11 +1167,12 @@ __device__ __forceinline__ void window_tile(const Image &g, const Window &win, c
     // interior: left edge stream of lane 0 and right edge stream of lane 31
     // inside the row, and the whole tile left of the last column
     const bool interior = VEC && (x0 - win.l >= 0) && (x0 + kTileCols + win.r <= g.W);
-    if (PIPE) {
+    if (AW > 0) {
+        constexpr int kAW = AW > 0 ? AW : 1;
         if (interior)
-            window_rows_pipe<MODE, WARMB>(g, win, T, o, x0, y0, y1, lane, slots, stripe);
+            window_rows_pipe<MODE, WARMB, false, kAW>(g, win, T, o, x0, y0, y1, lane, slots, stripe);
         else
-            window_rows_pipe<MODE, WARMB, true>(g, win, T, o, x0, y0, y1, lane, slots, stripe);
+            window_rows_pipe<MODE, WARMB, true, kAW>(g, win, T, o, x0, y0, y1, lane, slots, stripe);
     } else if (interior) {
         window_rows<MODE, VEC, true, S2T, false, WARMB>(g, win, T, o, x0, y0, y1, lane, stripe);
     } else {

@@ -22,15 +22,15 @@ struct TileSched {
     int64_t tiles_x, tile_h, edge_h, n_edge, tiles_total, row0, row1;
 };
 
-// PIPE: every tile takes the pipelined path (the host checked pipe_applies);
-// the two variants are separate kernels so that each gets its own register
-// allocation.  `stripes` (uniform schedules only): column sums at the first
-// row of every tile row.
-template <int MODE, bool VEC, typename S2T, bool WARMB, bool PIPE>
+// AW > 0: every tile takes the pipelined path with AW anchor words per lane
+// (the host checked pipe_words); the variants are separate kernels so that
+// each gets its own register allocation.  `stripes` (uniform schedules only):
+// column sums at the first row of every tile row.
+template <int MODE, bool VEC, typename S2T, bool WARMB, int AW>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock, kBlocksPerSM)
     k_window(Image g, Window win, Thresh T, Outputs o, TileSched S, const uint2 *stripes)
 {
-    __shared__ uint4 slots[kWarpsPerBlock][PIPE ? 384 : 1];  // 6 KB per warp (pipelined path)
+    __shared__ uint4 slots[kWarpsPerBlock][AW ? 384 : 1];  // 6 KB per warp (pipelined path)
     const int lane = threadIdx.x & 31;
     const int64_t wid = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
     const int64_t stride = (int64_t)gridDim.x * kWarpsPerBlock;
@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, kBlocksPerSM)
         }
         if (y1 > S.row1)
             y1 = S.row1;
-        window_tile<MODE, VEC, S2T, PIPE, WARMB>(g, win, T, o, tx * kTileCols, y0, y1, lane,
+        window_tile<MODE, VEC, S2T, AW, WARMB>(g, win, T, o, tx * kTileCols, y0, y1, lane,
                                                   slots[threadIdx.x >> 5], st);
     }
 }
@@ -422,7 +422,8 @@ static cudaError_t launch_t(const Image &g, const Window &win, const Thresh &T, 
                             int64_t row0, int64_t row1, cudaStream_t stream)
 {
     constexpr bool kCanPipe = VEC && (MODE == MODE_FP64 || MODE == MODE_FP32) && sizeof(S2T) == 4;
-    const bool pipe = kCanPipe && pipe_applies(MODE, VEC, sizeof(S2T) == 4, g, win);
+    const int aw = kCanPipe ? pipe_words(MODE, VEC, sizeof(S2T) == 4, g, win) : 0;
+    const bool pipe = aw > 0;
     const int64_t tile_h0 = window_tile_rows(row1 - row0, g.W, win.h, win.w);
     const int64_t tiles_y0 = (row1 - row0 + tile_h0 - 1) / tile_h0;
     uint2 *stripes = launch_stripes(g, win, row0, tile_h0, tiles_y0, stream);
@@ -430,11 +431,14 @@ static cudaError_t launch_t(const Image &g, const Window &win, const Thresh &T, 
     int64_t blocks = (S.tiles_total + kWarpsPerBlock - 1) / kWarpsPerBlock;
     if (blocks > 2147483647LL)
         blocks = 2147483647LL;
-    if (pipe)
-        k_window<MODE, VEC, S2T, WARMB, kCanPipe><<<(unsigned)blocks, 32 * kWarpsPerBlock, 0, stream>>>(
+    if (aw == 1)
+        k_window<MODE, VEC, S2T, WARMB, kCanPipe ? 1 : 0><<<(unsigned)blocks, 32 * kWarpsPerBlock, 0, stream>>>(
+            g, win, T, o, S, stripes);
+    else if (aw == 2)
+        k_window<MODE, VEC, S2T, WARMB, kCanPipe ? 2 : 0><<<(unsigned)blocks, 32 * kWarpsPerBlock, 0, stream>>>(
             g, win, T, o, S, stripes);
     else
-        k_window<MODE, VEC, S2T, WARMB, false><<<(unsigned)blocks, 32 * kWarpsPerBlock, 0, stream>>>(
+        k_window<MODE, VEC, S2T, WARMB, 0><<<(unsigned)blocks, 32 * kWarpsPerBlock, 0, stream>>>(
             g, win, T, o, S, stripes);
     cudaError_t e = cudaGetLastError();
     if (stripes && cudaFreeAsync(stripes, stream) != cudaSuccess && e == cudaSuccess)

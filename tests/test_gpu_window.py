@@ -145,7 +145,8 @@ def test_invalid_arguments_rejected():
 # Pages tall enough for the window kernel (not the small-page kernel) whose
 # first and last tile columns run the pipelined path with clamped byte
 # streams: a partial last tile, a partial last byte, W < 256, W = 8, pitch > W,
-# stripe warm-up (h >= 48) and the batched warm-up of short tiles.
+# stripe warm-up (h >= 48), the batched warm-up of short tiles and anchors of
+# one and two words per lane.
 EDGE_SHAPES = [
     # H, W, pitch, h, w
     (3000, 1000, 1000, 15, 15),
@@ -156,6 +157,8 @@ EDGE_SHAPES = [
     (20000, 12, 16, 5, 5),
     (20000, 8, 8, 3, 3),
     (600, 777, 784, 31, 127),
+    (2500, 1000, 1000, 9, 201),   # two anchor words per lane
+    (700, 777, 784, 63, 255),     # two anchor words, stripe warm-up
 ]
 
 
