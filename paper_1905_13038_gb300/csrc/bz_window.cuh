@@ -89,6 +89,18 @@ __device__ __forceinline__ T warp_incl_scan(T v, int lane)
     return v;
 }
 
+// Programmatic dependent launch: the kernels of a binarization call are
+// launched so that each may be scheduled while the previous kernel in the
+// stream drains (launch_pdl).  A kernel first lets its own dependents be
+// scheduled, then waits until the previous grid has completed and its memory
+// is visible; nothing is read before that wait.  Without the launch attribute
+// both instructions are no-ops.
+__device__ __forceinline__ void pdl_begin()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 // ------------------------------------------------------------ threshold --
 // Canonical FP64 threshold: IEEE binary64, round to nearest, no contraction,
 // in the documented order.

@@ -23,6 +23,7 @@ __global__ void __launch_bounds__(kSmThreads)
 {
     __shared__ uint8_t R[kSmRows][kSmCols];
     __shared__ uint32_t P1[kSmTH][kSmCols], P2[kSmTH][kSmCols];
+    pdl_begin();
     const int tid = threadIdx.x;
     const int64_t x0 = (int64_t)(blockIdx.x % tiles_x) * kSmTW;
     const int64_t y0 = row0 + (int64_t)(blockIdx.x / tiles_x) * kSmTH;
@@ -141,17 +142,15 @@ cudaError_t launch_small(int mode, const Image &g, const Window &win, const Thre
         return cudaErrorInvalidValue;
     switch (mode) {
     case MODE_FP64:
-        k_small<MODE_FP64><<<(unsigned)tiles, kSmThreads, 0, stream>>>(g, win, T, o, tiles_x, row0, row1);
-        break;
+        return launch_pdl(k_small<MODE_FP64>, (unsigned)tiles, kSmThreads, stream, g, win, T, o, tiles_x, row0,
+                          row1);
     case MODE_FP32:
-        k_small<MODE_FP32><<<(unsigned)tiles, kSmThreads, 0, stream>>>(g, win, T, o, tiles_x, row0, row1);
-        break;
+        return launch_pdl(k_small<MODE_FP32>, (unsigned)tiles, kSmThreads, stream, g, win, T, o, tiles_x, row0,
+                          row1);
     default:
-        k_small<MODE_FP64_DIRECT><<<(unsigned)tiles, kSmThreads, 0, stream>>>(g, win, T, o, tiles_x, row0,
-                                                                              row1);
-        break;
+        return launch_pdl(k_small<MODE_FP64_DIRECT>, (unsigned)tiles, kSmThreads, stream, g, win, T, o, tiles_x,
+                          row0, row1);
     }
-    return cudaGetLastError();
 }
 
 }  // namespace bz

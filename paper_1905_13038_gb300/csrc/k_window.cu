@@ -31,6 +31,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, kBlocksPerSM)
     k_window(Image g, Window win, Thresh T, Outputs o, TileSched S, const uint2 *stripes)
 {
     __shared__ uint4 slots[kWarpsPerBlock][AW ? 384 : 1];  // 6 KB per warp (pipelined path)
+    pdl_begin();
     const int lane = threadIdx.x & 31;
     const int64_t wid = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
     const int64_t stride = (int64_t)gridDim.x * kWarpsPerBlock;
@@ -136,6 +137,7 @@ __global__ void __launch_bounds__(kStripeThreads)
     k_stripes(Image g, int o, int u, int64_t row0, int64_t tile_h, int64_t S, int64_t words,
               int group, uint2 *out)
 {
+    pdl_begin();
     const int64_t t = (int64_t)blockIdx.x * kStripeThreads + threadIdx.x;
     const int64_t q = t % words, s0 = (t / words) * group;
     if (s0 >= S)
@@ -198,6 +200,7 @@ __global__ void __launch_bounds__(kStripeThreads)
     k_stripe_chunks(Image g, int64_t p0, int64_t tile_h, int hm, int64_t K, int64_t words,
                     uint4 *QR)
 {
+    pdl_begin();
     const int64_t t = (int64_t)blockIdx.x * kStripeThreads + threadIdx.x;
     const int64_t q = t % words, k = t / words;
     if (k >= K)
@@ -234,6 +237,7 @@ __global__ void __launch_bounds__(kStripeThreads)
 __global__ void __launch_bounds__(kStripeThreads)
     k_stripe_slide(int64_t W, int64_t S, int m, int group, const uint4 *QR, uint2 *out)
 {
+    pdl_begin();
     const int64_t t = (int64_t)blockIdx.x * kStripeThreads + threadIdx.x;
     const int64_t x = t % W, s0 = (t / W) * group;
     if (s0 >= S)
@@ -309,30 +313,46 @@ uint2 *launch_stripes(const Image &g, const Window &win, int64_t row0, int64_t t
         uint4 *QR = reinterpret_cast<uint4 *>(reinterpret_cast<unsigned char *>(stripes) + sbytes);
         const int64_t p0 = row0 - win.o + 1;
         const int64_t b1 = (words * K + kStripeThreads - 1) / kStripeThreads;
-        if (vec4)
-            k_stripe_chunks<true><<<(unsigned)b1, kStripeThreads, 0, stream>>>(g, p0, tile_h, hm, K,
-                                                                               words, QR);
-        else
-            k_stripe_chunks<false><<<(unsigned)b1, kStripeThreads, 0, stream>>>(g, p0, tile_h, hm, K,
-                                                                                words, QR);
+        cudaError_t e = vec4 ? launch_pdl(k_stripe_chunks<true>, (unsigned)b1, kStripeThreads, stream, g, p0,
+                                          tile_h, hm, K, words, QR)
+                             : launch_pdl(k_stripe_chunks<false>, (unsigned)b1, kStripeThreads, stream, g, p0,
+                                          tile_h, hm, K, words, QR);
         const int sg = 8;  // tile starts per sliding thread
         const int64_t b2 = (g.W * ((tiles_y + sg - 1) / sg) + kStripeThreads - 1) / kStripeThreads;
-        k_stripe_slide<<<(unsigned)b2, kStripeThreads, 0, stream>>>(g.W, tiles_y, m, sg, QR, stripes);
+        if (e == cudaSuccess)
+            e = launch_pdl(k_stripe_slide, (unsigned)b2, kStripeThreads, stream, g.W, tiles_y, m, sg,
+                           (const uint4 *)QR, stripes);
+        if (e != cudaSuccess) {
+            cudaFreeAsync(stripes, stream);
+            return nullptr;
+        }
     } else {
         const int64_t threads = words * ((tiles_y + group - 1) / group);
         const int64_t sblocks = (threads + kStripeThreads - 1) / kStripeThreads;
-        if (vec4)
-            k_stripes<true><<<(unsigned)sblocks, kStripeThreads, 0, stream>>>(
-                g, win.o, win.u, row0, tile_h, tiles_y, words, group, stripes);
-        else
-            k_stripes<false><<<(unsigned)sblocks, kStripeThreads, 0, stream>>>(
-                g, win.o, win.u, row0, tile_h, tiles_y, words, group, stripes);
+        const cudaError_t e =
+            vec4 ? launch_pdl(k_stripes<true>, (unsigned)sblocks, kStripeThreads, stream, g, win.o, win.u, row0,
+                              tile_h, tiles_y, words, group, stripes)
+                 : launch_pdl(k_stripes<false>, (unsigned)sblocks, kStripeThreads, stream, g, win.o, win.u,
+                              row0, tile_h, tiles_y, words, group, stripes);
+        if (e != cudaSuccess) {
+            cudaFreeAsync(stripes, stream);
+            return nullptr;
+        }
     }
     if (cudaGetLastError() != cudaSuccess) {
         cudaFreeAsync(stripes, stream);
         return nullptr;
     }
     return stripes;
+}
+
+bool pdl_enabled()
+{
+    static const bool on = [] {
+        const char *e = getenv("BZ_PDL");
+        return !(e && atoi(e) == 0);
+    }();
+    return on;
 }
 
 // Warps resident at once on this device (one wave of k_window).
@@ -431,16 +451,17 @@ static cudaError_t launch_t(const Image &g, const Window &win, const Thresh &T, 
     int64_t blocks = (S.tiles_total + kWarpsPerBlock - 1) / kWarpsPerBlock;
     if (blocks > 2147483647LL)
         blocks = 2147483647LL;
+    const uint2 *cst = stripes;
+    cudaError_t e;
     if (aw == 1)
-        k_window<MODE, VEC, S2T, WARMB, kCanPipe ? 1 : 0><<<(unsigned)blocks, 32 * kWarpsPerBlock, 0, stream>>>(
-            g, win, T, o, S, stripes);
+        e = launch_pdl(k_window<MODE, VEC, S2T, WARMB, kCanPipe ? 1 : 0>, (unsigned)blocks, 32 * kWarpsPerBlock,
+                       stream, g, win, T, o, S, cst);
     else if (aw == 2)
-        k_window<MODE, VEC, S2T, WARMB, kCanPipe ? 2 : 0><<<(unsigned)blocks, 32 * kWarpsPerBlock, 0, stream>>>(
-            g, win, T, o, S, stripes);
+        e = launch_pdl(k_window<MODE, VEC, S2T, WARMB, kCanPipe ? 2 : 0>, (unsigned)blocks, 32 * kWarpsPerBlock,
+                       stream, g, win, T, o, S, cst);
     else
-        k_window<MODE, VEC, S2T, WARMB, 0><<<(unsigned)blocks, 32 * kWarpsPerBlock, 0, stream>>>(
-            g, win, T, o, S, stripes);
-    cudaError_t e = cudaGetLastError();
+        e = launch_pdl(k_window<MODE, VEC, S2T, WARMB, 0>, (unsigned)blocks, 32 * kWarpsPerBlock, stream, g, win,
+                       T, o, S, cst);
     if (stripes && cudaFreeAsync(stripes, stream) != cudaSuccess && e == cudaSuccess)
         e = cudaGetLastError();
     return e;
