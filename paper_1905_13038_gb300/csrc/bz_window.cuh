@@ -1167,15 +1167,43 @@ __host__ __device__ inline int pipe_words(int mode, bool vec, bool s2_32, const 
     return span <= 128 ? 1 : (span <= 256 ? 2 : 0);
 }
 
+// Ask L2 for every input byte a tile will read (rows y0 - o + 1 .. y1 - 1 + u,
+// columns x0 - l .. x0 + 255 + r, clipped to the image), one bulk prefetch
+// per row, so that the warm-up and slide loads of a launch whose image is not
+// in L2 yet wait for L2 rather than for HBM.  Each prefetched range is the
+// row's span rounded out to 16-byte blocks, which stay inside the blocks
+// that hold its first and last bytes.
+__device__ __forceinline__ void tile_prefetch_l2(const Image &g, const Window &win, int64_t x0, int64_t y0,
+                                                 int64_t y1, int lane)
+{
+    int64_t r0 = y0 - win.o + 1, r1 = y1 - 1 + win.u;  // inclusive
+    r0 = r0 < 0 ? 0 : r0;
+    r1 = r1 > g.H - 1 ? g.H - 1 : r1;
+    int64_t c0 = x0 - win.l, c1 = x0 + kTileCols + win.r;  // [c0, c1)
+    c0 = c0 < 0 ? 0 : c0;
+    c1 = c1 > g.W ? g.W : c1;
+    if (c0 >= c1)
+        return;
+    for (int64_t row = r0 + lane; row <= r1; row += 32) {
+        const uintptr_t a = reinterpret_cast<uintptr_t>(g.img + row * g.pitch + c0) & ~(uintptr_t)15;
+        const uintptr_t e = (reinterpret_cast<uintptr_t>(g.img + row * g.pitch + c1) + 15) & ~(uintptr_t)15;
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((unsigned)(e - a)) : "memory");
+    }
+}
+
 // One warp computes the tile of columns [x0, x0+256) x rows [y0, y1).
+// prefetch: start with tile_prefetch_l2.
 // AW > 0: the launch takes the pipelined path with AW anchor words per lane
 // (pipe_words) and the caller provides 6 KB of shared memory per warp
 // (`slots`); interior and edge tiles then both take it.  AW = 0: window_rows.
 template <int MODE, bool VEC, typename S2T, int AW, bool WARMB = false>
 __device__ __forceinline__ void window_tile(const Image &g, const Window &win, const Thresh &T,
                                             const Outputs &o, int64_t x0, int64_t y0, int64_t y1,
-                                            int lane, uint4 *slots, const uint2 *stripe = nullptr)
+                                            int lane, uint4 *slots, const uint2 *stripe = nullptr,
+                                            bool prefetch = false)
 {
+    if (prefetch)
+        tile_prefetch_l2(g, win, x0, y0, y1, lane);
     // interior: left edge stream of lane 0 and right edge stream of lane 31
     // inside the row, and the whole tile left of the last column
     const bool interior = VEC && (x0 - win.l >= 0) && (x0 + kTileCols + win.r <= g.W);

@@ -20,6 +20,7 @@ constexpr int kBlocksPerSM = 4;  // 128 registers per thread
 // and every column in the tile_h grid.
 struct TileSched {
     int64_t tiles_x, tile_h, edge_h, n_edge, tiles_total, row0, row1;
+    int prefetch;  // tiles start with an L2 prefetch of their input
 };
 
 // AW > 0: every tile takes the pipelined path with AW anchor words per lane
@@ -31,13 +32,12 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, kBlocksPerSM)
     k_window(Image g, Window win, Thresh T, Outputs o, TileSched S, const uint2 *stripes)
 {
     __shared__ uint4 slots[kWarpsPerBlock][AW ? 384 : 1];  // 6 KB per warp (pipelined path)
-    pdl_begin();
     const int lane = threadIdx.x & 31;
     const int64_t wid = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
     const int64_t stride = (int64_t)gridDim.x * kWarpsPerBlock;
-    for (int64_t t = wid; t < S.tiles_total; t += stride) {
-        int64_t tx, y0, y1;
-        const uint2 *st = nullptr;
+    // tile t: column tx, rows [y0, y1), stripe sums st
+    auto tile_of = [&](int64_t t, int64_t &tx, int64_t &y0, int64_t &y1, const uint2 *&st) {
+        st = nullptr;
         if (t < S.n_edge) {
             tx = (t & 1) ? S.tiles_x - 1 : 0;
             y0 = S.row0 + (t >> 1) * S.edge_h;
@@ -54,8 +54,24 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, kBlocksPerSM)
         }
         if (y1 > S.row1)
             y1 = S.row1;
+    };
+    // let the next kernel be scheduled; prefetch this warp's first tile
+    // into L2 while the previous kernel drains (a prefetch reads no result of
+    // it), then wait for that kernel
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    if (S.prefetch && wid < S.tiles_total) {
+        int64_t tx, y0, y1;
+        const uint2 *st;
+        tile_of(wid, tx, y0, y1, st);
+        tile_prefetch_l2(g, win, tx * kTileCols, y0, y1, lane);
+    }
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    for (int64_t t = wid; t < S.tiles_total; t += stride) {
+        int64_t tx, y0, y1;
+        const uint2 *st;
+        tile_of(t, tx, y0, y1, st);
         window_tile<MODE, VEC, S2T, AW, WARMB>(g, win, T, o, tx * kTileCols, y0, y1, lane,
-                                                  slots[threadIdx.x >> 5], st);
+                                                  slots[threadIdx.x >> 5], st, S.prefetch != 0 && t != wid);
     }
 }
 
@@ -419,19 +435,33 @@ static TileSched make_sched(const Image &g, const Window &win, int64_t row0, int
     S.n_edge = 0;
     S.row0 = row0;
     S.row1 = row1;
+    // without stripes the image is usually not in L2 yet (the stripe
+    // pre-pass has just read it otherwise).  BZ_PREFETCH=0 turns it off.
+    static const bool pf = [] {
+        const char *e = getenv("BZ_PREFETCH");
+        return !(e && atoi(e) == 0);
+    }();
+    S.prefetch = (pf && !stripes) ? 1 : 0;
     const int64_t uniform = S.tiles_x * ((rows + S.tile_h - 1) / S.tile_h);
     S.tiles_total = uniform;
     const double f = edge_fraction(pipe);
     if (!stripes && S.tiles_x >= 3 && f < 1.0 && S.tile_h > 4) {
+        // the shortest interior tiles (at most two rows taller than the
+        // uniform ones) whose grid, with edge tiles of f times their height,
+        // still fits in one wave
         const int64_t cap = uniform > resident_warps() ? uniform : resident_warps();
-        int64_t eh = (int64_t)((double)S.tile_h * f + 0.5);
-        eh = eh < 1 ? 1 : eh;
-        const int64_t ne = 2 * ((rows + eh - 1) / eh);
-        const int64_t total = ne + (S.tiles_x - 2) * ((rows + S.tile_h - 1) / S.tile_h);
-        if (eh < S.tile_h && total <= cap) {
-            S.edge_h = eh;
-            S.n_edge = ne;
-            S.tiles_total = total;
+        for (int64_t th = S.tile_h; th <= S.tile_h + 2; th++) {
+            int64_t eh = (int64_t)((double)th * f + 0.5);
+            eh = eh < 1 ? 1 : eh;
+            const int64_t ne = 2 * ((rows + eh - 1) / eh);
+            const int64_t total = ne + (S.tiles_x - 2) * ((rows + th - 1) / th);
+            if (eh < th && total <= cap) {
+                S.tile_h = th;
+                S.edge_h = eh;
+                S.n_edge = ne;
+                S.tiles_total = total;
+                break;
+            }
         }
     }
     return S;
