@@ -136,6 +136,14 @@ bz_status binarize_precision_report(int32_t method, const uint8_t *image,
                                     uint64_t *flips_dev,
                                     double *max_abs_dt_dev, void *stream);
 
+/* Number of kernels one binarize_sauvola / binarize_niblack call on an
+ * H x W image with an h x w window launches on the current device (the
+ * window kernel, plus the stripe pre-pass for tall windows: it depends on the
+ * device's SM count).  For planning graph captures and for counting launches;
+ * -1 for invalid arguments. */
+int32_t bz_kernels_per_call(int64_t H, int64_t W, int32_t h, int32_t w,
+                            bz_precision precision);
+
 /* Number of pixels the most recent BZ_FP64 call on this device could not
  * decide in FP32 and evaluated in FP64, read back synchronously after the
  * stream finishes.  Diagnostic only; returns -1 when unknown. */

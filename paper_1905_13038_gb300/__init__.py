@@ -20,7 +20,8 @@ from . import _build
 __all__ = [
     "build", "library_path", "FP64", "FP32", "FP64_DIRECT", "SAUVOLA", "NIBLACK", "QUANTILE",
     "BinarizeError", "binarize_sauvola", "binarize_niblack", "binarize_quantile", "window_sums",
-    "window_quantile", "binarize_precision_report", "last_fp64_fallbacks", "Job", "binarize_batch",
+    "window_quantile", "binarize_precision_report", "last_fp64_fallbacks", "kernels_per_call", "Job",
+    "binarize_batch",
     "binarize_batch_noalloc",
     "Server", "status_string",
     "WOLF", "FENG", "RAIS", "NICK", "PHANSALKAR", "binarize_wolf", "binarize_feng", "binarize_rais",
@@ -89,6 +90,7 @@ def _load():
         "window_quantile": ([P, i64, i64, i64, i32, i32, i32, i32, P, P], st),
         "binarize_precision_report": ([i32, P, i64, i64, i64, i32, i32, f64, f64, P, P, P], st),
         "bz_last_fp64_fallbacks": ([P], i64),
+        "bz_kernels_per_call": ([i64, i64, i32, i32, st], i32),
         "binarize_wolf": ([P, i64, i64, i64, i32, i32, f64, f64, P, i64, st, P], st),
         "binarize_feng": ([P, i64, i64, i64, i32, i32, f64, f64, f64, f64, f64, P, i64, st, P], st),
         "binarize_rais": ([P, i64, i64, i64, i32, i32, f64, P, i64, st, P], st),
@@ -394,6 +396,12 @@ def inplace_scratch_bytes(H: int, W: int, h: int, band_rows: int = 0) -> int:
 
 def last_fp64_fallbacks(stream=None) -> int:
     return int(_load().bz_last_fp64_fallbacks(_stream(stream)))
+
+
+def kernels_per_call(H: int, W: int, h: int, w: int, precision="fp64") -> int:
+    """Kernels one binarize_sauvola / binarize_niblack call launches on the
+    current device for this geometry (window kernel plus stripe pre-pass)."""
+    return int(_load().bz_kernels_per_call(H, W, h, w, _PREC[precision]))
 
 
 class Job:

@@ -732,6 +732,21 @@ int64_t bz_inplace_scratch_bytes(int64_t H, int64_t W, int32_t h, int64_t band_r
     return 2 * band * ((W + 7) / 8);
 }
 
+int32_t bz_kernels_per_call(int64_t H, int64_t W, int32_t h, int32_t w, bz_precision precision)
+{
+    if (H < 1 || W < 1 || h < 1 || w < 1)
+        return -1;
+    int mode;
+    switch (precision) {
+    case BZ_FP64: mode = MODE_FP64; break;
+    case BZ_FP32: mode = MODE_FP32; break;
+    case BZ_FP64_DIRECT: mode = MODE_FP64_DIRECT; break;
+    default: return -1;
+    }
+    const Image g{nullptr, H, W, (W + 7) & ~(int64_t)7};
+    return window_kernel_count(mode, g, make_window(h, w), 0, H);
+}
+
 int64_t bz_last_fp64_fallbacks(void *stream)
 {
     int dev = 0;

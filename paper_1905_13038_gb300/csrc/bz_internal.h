@@ -65,6 +65,8 @@ cudaError_t launch_window(int mode, const Image &g, const Window &win, const Thr
                           const Outputs &o, cudaStream_t stream);
 // The same over the output rows [row0, row1) only (windows still see the
 // whole image).
+// Kernels one launch_window_rows call enqueues (stripe pre-pass included).
+int window_kernel_count(int mode, const Image &g, const Window &win, int64_t row0, int64_t row1);
 cudaError_t launch_window_rows(int mode, const Image &g, const Window &win, const Thresh &T,
                                const Outputs &o, int64_t row0, int64_t row1, cudaStream_t stream);
 

@@ -289,7 +289,13 @@ static int stripe_group()
 
 // Windows at least this tall start their tiles from the stripe pre-pass
 // (measured on GB300; BZ_STRIPES=0/1 forces it off/on).
-static bool use_stripes(int h)
+// Stripes pay off once the window spans about five tile heights: each tile's
+// own warm-up reads h rows for tile_h output rows.  Measured on GB300 (4096 x
+// 3072 page, 21-row tiles): 63 x 63 64 us per call without stripes (the edge
+// columns then also get the balanced schedule) against 88 us with them;
+// 255 x 255 143 us without against 78 us with.  BZ_STRIPES=0/1 forces it
+// (tuning).
+static bool use_stripes(int h, int64_t tile_h)
 {
     static const int env = [] {
         const char *e = getenv("BZ_STRIPES");
@@ -297,13 +303,13 @@ static bool use_stripes(int h)
     }();
     if (env >= 0)
         return env != 0;
-    return h >= 48;
+    return h >= 48 && h >= 5 * tile_h;
 }
 
 uint2 *launch_stripes(const Image &g, const Window &win, int64_t row0, int64_t tile_h,
                       int64_t tiles_y, cudaStream_t stream)
 {
-    if (!use_stripes(win.h) || tiles_y <= 1)
+    if (!use_stripes(win.h, tile_h) || tiles_y <= 1)
         return nullptr;
     // chunked form when the window spans at least four tile heights (measured
     // on GB300: 255 x 255 86 vs 105 us; at 63 x 63, three tile heights, the
@@ -507,8 +513,13 @@ static cudaError_t launch_m(const Image &g, const Window &win, const Thresh &T, 
     const bool wide = (int64_t)win.h * win.w > 66051;  // S2 may reach 2^32
     // short tiles (a small image): the launch is latency-bound, so the
     // warm-up issues its loads in batches (binarize modes only)
+    static const int env_warmb = [] {  // BZ_WARMB=0/1 forces it (tuning)
+        const char *e = getenv("BZ_WARMB");
+        return e ? atoi(e) : -1;
+    }();
     const bool warmb = (MODE == MODE_FP64 || MODE == MODE_FP32) &&
-                       window_tile_rows(row1 - row0, g.W, win.h, win.w) <= 4;
+                       (env_warmb >= 0 ? env_warmb != 0
+                                       : window_tile_rows(row1 - row0, g.W, win.h, win.w) <= 4);
     constexpr bool kB = (MODE == MODE_FP64 || MODE == MODE_FP32);
     if (warmb) {
         if (vec)
@@ -537,6 +548,22 @@ cudaError_t launch_window_rows(int mode, const Image &g, const Window &win, cons
     case MODE_REPORT: return launch_m<MODE_REPORT>(g, win, T, o, row0, row1, stream);
     default: return cudaErrorInvalidValue;
     }
+}
+
+int window_kernel_count(int mode, const Image &g, const Window &win, int64_t row0, int64_t row1)
+{
+    if (small_path_applies(mode, g, win, row0, row1))
+        return 1;
+    const int64_t tile_h = window_tile_rows(row1 - row0, g.W, win.h, win.w);
+    const int64_t tiles_y = (row1 - row0 + tile_h - 1) / tile_h;
+    if (!use_stripes(win.h, tile_h) || tiles_y <= 1)
+        return 1;
+    static const int env_mode = [] {
+        const char *e = getenv("BZ_STRIPE_MODE");
+        return e ? atoi(e) : -1;
+    }();
+    const int m = (int)(win.h / tile_h);
+    return (env_mode >= 0 ? env_mode : (m >= 4 ? 1 : 0)) ? 3 : 2;
 }
 
 cudaError_t launch_window(int mode, const Image &g, const Window &win, const Thresh &T,

@@ -16,7 +16,7 @@ def declared_functions():
             continue
         text = open(os.path.join(ROOT, "include", fn)).read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-        for m in re.finditer(r"\b(?:bz_status|int64_t|const char\s*\*)\s*\**\s*(\w+)\s*\(", text):
+        for m in re.finditer(r"\b(?:bz_status|int64_t|int32_t|const char\s*\*)\s*\**\s*(\w+)\s*\(", text):
             names.add(m.group(1))
     return names
 
@@ -30,7 +30,7 @@ def test_header_declares_expected_entry_points():
               "binarize_rais", "binarize_nick", "binarize_phansalkar", "global_stats",
               "binarize_precision_report_ext", "binarize_batch_noalloc", "window_minmax",
               "binarize_bernsen", "haar_feature", "binarize_inplace", "bz_inplace_scratch_bytes",
-              "binarize_host"]:
+              "binarize_host", "bz_kernels_per_call"]:
         assert n in names, n
 
 
