@@ -211,6 +211,62 @@ __global__ void __launch_bounds__(kStripeThreads)
 // every chunk (Q_k) and its first h - m tile_h rows (R_k) in parallel, each
 // image row read once per column; phase 2 slides a window of m chunk sums down
 // each column: C(s) = sum_{k=s}^{s+m-1} Q_k + R_{s+m}.
+// Column sums of 4 columns over a run of rows, packed: the sums of columns
+// 0 and 2 (lo) and 1 and 3 (hi) in 16-bit halves, valid for up to 257 rows;
+// the sums of squares per column (one dp4a each, the word times the word
+// with one byte kept).
+struct PackedSums {
+    uint32_t lo = 0u, hi = 0u, d[4] = {0u, 0u, 0u, 0u};
+    __device__ __forceinline__ void add(uint32_t wd)
+    {
+        lo += wd & 0x00FF00FFu;
+        hi += (wd >> 8) & 0x00FF00FFu;
+#pragma unroll
+        for (int b = 0; b < 4; b++)
+            d[b] = __dp4a(wd, wd & (0xFFu << (8 * b)), d[b]);
+    }
+    // move the packed column sums into 32-bit C and reset them
+    __device__ __forceinline__ void flush(uint32_t (&C)[4])
+    {
+        C[0] += lo & 0xFFFFu;
+        C[2] += lo >> 16;
+        C[1] += hi & 0xFFFFu;
+        C[3] += hi >> 16;
+        lo = hi = 0u;
+    }
+};
+
+// Sums of the rows [r0, r1) (inside the image) of the 4 columns at x into
+// C (flushed) and D, loads issued 8 rows at a time.
+template <bool VEC4>
+__device__ __forceinline__ void stripe_rows(const Image &g, int64_t x, int64_t r0, int64_t r1, uint32_t (&C)[4],
+                                            uint32_t (&D)[4])
+{
+    PackedSums P;
+    int run = 0;  // rows in the packed sums
+    int64_t r = r0;
+    for (; r + 8 <= r1; r += 8) {
+        uint32_t wd[8];
+#pragma unroll
+        for (int j = 0; j < 8; j++)
+            wd[j] = stripe_word<VEC4>(g, r + j, x);
+#pragma unroll
+        for (int j = 0; j < 8; j++)
+            P.add(wd[j]);
+        run += 8;
+        if (run >= 248) {
+            P.flush(C);
+            run = 0;
+        }
+    }
+    for (; r < r1; r++)
+        P.add(stripe_word<VEC4>(g, r, x));
+    P.flush(C);
+#pragma unroll
+    for (int b = 0; b < 4; b++)
+        D[b] += P.d[b];
+}
+
 template <bool VEC4>
 __global__ void __launch_bounds__(kStripeThreads)
     k_stripe_chunks(Image g, int64_t p0, int64_t tile_h, int hm, int64_t K, int64_t words,
@@ -222,57 +278,82 @@ __global__ void __launch_bounds__(kStripeThreads)
     if (k >= K)
         return;
     const int64_t x = 4 * q;
+    // chunk rows [pk, pk + tile_h) and its first hm rows, clipped to the
+    // image (rows outside it are zero)
+    const int64_t pk = p0 + k * tile_h;
+    const int64_t a0 = pk > 0 ? pk : 0;
+    const int64_t a1 = pk + tile_h < g.H ? pk + tile_h : g.H;
+    int64_t am = pk + hm;
+    am = am < a0 ? a0 : (am > a1 ? a1 : am);
     uint32_t C[4] = {0u, 0u, 0u, 0u}, D[4] = {0u, 0u, 0u, 0u};
     uint32_t RC[4] = {0u, 0u, 0u, 0u}, RD[4] = {0u, 0u, 0u, 0u};
-    const int64_t pk = p0 + k * tile_h;
-    for (int64_t a = 0; a < tile_h; a += kStripeBatch) {
-        uint32_t wd[kStripeBatch];
+    if (a0 < am)
+        stripe_rows<VEC4>(g, x, a0, am, C, D);
 #pragma unroll
-        for (int j = 0; j < kStripeBatch; j++) {
-            const int64_t r = pk + a + j;
-            wd[j] = (a + j < tile_h && r >= 0 && r < g.H) ? stripe_word<VEC4>(g, r, x) : 0u;
-        }
-#pragma unroll
-        for (int j = 0; j < kStripeBatch; j++) {
-            if (a + j == hm) {  // R: the sums of the first hm rows
-#pragma unroll
-                for (int b = 0; b < 4; b++) {
-                    RC[b] = C[b];
-                    RD[b] = D[b];
-                }
-            }
-            stripe_acc(C, D, wd[j], 1);
-        }
+    for (int b = 0; b < 4; b++) {
+        RC[b] = C[b];
+        RD[b] = D[b];
     }
+    if (am < a1)
+        stripe_rows<VEC4>(g, x, am, a1, C, D);
 #pragma unroll
     for (int b = 0; b < 4; b++)
         if (x + b < g.W)
             QR[k * g.W + x + b] = make_uint4(C[b], D[b], RC[b], RD[b]);
 }
 
+// Phase 2: one thread per column and G consecutive tile starts; the loads of
+// its G starts are independent of the running sums, so they are issued
+// together.
+template <int G>
 __global__ void __launch_bounds__(kStripeThreads)
-    k_stripe_slide(int64_t W, int64_t S, int m, int group, const uint4 *QR, uint2 *out)
+    k_stripe_slide(int64_t W, int64_t S, int m, const uint4 *QR, uint2 *out)
 {
     pdl_begin();
     const int64_t t = (int64_t)blockIdx.x * kStripeThreads + threadIdx.x;
-    const int64_t x = t % W, s0 = (t / W) * group;
+    const int64_t x = t % W, s0 = (t / W) * G;
     if (s0 >= S)
         return;
-    const int64_t s1 = s0 + group < S ? s0 + group : S;
     uint32_t c = 0, d = 0;
-    for (int k = 0; k < m; k++) {
+    int k = 0;
+    for (; k + 4 <= m; k += 4) {
+        uint4 v[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+            v[j] = __ldg(QR + (s0 + k + j) * W + x);
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            c += v[j].x;
+            d += v[j].y;
+        }
+    }
+    for (; k < m; k++) {
         const uint4 v = __ldg(QR + (s0 + k) * W + x);
         c += v.x;
         d += v.y;
     }
-    for (int64_t s = s0; s < s1; s++) {
-        if (s > s0) {
-            const uint4 vin = __ldg(QR + (s + m - 1) * W + x), vout = __ldg(QR + (s - 1) * W + x);
-            c += vin.x - vout.x;
-            d += vin.y - vout.y;
+    uint4 vin[G], vout[G], rr[G];
+#pragma unroll
+    for (int j = 0; j < G; j++) {
+        const int64_t s = s0 + j;
+        if (s < S) {
+            rr[j] = __ldg(QR + (s + m) * W + x);
+            if (j > 0) {
+                vin[j] = __ldg(QR + (s + m - 1) * W + x);
+                vout[j] = __ldg(QR + (s - 1) * W + x);
+            }
         }
-        const uint4 r = __ldg(QR + (s + m) * W + x);
-        out[s * W + x] = make_uint2(c + r.z, d + r.w);
+    }
+#pragma unroll
+    for (int j = 0; j < G; j++) {
+        const int64_t s = s0 + j;
+        if (s < S) {
+            if (j > 0) {
+                c += vin[j].x - vout[j].x;
+                d += vin[j].y - vout[j].y;
+            }
+            out[s * W + x] = make_uint2(c + rr[j].z, d + rr[j].w);
+        }
     }
 }
 
@@ -339,10 +420,10 @@ uint2 *launch_stripes(const Image &g, const Window &win, int64_t row0, int64_t t
                                           tile_h, hm, K, words, QR)
                              : launch_pdl(k_stripe_chunks<false>, (unsigned)b1, kStripeThreads, stream, g, p0,
                                           tile_h, hm, K, words, QR);
-        const int sg = 8;  // tile starts per sliding thread
+        constexpr int sg = 8;  // tile starts per sliding thread
         const int64_t b2 = (g.W * ((tiles_y + sg - 1) / sg) + kStripeThreads - 1) / kStripeThreads;
         if (e == cudaSuccess)
-            e = launch_pdl(k_stripe_slide, (unsigned)b2, kStripeThreads, stream, g.W, tiles_y, m, sg,
+            e = launch_pdl(k_stripe_slide<sg>, (unsigned)b2, kStripeThreads, stream, g.W, tiles_y, m,
                            (const uint4 *)QR, stripes);
         if (e != cudaSuccess) {
             cudaFreeAsync(stripes, stream);
