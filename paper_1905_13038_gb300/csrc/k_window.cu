@@ -237,30 +237,31 @@ struct PackedSums {
 };
 
 // Sums of the rows [r0, r1) (inside the image) of the 4 columns at x into
-// C (flushed) and D, loads issued 8 rows at a time.
+// C (flushed) and D.  The loads of up to kChunkBatch rows are issued
+// together (the pre-pass is bound by memory latency: one round trip per
+// batch), the rows past r1 predicated off.
+constexpr int kChunkBatch = 24;
+
 template <bool VEC4>
 __device__ __forceinline__ void stripe_rows(const Image &g, int64_t x, int64_t r0, int64_t r1, uint32_t (&C)[4],
                                             uint32_t (&D)[4])
 {
     PackedSums P;
-    int run = 0;  // rows in the packed sums
-    int64_t r = r0;
-    for (; r + 8 <= r1; r += 8) {
-        uint32_t wd[8];
+    int run = 0;  // rows in the packed sums (flushed at 240 < 257)
+    for (int64_t r = r0; r < r1; r += kChunkBatch) {
+        uint32_t wd[kChunkBatch];
 #pragma unroll
-        for (int j = 0; j < 8; j++)
-            wd[j] = stripe_word<VEC4>(g, r + j, x);
+        for (int j = 0; j < kChunkBatch; j++)
+            wd[j] = r + j < r1 ? stripe_word<VEC4>(g, r + j, x) : 0u;
 #pragma unroll
-        for (int j = 0; j < 8; j++)
+        for (int j = 0; j < kChunkBatch; j++)
             P.add(wd[j]);
-        run += 8;
-        if (run >= 248) {
+        run += kChunkBatch;
+        if (run >= 240) {
             P.flush(C);
             run = 0;
         }
     }
-    for (; r < r1; r++)
-        P.add(stripe_word<VEC4>(g, r, x));
     P.flush(C);
 #pragma unroll
     for (int b = 0; b < 4; b++)
@@ -315,22 +316,21 @@ __global__ void __launch_bounds__(kStripeThreads)
     if (s0 >= S)
         return;
     uint32_t c = 0, d = 0;
-    int k = 0;
-    for (; k + 4 <= m; k += 4) {
-        uint4 v[4];
+    for (int k = 0; k < m; k += 16) {  // 16 chunk sums per round trip
+        uint2 v[16];
 #pragma unroll
-        for (int j = 0; j < 4; j++)
-            v[j] = __ldg(QR + (s0 + k + j) * W + x);
+        for (int j = 0; j < 16; j++) {
+            v[j] = make_uint2(0u, 0u);
+            if (k + j < m) {
+                const uint4 q = __ldg(QR + (s0 + k + j) * W + x);
+                v[j] = make_uint2(q.x, q.y);
+            }
+        }
 #pragma unroll
-        for (int j = 0; j < 4; j++) {
+        for (int j = 0; j < 16; j++) {
             c += v[j].x;
             d += v[j].y;
         }
-    }
-    for (; k < m; k++) {
-        const uint4 v = __ldg(QR + (s0 + k) * W + x);
-        c += v.x;
-        d += v.y;
     }
     uint4 vin[G], vout[G], rr[G];
 #pragma unroll
