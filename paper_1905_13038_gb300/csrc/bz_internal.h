@@ -53,12 +53,15 @@ bool small_path_applies(int mode, const Image &g, const Window &win, int64_t row
 cudaError_t launch_small(int mode, const Image &g, const Window &win, const Thresh &T,
                          const Outputs &o, int64_t row0, int64_t row1, cudaStream_t stream);
 
-// Stripe pre-pass on `stream` for windows of 48 rows or more: (C, D) column
+// Stripe pre-pass on `stream` for windows of at least 48 rows spanning five
+// or more tile heights: (C, D) column
 // sums at every tile start row0 + s * tile_h, s < tiles_y, in a stream-ordered
 // scratch of tiles_y * W uint2 that the caller frees on the stream after the
 // window kernel; nullptr when not used or not available.
 uint2 *launch_stripes(const Image &g, const Window &win, int64_t row0, int64_t tile_h,
                       int64_t tiles_y, cudaStream_t stream);
+// Kernels launch_stripes enqueues for this geometry (0: no stripes).
+int stripe_kernel_count(const Window &win, int64_t tile_h, int64_t tiles_y);
 
 // Launches of the window path; mode is a bz::Mode.
 cudaError_t launch_window(int mode, const Image &g, const Window &win, const Thresh &T,
