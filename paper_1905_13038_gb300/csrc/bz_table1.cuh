@@ -84,9 +84,11 @@ __device__ __forceinline__ double canonical_t_ext(int method, uint32_t S1, uint6
 {
     const long long V = (long long)n * (long long)S2 - (long long)S1 * (long long)S1;
     const double nd = __uint2double_rn(n);
-    const double m = __ddiv_rn(__uint2double_rn(S1), nd);
-    const double v = __ddiv_rn(__ll2double_rn(V), __dmul_rn(nd, nd));
-    const double s = __dsqrt_rn(v);
+    // V = 0: all in-image pixels of the window are equal, so the quotients
+    // below are exact (m = S1 / n, v = s = +0) and need no FP64 division
+    const double m = V == 0 ? __uint2double_rn(S1 / n) : __ddiv_rn(__uint2double_rn(S1), nd);
+    const double v = V == 0 ? 0.0 : __ddiv_rn(__ll2double_rn(V), __dmul_rn(nd, nd));
+    const double s = V == 0 ? 0.0 : __dsqrt_rn(v);
     switch (method) {
     case METHOD_WOLF:
         return __dadd_rn(m, -__dmul_rn(__dmul_rn(k, __dadd_rn(m, -G.L)),

@@ -108,6 +108,16 @@ __device__ __forceinline__ double canonical_t(int method, uint32_t S1, uint64_t 
                                               double k, double R)
 {
     const long long V = (long long)n * (long long)S2 - (long long)S1 * (long long)S1;
+    if (V == 0) {
+        // every in-image pixel of the window has the value S1 / n (equality
+        // in the Cauchy-Schwarz inequality n S2 >= S1^2), so the canonical
+        // sequence has m = S1 / n exactly, v = s = +0 and 0/R = +0: no
+        // division or square root is left (the same doubles as below)
+        const double m = __uint2double_rn(S1 / n);
+        if (method == 0)
+            return __dmul_rn(m, __dadd_rn(1.0, __dmul_rn(k, -1.0)));
+        return __dadd_rn(m, __dmul_rn(k, 0.0));
+    }
     const double nd = __uint2double_rn(n);
     const double m = __ddiv_rn(__uint2double_rn(S1), nd);
     const double s = __dsqrt_rn(__ddiv_rn(__ll2double_rn(V), __dmul_rn(nd, nd)));
@@ -813,7 +823,8 @@ __device__ __forceinline__ uint2 shift8(uint2 v, int sh)
 // narrower than a tile): streams that leave the row are clamped and shifted
 // (edge_clamp), the anchor window is clipped to the row, and the per-column
 // counts and their reciprocals come from a per-warp table.
-// smem: 6144 bytes per warp (two 2 KB row slots, then the 2 KB column table).
+// smem: 6656 bytes per warp (two 2 KB row slots, the 2 KB column table, and
+// 512 bytes for the FP64 near-tie list and its results).
 template <int MODE, bool WARMB = false, bool EDGE = false, int AW = 1>
 __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &win, const Thresh &T,
                                                  const Outputs &o, int64_t x0, int64_t y0,
@@ -1041,9 +1052,9 @@ __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &w
                                                      : __frcp_rn((float)rows) * (EDGE ? 1.0f : inv_w);
         // count and 1/count of column m: the window width (interior tiles) or
         // the table entry (edge tiles)
-        auto count = [&](int m, uint32_t &n_m, float &inv_m) {
+        auto count_of = [&](int ln, int m, uint32_t &n_m, float &inv_m) {
             if (EDGE) {
-                const uint2 e = ctab[m * 32 + lane];
+                const uint2 e = ctab[m * 32 + ln];
                 n_m = nrow * e.y;
                 inv_m = inv_nw * __uint_as_float(e.x);
             } else {
@@ -1051,6 +1062,7 @@ __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &w
                 inv_m = inv_nw;
             }
         };
+        auto count = [&](int m, uint32_t &n_m, float &inv_m) { count_of(lane, m, n_m, inv_m); };
         // FP32 threshold of pixel m: returns its bit and sets `slack` =
         // |d| - E, certified when > 0 (columns past the row count as
         // certified).  SIMPLE: Sauvola with alpha, beta >= 0 (mag = t).
@@ -1093,26 +1105,60 @@ __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &w
                 minslack = fminf(minslack, sk);
             }
         }
-        if (MODE == MODE_FP64 && __any_sync(0xFFFFFFFFu, !(minslack > 0.0f)) && !(minslack > 0.0f)) {
-            // rare path: re-read the row's sums (volatile, so that the hot
-            // path keeps no copy alive), re-evaluate the 8 pixels and decide
-            // the uncertified ones in FP64
+        if (MODE == MODE_FP64 && __any_sync(0xFFFFFFFFu, !(minslack > 0.0f))) {
+            // rare path (the whole warp): the lanes with an uncertified pixel
+            // re-read the row's sums (volatile, so that the hot path keeps no
+            // copy alive) and re-evaluate their 8 pixels; the uncertified
+            // ones are then decided in FP64, spread over the lanes of the
+            // warp (up to 32 per round), since FP64 is slow and such pixels
+            // come in clusters (flat or saturated areas)
+            __syncwarp();  // the slot and the column table are read across lanes
             const volatile uint32_t *vs = reinterpret_cast<const volatile uint32_t *>(sl);
-            byte = 0;
-            for (int m = 0; m < kColsPerLane; m++) {
-                const uint32_t S1 = vs[((m >> 2) * 32 + lane) * 4 + (m & 3)];
-                const uint32_t S2 = vs[((2 + (m >> 2)) * 32 + lane) * 4 + (m & 3)];
-                float sk;
-                uint32_t b = eval(simple, m, S1, S2, sk);
-                if (!(sk > 0.0f)) {
+            uint32_t und = 0;
+            if (!(minslack > 0.0f)) {
+                byte = 0;
+                for (int m = 0; m < kColsPerLane; m++) {
+                    const uint32_t S1 = vs[((m >> 2) * 32 + lane) * 4 + (m & 3)];
+                    const uint32_t S2 = vs[((2 + (m >> 2)) * 32 + lane) * 4 + (m & 3)];
+                    float sk;
+                    const uint32_t b = eval(simple, m, S1, S2, sk);
+                    if (sk > 0.0f)
+                        byte |= b << m;
+                    else
+                        und |= 1u << m;
+                }
+            }
+            // the warp's list of uncertified (lane, pixel) pairs and their bits
+            uint8_t *list = reinterpret_cast<uint8_t *>(slots + 384);
+            uint8_t *res = list + 256;
+            const uint32_t cnt = (uint32_t)__popc(und);
+            const uint32_t incl = warp_incl_scan<uint32_t>(cnt, lane);
+            const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+            uint32_t at = incl - cnt;
+            for (uint32_t u2 = und; u2; u2 &= u2 - 1)
+                list[at++] = (uint8_t)(lane * 8 + (__ffs(u2) - 1));
+            __syncwarp();
+            for (uint32_t r0 = 0; r0 < total; r0 += 32) {
+                const uint32_t e = r0 + lane < total ? list[r0 + lane] : (uint32_t)(lane * 8);
+                const int own = (int)(e >> 3), m = (int)(e & 7u);
+                const uint2 Pown = make_uint2(__shfl_sync(0xFFFFFFFFu, P.x, own), __shfl_sync(0xFFFFFFFFu, P.y, own));
+                if (r0 + lane < total) {
+                    const uint32_t S1 = vs[((m >> 2) * 32 + own) * 4 + (m & 3)];
+                    const uint32_t S2 = vs[((2 + (m >> 2)) * 32 + own) * 4 + (m & 3)];
                     uint32_t n_m;
                     float inv_m;
-                    count(m, n_m, inv_m);
-                    b = fp64_bit(T.method, (uint32_t)byte_at(P, m), S1, (uint64_t)S2, n_m, T.k, T.R);
-                    nfb++;
+                    count_of(own, m, n_m, inv_m);
+                    res[e] = (uint8_t)fp64_bit(T.method, (uint32_t)byte_at(Pown, m), S1, (uint64_t)S2, n_m, T.k,
+                                               T.R);
                 }
-                byte |= b << m;
             }
+            __syncwarp();
+            for (uint32_t u2 = und; u2; u2 &= u2 - 1) {
+                const int m = __ffs(u2) - 1;
+                byte |= (uint32_t)res[lane * 8 + m] << m;
+            }
+            nfb += cnt;
+            __syncwarp();  // the list is rewritten by the next row
         }
         if (!EDGE)
             o.bits[(i - o.out_row0) * o.out_pitch + (j0 >> 3)] = (uint8_t)byte;
@@ -1194,7 +1240,7 @@ __device__ __forceinline__ void tile_prefetch_l2(const Image &g, const Window &w
 // One warp computes the tile of columns [x0, x0+256) x rows [y0, y1).
 // prefetch: start with tile_prefetch_l2.
 // AW > 0: the launch takes the pipelined path with AW anchor words per lane
-// (pipe_words) and the caller provides 6 KB of shared memory per warp
+// (pipe_words) and the caller provides 6.5 KB of shared memory per warp
 // (`slots`); interior and edge tiles then both take it.  AW = 0: window_rows.
 template <int MODE, bool VEC, typename S2T, int AW, bool WARMB = false>
 __device__ __forceinline__ void window_tile(const Image &g, const Window &win, const Thresh &T,
