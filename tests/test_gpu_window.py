@@ -105,6 +105,26 @@ def test_constant_and_checkerboard_ties():
     check_packed(bz.binarize_niblack(t, 4, 4, 0.3), oracle.niblack(cb, 4, 4, k=0.3)[1], W)
 
 
+@pytest.mark.parametrize("H,W", [(3000, 1000), (60, 300)])
+@pytest.mark.parametrize("precision", ["fp64", "fp64_direct"])
+def test_flat_and_saturated_regions(H, W, precision):
+    """Large constant areas (0, 255 and a mid gray) beside noisy text: windows
+    with V = 0 and clusters of near-ties, decided in FP64 (spread over the
+    warp in the window kernel); Sauvola with k > 0, k < 0 and a k so small
+    that 1 - k rounds to 1, and Niblack."""
+    import paper_1905_13038_gb300 as bz
+    img = synth.document(H, W, 99 + H, stains=1)
+    img[: H // 3, : W // 2] = 0
+    img[H // 3: 2 * H // 3, W // 3:] = 255
+    img[2 * H // 3:, : W // 4] = 128
+    t, _ = to_device(img)
+    for k in (0.5, -0.1, 1e-18):
+        out = bz.binarize_sauvola(t, 15, 31, k, 128.0, precision=precision)
+        check_packed(out, oracle.sauvola(img, 15, 31, k=k)[1], W)
+    out = bz.binarize_niblack(t, 15, 31, -0.2, precision=precision)
+    check_packed(out, oracle.niblack(img, 15, 31, k=-0.2)[1], W)
+
+
 def test_fp32_path_and_report_small():
     import paper_1905_13038_gb300 as bz
     img = image_for(400, 900, 9)
