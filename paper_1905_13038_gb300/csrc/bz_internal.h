@@ -63,6 +63,11 @@ uint2 *launch_stripes(const Image &g, const Window &win, int64_t row0, int64_t t
 // Kernels launch_stripes enqueues for this geometry (0: no stripes).
 int stripe_kernel_count(const Window &win, int64_t tile_h, int64_t tiles_y);
 
+// The tile schedule of a window-kernel launch over rows [row0, row1): one-wave
+// interior tiles and, without stripes, shorter edge tiles (pipe: the edge
+// tiles take the pipelined path, else the generic one).
+TileSched make_sched(const Image &g, const Window &win, int64_t row0, int64_t row1, bool pipe, bool stripes);
+
 // Launches of the window path; mode is a bz::Mode.
 cudaError_t launch_window(int mode, const Image &g, const Window &win, const Thresh &T,
                           const Outputs &o, cudaStream_t stream);

@@ -1197,6 +1197,42 @@ __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &w
     }
 }
 
+// The tiles of one launch.  Edge tiles (the first and last tile columns)
+// clamp their byte streams and look up per-column counts, or take the
+// generic path, so they take longer per row; with a one-wave grid the
+// slowest warps set the launch's duration.  A balanced schedule therefore
+// gives the two edge columns shorter tiles (edge_h < tile_h rows) and lists
+// them first (n_edge tiles, alternating left and right column); the uniform
+// schedule has n_edge = 0 and every column in the tile_h grid.
+struct TileSched {
+    int64_t tiles_x, tile_h, edge_h, n_edge, tiles_total, row0, row1;
+    int prefetch;  // tiles start with an L2 prefetch of their input
+};
+
+// Tile t of a schedule: column tx, rows [y0, y1), and its stripe sums st
+// (uniform schedules with a stripe pre-pass only; else nullptr).
+__device__ __forceinline__ void sched_tile(const TileSched &S, int64_t W, const uint2 *stripes, int64_t t,
+                                           int64_t &tx, int64_t &y0, int64_t &y1, const uint2 *&st)
+{
+    st = nullptr;
+    if (t < S.n_edge) {
+        tx = (t & 1) ? S.tiles_x - 1 : 0;
+        y0 = S.row0 + (t >> 1) * S.edge_h;
+        y1 = y0 + S.edge_h;
+    } else {
+        const int64_t t2 = t - S.n_edge;
+        const int64_t ncol = S.n_edge ? S.tiles_x - 2 : S.tiles_x;
+        const int64_t ty = t2 / ncol;
+        tx = (S.n_edge ? 1 : 0) + (t2 - ty * ncol);
+        y0 = S.row0 + ty * S.tile_h;
+        y1 = y0 + S.tile_h;
+        if (stripes)
+            st = stripes + ty * W;
+    }
+    if (y1 > S.row1)
+        y1 = S.row1;
+}
+
 // Whether the pipelined path applies to a launch (host and device): binarize
 // modes, 32-bit S2, aligned 8-byte loads, W in [8, 2^30], and an anchor
 // window [x0 - l, x0 + r) that AW words per lane cover: at most 128 AW bytes

@@ -158,22 +158,22 @@ cudaError_t launch_global_finalize(const GStats *gs, unsigned long long N, doubl
 }
 
 // The window kernel with a Table 1 threshold other than Sauvola/Niblack:
-// warp tiles of 256 columns, grid-stride, the general (non-pipelined) row
-// routine on interior and edge tiles.
+// warp tiles of 256 columns in the window kernel's tile schedule (one wave,
+// shorter edge tiles), the general (non-pipelined) row routine on interior
+// and edge tiles.
 template <int MODE, bool VEC, typename S2T>
 __global__ void __launch_bounds__(32 * kWarpsPerBlockExt, 4)
-    k_window_ext(Image g, Window win, ThreshExt T, Outputs o, int64_t tiles_x, int64_t tiles_total,
-                 int64_t tile_h, const uint2 *stripes)
+    k_window_ext(Image g, Window win, ThreshExt T, Outputs o, TileSched S, const uint2 *stripes)
 {
     const int lane = threadIdx.x & 31;
     const int64_t wid = (int64_t)blockIdx.x * kWarpsPerBlockExt + (threadIdx.x >> 5);
     const int64_t stride = (int64_t)gridDim.x * kWarpsPerBlockExt;
-    for (int64_t t = wid; t < tiles_total; t += stride) {
-        const int64_t tx = t % tiles_x, ty = t / tiles_x;
-        const int64_t x0 = tx * kTileCols, y0 = ty * tile_h;
-        const int64_t y1 = y0 + tile_h < g.H ? y0 + tile_h : g.H;
+    for (int64_t t = wid; t < S.tiles_total; t += stride) {
+        int64_t tx, y0, y1;
+        const uint2 *st;
+        sched_tile(S, g.W, stripes, t, tx, y0, y1, st);
+        const int64_t x0 = tx * kTileCols;
         const bool interior = VEC && (x0 - win.l >= 0) && (x0 + kTileCols + win.r <= g.W);
-        const uint2 *st = stripes ? stripes + ty * g.W : nullptr;
         if (interior)
             window_rows<MODE, VEC, true, S2T, true>(g, win, T, o, x0, y0, y1, lane, st);
         else
@@ -186,15 +186,14 @@ static cudaError_t launch_ext_t(const Image &g, const Window &win, const ThreshE
                                 const Outputs &o, cudaStream_t stream)
 {
     const int64_t tile_h = window_tile_rows(g.H, g.W, win.h, win.w);
-    const int64_t tiles_x = (g.W + kTileCols - 1) / kTileCols;
     const int64_t tiles_y = (g.H + tile_h - 1) / tile_h;
-    const int64_t tiles = tiles_x * tiles_y;
-    int64_t blocks = (tiles + kWarpsPerBlockExt - 1) / kWarpsPerBlockExt;
+    uint2 *stripes = launch_stripes(g, win, 0, tile_h, tiles_y, stream);
+    const TileSched S = make_sched(g, win, 0, g.H, false, stripes != nullptr);
+    int64_t blocks = (S.tiles_total + kWarpsPerBlockExt - 1) / kWarpsPerBlockExt;
     if (blocks > 2147483647LL)
         blocks = 2147483647LL;
-    uint2 *stripes = launch_stripes(g, win, 0, tile_h, tiles_y, stream);
     k_window_ext<MODE, VEC, S2T><<<(unsigned)blocks, 32 * kWarpsPerBlockExt, 0, stream>>>(
-        g, win, T, o, tiles_x, tiles, tile_h, stripes);
+        g, win, T, o, S, stripes);
     cudaError_t e = cudaGetLastError();
     if (stripes && cudaFreeAsync(stripes, stream) != cudaSuccess && e == cudaSuccess)
         e = cudaGetLastError();

@@ -11,18 +11,6 @@ namespace bz {
 constexpr int kWarpsPerBlock = 4;
 constexpr int kBlocksPerSM = 4;  // 128 registers per thread
 
-// The tiles of one launch.  Edge tiles (the first and last tile columns)
-// clamp their byte streams and look up per-column counts, so they take
-// longer per row; with a one-wave grid the slowest warps set the launch's
-// duration.  A balanced schedule therefore gives the two edge columns
-// shorter tiles (edge_h < tile_h rows) and lists them first (n_edge tiles,
-// alternating left and right column); the uniform schedule has n_edge = 0
-// and every column in the tile_h grid.
-struct TileSched {
-    int64_t tiles_x, tile_h, edge_h, n_edge, tiles_total, row0, row1;
-    int prefetch;  // tiles start with an L2 prefetch of their input
-};
-
 // AW > 0: every tile takes the pipelined path with AW anchor words per lane
 // (the host checked pipe_words); the variants are separate kernels so that
 // each gets its own register allocation.  `stripes` (uniform schedules only):
@@ -35,25 +23,8 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, kBlocksPerSM)
     const int lane = threadIdx.x & 31;
     const int64_t wid = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
     const int64_t stride = (int64_t)gridDim.x * kWarpsPerBlock;
-    // tile t: column tx, rows [y0, y1), stripe sums st
     auto tile_of = [&](int64_t t, int64_t &tx, int64_t &y0, int64_t &y1, const uint2 *&st) {
-        st = nullptr;
-        if (t < S.n_edge) {
-            tx = (t & 1) ? S.tiles_x - 1 : 0;
-            y0 = S.row0 + (t >> 1) * S.edge_h;
-            y1 = y0 + S.edge_h;
-        } else {
-            const int64_t t2 = t - S.n_edge;
-            const int64_t ncol = S.n_edge ? S.tiles_x - 2 : S.tiles_x;
-            const int64_t ty = t2 / ncol;
-            tx = (S.n_edge ? 1 : 0) + (t2 - ty * ncol);
-            y0 = S.row0 + ty * S.tile_h;
-            y1 = y0 + S.tile_h;
-            if (stripes)
-                st = stripes + ty * g.W;
-        }
-        if (y1 > S.row1)
-            y1 = S.row1;
+        sched_tile(S, g.W, stripes, t, tx, y0, y1, st);
     };
     // let the next kernel be scheduled; prefetch this warp's first tile
     // into L2 while the previous kernel drains (a prefetch reads no result of
@@ -159,8 +130,11 @@ int64_t window_tile_rows(int64_t H, int64_t W, int h, int w)
 
 // Edge-tile height as a fraction of the interior height: the measured time
 // per row of an edge tile is about 1.2x an interior row's on the pipelined
-// path and 1.3-2x on the generic path (GB300, 4096 x 3072 page).
-// BZ_EDGE_FRAC overrides it (tuning; >= 1 disables the balanced schedule).
+// path and 1.3-2x on the generic path (GB300, 4096 x 3072 page).  Table 1
+// methods (generic path), Wolf / Rais / Phansalkar at 15², 31², 63²: 0.5
+// gave 778 us summed over the nine calls, 0.6 788, 0.7 795, uniform tiles
+// 940.  BZ_EDGE_FRAC overrides it (tuning; >= 1 disables the balanced
+// schedule).
 static double edge_fraction(bool pipe)
 {
     static const double env = [] {
@@ -169,14 +143,14 @@ static double edge_fraction(bool pipe)
     }();
     if (env > 0.0)
         return env;
-    return pipe ? 0.82 : 0.7;
+    return pipe ? 0.82 : 0.5;
 }
 
 // The tile schedule of a launch over rows [row0, row1): one-wave interior
 // tiles, and for launches without stripe warm-up and with at least three
 // tile columns, shorter edge tiles as long as the whole grid stays one wave.
-static TileSched make_sched(const Image &g, const Window &win, int64_t row0, int64_t row1, bool pipe,
-                            bool stripes)
+TileSched make_sched(const Image &g, const Window &win, int64_t row0, int64_t row1, bool pipe,
+                     bool stripes)
 {
     TileSched S;
     const int64_t rows = row1 - row0;
