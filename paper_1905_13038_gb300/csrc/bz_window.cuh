@@ -825,7 +825,7 @@ __device__ __forceinline__ uint2 shift8(uint2 v, int sh)
 // counts and their reciprocals come from a per-warp table.
 // smem: 6656 bytes per warp (two 2 KB row slots, the 2 KB column table, and
 // 512 bytes for the FP64 near-tie list and its results).
-template <int MODE, bool WARMB = false, bool EDGE = false, int AW = 1>
+template <int MODE, bool WARMB = false, bool EDGE = false, int AW = 1, int EXTM = 0>
 __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &win, const Thresh &T,
                                                  const Outputs &o, int64_t x0, int64_t y0,
                                                  int64_t y1, int lane, uint4 *slots,
@@ -1017,7 +1017,13 @@ __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &w
         sl[3 * 32 + lane] = make_uint4(off2 + p2[4], off2 + p2[5], off2 + p2[6], off2 + p2[7]);
     };
 
-    const bool simple = T.method == 0 && T.alpha >= 0.0f && T.beta >= 0.0f;
+    const bool simple = !EXTM && T.method == 0 && T.alpha >= 0.0f && T.beta >= 0.0f;
+    // EXTM: a Table 1 method other than Sauvola / Niblack (T is then a
+    // ThreshExt): its FP32 constants from the global statistics
+    const ThreshExt &TX = static_cast<const ThreshExt &>(T);
+    ExtF F{};
+    if (EXTM)
+        F = make_extf(EXTM, T.k, T.R, TX.X, global_lms(*TX.gs, TX.N), T.eps);
     unsigned long long nfb = 0;
 
     // EDGE: column counts of this lane's 8 columns (1 past the row) and
@@ -1072,17 +1078,19 @@ __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &w
             count(m, n_m, inv_m);
             const float mu = __uint2float_rn(S1) * inv_m;
             const float var = v_float<S2T>(n_m, (uint64_t)S2, S1) * (inv_m * inv_m);
-            float t, mag;
-            if (SIMPLE) {
+            float t, bnd;
+            if (EXTM) {
+                t = ext_t32<EXTM ? EXTM : METHOD_WOLF>(F, mu, var, inv_m, bnd);
+            } else if (SIMPLE) {
                 t = mu * fmaf(T.beta, sqrt_approx(var), T.alpha);
-                mag = t;
+                bnd = fmaf(T.eps, t, T.delta64);
             } else {
                 const float s = sqrt_approx(var);
                 t = fmaf(fmaf(T.beta, mu, T.gamma), s, T.alpha * mu);
-                mag = fmaf(fmaf(T.abeta, mu, T.agamma), s, T.aalpha * mu);
+                bnd = fmaf(T.eps, fmaf(fmaf(T.abeta, mu, T.agamma), s, T.aalpha * mu), T.delta64);
             }
             const float d = t - pixel_f(P, m);
-            slack = fabsf(d) - fmaf(T.eps, mag, T.delta64);
+            slack = fabsf(d) - bnd;
             if (EDGE && !(vmask >> m & 1u))
                 slack = 1.0f;
             return __float_as_uint(d) >> 31;
@@ -1138,6 +1146,9 @@ __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &w
             for (uint32_t u2 = und; u2; u2 &= u2 - 1)
                 list[at++] = (uint8_t)(lane * 8 + (__ffs(u2) - 1));
             __syncwarp();
+            Global G{};
+            if (EXTM)
+                G = global_lms(*TX.gs, TX.N);
             for (uint32_t r0 = 0; r0 < total; r0 += 32) {
                 const uint32_t e = r0 + lane < total ? list[r0 + lane] : (uint32_t)(lane * 8);
                 const int own = (int)(e >> 3), m = (int)(e & 7u);
@@ -1148,8 +1159,14 @@ __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &w
                     uint32_t n_m;
                     float inv_m;
                     count_of(own, m, n_m, inv_m);
-                    res[e] = (uint8_t)fp64_bit(T.method, (uint32_t)byte_at(Pown, m), S1, (uint64_t)S2, n_m, T.k,
-                                               T.R);
+                    if (EXTM) {
+                        res[e] = (uint8_t)fp64_bit_ext(EXTM, (uint32_t)byte_at(Pown, m), S1, (uint64_t)S2, n_m,
+                                                       T.k, T.R, TX.X.alpha1, TX.X.k1, TX.X.k2, TX.X.gamma,
+                                                       TX.X.p, TX.X.q, G.L, G.M, G.S);
+                    } else {
+                        res[e] = (uint8_t)fp64_bit(T.method, (uint32_t)byte_at(Pown, m), S1, (uint64_t)S2, n_m,
+                                                   T.k, T.R);
+                    }
                 }
             }
             __syncwarp();

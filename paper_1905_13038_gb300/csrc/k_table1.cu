@@ -181,6 +181,58 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlockExt, 4)
     }
 }
 
+// The pipelined window kernel with Table 1 method METHOD (binarize modes,
+// launches for which pipe_words gives one anchor word per lane): interior
+// and edge tiles both take window_rows_pipe, in the balanced tile schedule.
+template <int MODE, int METHOD>
+__global__ void __launch_bounds__(32 * kWarpsPerBlockExt, 4)
+    k_window_ext_pipe(Image g, Window win, ThreshExt T, Outputs o, TileSched S, const uint2 *stripes)
+{
+    __shared__ uint4 slots[kWarpsPerBlockExt][416];  // 6.5 KB per warp
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = (int64_t)blockIdx.x * kWarpsPerBlockExt + (threadIdx.x >> 5);
+    const int64_t stride = (int64_t)gridDim.x * kWarpsPerBlockExt;
+    for (int64_t t = wid; t < S.tiles_total; t += stride) {
+        int64_t tx, y0, y1;
+        const uint2 *st;
+        sched_tile(S, g.W, stripes, t, tx, y0, y1, st);
+        const int64_t x0 = tx * kTileCols;
+        if ((x0 - win.l >= 0) && (x0 + kTileCols + win.r <= g.W))
+            window_rows_pipe<MODE, false, false, 1, METHOD>(g, win, T, o, x0, y0, y1, lane,
+                                                            slots[threadIdx.x >> 5], st);
+        else
+            window_rows_pipe<MODE, false, true, 1, METHOD>(g, win, T, o, x0, y0, y1, lane,
+                                                           slots[threadIdx.x >> 5], st);
+    }
+}
+
+template <int MODE>
+static cudaError_t launch_ext_pipe(const Image &g, const Window &win, const ThreshExt &T, const Outputs &o,
+                                   cudaStream_t stream)
+{
+    const int64_t tile_h = window_tile_rows(g.H, g.W, win.h, win.w);
+    const int64_t tiles_y = (g.H + tile_h - 1) / tile_h;
+    uint2 *stripes = launch_stripes(g, win, 0, tile_h, tiles_y, stream);
+    const TileSched S = make_sched(g, win, 0, g.H, true, stripes != nullptr);
+    int64_t blocks = (S.tiles_total + kWarpsPerBlockExt - 1) / kWarpsPerBlockExt;
+    if (blocks > 2147483647LL)
+        blocks = 2147483647LL;
+    const dim3 grid((unsigned)blocks), block(32 * kWarpsPerBlockExt);
+    switch (T.method) {
+    case METHOD_WOLF: k_window_ext_pipe<MODE, METHOD_WOLF><<<grid, block, 0, stream>>>(g, win, T, o, S, stripes); break;
+    case METHOD_FENG: k_window_ext_pipe<MODE, METHOD_FENG><<<grid, block, 0, stream>>>(g, win, T, o, S, stripes); break;
+    case METHOD_RAIS: k_window_ext_pipe<MODE, METHOD_RAIS><<<grid, block, 0, stream>>>(g, win, T, o, S, stripes); break;
+    case METHOD_NICK: k_window_ext_pipe<MODE, METHOD_NICK><<<grid, block, 0, stream>>>(g, win, T, o, S, stripes); break;
+    default:
+        k_window_ext_pipe<MODE, METHOD_PHANSALKAR><<<grid, block, 0, stream>>>(g, win, T, o, S, stripes);
+        break;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (stripes && cudaFreeAsync(stripes, stream) != cudaSuccess && e == cudaSuccess)
+        e = cudaGetLastError();
+    return e;
+}
+
 template <int MODE, bool VEC, typename S2T>
 static cudaError_t launch_ext_t(const Image &g, const Window &win, const ThreshExt &T,
                                 const Outputs &o, cudaStream_t stream)
@@ -206,6 +258,8 @@ static cudaError_t launch_ext_m(const Image &g, const Window &win, const ThreshE
 {
     const bool vec = ((uintptr_t)g.img % 8 == 0) && (g.pitch % 8 == 0);
     const bool wide = (int64_t)win.h * win.w > 66051;
+    if ((MODE == MODE_FP64 || MODE == MODE_FP32) && pipe_words(MODE, vec, !wide, g, win) == 1)
+        return launch_ext_pipe<MODE == MODE_FP32 ? MODE_FP32 : MODE_FP64>(g, win, T, o, stream);
     if (vec)
         return wide ? launch_ext_t<MODE, true, unsigned long long>(g, win, T, o, stream)
                     : launch_ext_t<MODE, true, uint32_t>(g, win, T, o, stream);
