@@ -173,6 +173,20 @@ bz_status binarize_host(int32_t method, const uint8_t *image_host, int64_t H,
                         int64_t out_pitch, bz_precision precision,
                         void *stream);
 
+/* The same for n window sizes of one image (multi-scale use): the image is
+ * uploaded once, binarized with each window (h[q], w[q]) in turn and the n
+ * packed outputs downloaded into out_host[q] (each H rows of out_pitch
+ * bytes; none may overlap the image or one another).  1 <= n <= 64; h, w
+ * and out_host are host arrays of n entries, read during the call only.
+ * bz_last_fp64_fallbacks then reports the sum over the n windows.  Ordering,
+ * lifetime and errors as for binarize_host. */
+bz_status binarize_host_multi(int32_t method, const uint8_t *image_host,
+                              int64_t H, int64_t W, int64_t in_pitch,
+                              int32_t n, const int32_t *h, const int32_t *w,
+                              double k, double R, uint8_t *const *out_host,
+                              int64_t out_pitch, bz_precision precision,
+                              void *stream);
+
 /* ---------------------------------------------------------------------- */
 /* In-place binarization (Sec. 3.2 assumptions: the algorithm can be made */
 /* in-place by keeping the gray levels that later windows still need).    */

@@ -27,7 +27,7 @@ __all__ = [
     "WOLF", "FENG", "RAIS", "NICK", "PHANSALKAR", "binarize_wolf", "binarize_feng", "binarize_rais",
     "binarize_nick", "binarize_phansalkar", "global_stats", "binarize_precision_report_ext",
     "window_minmax", "binarize_bernsen", "haar_feature", "HAAR_FEATURES", "binarize_inplace",
-    "inplace_scratch_bytes", "binarize_host",
+    "inplace_scratch_bytes", "binarize_host", "binarize_host_multi",
 ]
 
 FP64, FP32, FP64_DIRECT = 0, 1, 2
@@ -102,6 +102,7 @@ def _load():
         "haar_feature": ([P, i64, i64, i64, ctypes.POINTER(_HaarC), P, P], st),
         "binarize_inplace": ([i32, P, i64, i64, i64, i32, i32, f64, f64, i64, st, P], st),
         "binarize_host": ([i32, P, i64, i64, i64, i32, i32, f64, f64, P, i64, st, P], st),
+        "binarize_host_multi": ([i32, P, i64, i64, i64, i32, P, P, f64, f64, P, i64, st, P], st),
         "bz_inplace_scratch_bytes": ([i64, i64, i32, i64], i64),
         "binarize_precision_report_ext": ([i32, P, i64, i64, i64, i32, i32, P, P, P, P], st),
         "binarize_batch": ([ctypes.POINTER(_JobC), i32, st, P], st),
@@ -388,6 +389,37 @@ def binarize_host(method: int, image, h: int, w: int, k: float = 0.5, R: float =
     if sync:
         torch.cuda.Stream(stream_ptr=s.value).synchronize() if s.value else torch.cuda.synchronize()
     return out
+
+
+def binarize_host_multi(method: int, image, windows, k: float = 0.5, R: float = 128.0, outs=None,
+                        precision="fp64", W: int | None = None, stream=None, sync: bool = True):
+    """binarize_host for several window sizes of one image: one upload, one
+    packed output per (h, w) in `windows` (CPU uint8 tensors (H, ceil(W/8)),
+    returned as a list).  With sync=False the call only enqueues."""
+    import torch
+    if image.is_cuda or image.dtype != torch.uint8 or image.dim() != 2 or image.stride(1) != 1:
+        raise ValueError("image must be a 2-D uint8 CPU tensor with unit column stride")
+    H = image.shape[0]
+    pitch = image.stride(0) if H > 1 else image.shape[1]
+    W = image.shape[1] if W is None else W
+    n = len(windows)
+    if outs is None:
+        outs = [torch.empty((H, (W + 7) // 8), dtype=torch.uint8, pin_memory=image.is_pinned())
+                for _ in range(n)]
+    if len(outs) != n or n == 0:
+        raise ValueError("one output per window")
+    op = outs[0].stride(0) if outs[0].shape[0] > 1 else outs[0].shape[1]
+    if any((o.stride(0) if o.shape[0] > 1 else o.shape[1]) != op for o in outs):
+        raise ValueError("outputs must share one row pitch")
+    hs = (ctypes.c_int32 * n)(*[int(h) for h, _ in windows])
+    ws = (ctypes.c_int32 * n)(*[int(w) for _, w in windows])
+    ptrs = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])
+    s = _stream(stream)
+    _check("binarize_host_multi", _load().binarize_host_multi(method, image.data_ptr(), H, W, pitch, n, hs, ws,
+                                                              k, R, ptrs, op, _PREC[precision], s))
+    if sync:
+        torch.cuda.Stream(stream_ptr=s.value).synchronize() if s.value else torch.cuda.synchronize()
+    return outs
 
 
 def inplace_scratch_bytes(H: int, W: int, h: int, band_rows: int = 0) -> int:

@@ -645,19 +645,32 @@ static bool host_grow(uint8_t *&buf, size_t &cap, size_t need, cudaEvent_t last)
     return true;
 }
 
-bz_status binarize_host(int32_t method, const uint8_t *image_host, int64_t H, int64_t W,
-                        int64_t in_pitch, int32_t h, int32_t w, double k, double R,
-                        uint8_t *out_host, int64_t out_pitch, bz_precision precision, void *stream)
+// One host-memory call over n windows of the same image: one upload, n
+// window launches, n downloads (binarize_host is n = 1).
+static bz_status host_run(int32_t method, const uint8_t *image_host, int64_t H, int64_t W, int64_t in_pitch,
+                          int32_t n, const int32_t *hv, const int32_t *wv, double k, double R,
+                          uint8_t *const *outs, int64_t out_pitch, bz_precision precision, void *stream)
 {
-    bz_status st = check_image(image_host, H, W, in_pitch, h, w);
-    if (st != BZ_OK)
-        return st;
-    const int64_t cw = (W + 7) / 8;
-    if (!out_host || out_pitch < cw || out_pitch > (INT64_MAX / H))
+    if (n < 1 || n > 64 || !hv || !wv || !outs)
         return BZ_EINVAL;
-    if (ranges_overlap(image_host, (size_t)((H - 1) * in_pitch + W), out_host,
-                       (size_t)((H - 1) * out_pitch + cw)))
-        return BZ_EOVERLAP;
+    for (int q = 0; q < n; q++) {
+        const bz_status st = check_image(image_host, H, W, in_pitch, hv[q], wv[q]);
+        if (st != BZ_OK)
+            return st;
+    }
+    const int64_t cw = (W + 7) / 8;
+    if (out_pitch < cw || out_pitch > (INT64_MAX / H))
+        return BZ_EINVAL;
+    const size_t in_span = (size_t)((H - 1) * in_pitch + W), out_span = (size_t)((H - 1) * out_pitch + cw);
+    for (int q = 0; q < n; q++) {
+        if (!outs[q])
+            return BZ_EINVAL;
+        if (ranges_overlap(image_host, in_span, outs[q], out_span))
+            return BZ_EOVERLAP;
+        for (int q2 = 0; q2 < q; q2++)
+            if (ranges_overlap(outs[q2], out_span, outs[q], out_span))
+                return BZ_EOVERLAP;
+    }
     if ((method != 0 && method != 1) || !finite_params(method, k, R))
         return BZ_EINVAL;
     int mode;
@@ -673,43 +686,48 @@ bz_status binarize_host(int32_t method, const uint8_t *image_host, int64_t H, in
     HostState *hs = host_state(dev);
     if (!hs)
         return BZ_ECUDA;
-    const Window win = make_window(h, w);
     const Thresh T = make_thresh(method, k, method == 0 ? R : 128.0);
     // device rows of 16-byte multiples; a host pitch that already is one (and
     // no wider than needed) keeps the copy a single contiguous transfer
     const int64_t dpitch = (in_pitch % 16 == 0 && in_pitch - W < 16) ? in_pitch : (W + 15) & ~(int64_t)15;
-    Outputs o{};
-    o.out_pitch = cw;
+    const size_t plane = (size_t)(H * cw);
     unsigned long long *fb = mode == MODE_FP64 ? fallback_counter(dev) : nullptr;
     std::lock_guard<std::mutex> lk(hs->mu);
     HostSlot &sl = hs->slot[hs->next];
     hs->next ^= 1;
     bool ok = host_grow(sl.img, sl.img_cap, (size_t)(H * dpitch), sl.down) &&
-              host_grow(sl.out, sl.out_cap, (size_t)(H * cw), sl.down);
-    o.bits = sl.out;
-    o.fallbacks = fb;
+              host_grow(sl.out, sl.out_cap, plane * (size_t)n, sl.down);
     // upload once the slot's previous compute has read its image
     ok = ok && cudaStreamWaitEvent(hs->up, sl.comp, 0) == cudaSuccess;
     if (ok && dpitch == in_pitch)
-        ok = cudaMemcpyAsync(sl.img, image_host, (size_t)((H - 1) * in_pitch + W), cudaMemcpyHostToDevice,
-                             hs->up) == cudaSuccess;
+        ok = cudaMemcpyAsync(sl.img, image_host, in_span, cudaMemcpyHostToDevice, hs->up) == cudaSuccess;
     else if (ok)
         ok = cudaMemcpy2DAsync(sl.img, (size_t)dpitch, image_host, (size_t)in_pitch, (size_t)W, (size_t)H,
                                cudaMemcpyHostToDevice, hs->up) == cudaSuccess;
     ok = ok && cudaEventRecord(sl.up, hs->up) == cudaSuccess;
-    // compute once the upload is done and the slot's previous output is home
+    // compute once the upload is done and the slot's previous outputs are home
     ok = ok && cudaStreamWaitEvent(hs->comp, sl.up, 0) == cudaSuccess &&
          cudaStreamWaitEvent(hs->comp, sl.down, 0) == cudaSuccess &&
-         (!fb || cudaMemsetAsync(fb, 0, sizeof(unsigned long long), hs->comp) == cudaSuccess) &&
-         launch_window(mode, Image{sl.img, H, W, dpitch}, win, T, o, hs->comp) == cudaSuccess &&
-         cudaEventRecord(sl.comp, hs->comp) == cudaSuccess;
+         (!fb || cudaMemsetAsync(fb, 0, sizeof(unsigned long long), hs->comp) == cudaSuccess);
+    for (int q = 0; ok && q < n; q++) {
+        Outputs o{};
+        o.bits = sl.out + plane * (size_t)q;
+        o.out_pitch = cw;
+        o.fallbacks = fb;
+        ok = launch_window(mode, Image{sl.img, H, W, dpitch}, make_window(hv[q], wv[q]), T, o, hs->comp) ==
+             cudaSuccess;
+    }
+    ok = ok && cudaEventRecord(sl.comp, hs->comp) == cudaSuccess;
     // download, and order the caller's stream after it
     ok = ok && cudaStreamWaitEvent(hs->down, sl.comp, 0) == cudaSuccess;
-    if (ok && out_pitch == cw)
-        ok = cudaMemcpyAsync(out_host, sl.out, (size_t)(H * cw), cudaMemcpyDeviceToHost, hs->down) == cudaSuccess;
-    else if (ok)
-        ok = cudaMemcpy2DAsync(out_host, (size_t)out_pitch, sl.out, (size_t)cw, (size_t)cw, (size_t)H,
-                               cudaMemcpyDeviceToHost, hs->down) == cudaSuccess;
+    for (int q = 0; ok && q < n; q++) {
+        const uint8_t *src = sl.out + plane * (size_t)q;
+        if (out_pitch == cw)
+            ok = cudaMemcpyAsync(outs[q], src, plane, cudaMemcpyDeviceToHost, hs->down) == cudaSuccess;
+        else
+            ok = cudaMemcpy2DAsync(outs[q], (size_t)out_pitch, src, (size_t)cw, (size_t)cw, (size_t)H,
+                                   cudaMemcpyDeviceToHost, hs->down) == cudaSuccess;
+    }
     ok = ok && cudaEventRecord(sl.down, hs->down) == cudaSuccess &&
          cudaStreamWaitEvent((cudaStream_t)stream, sl.down, 0) == cudaSuccess;
     if (!ok) {  // leave nothing of this call in flight
@@ -718,6 +736,25 @@ bz_status binarize_host(int32_t method, const uint8_t *image_host, int64_t H, in
         cudaStreamSynchronize(hs->down);
     }
     return ok ? BZ_OK : BZ_ECUDA;
+}
+
+bz_status binarize_host(int32_t method, const uint8_t *image_host, int64_t H, int64_t W,
+                        int64_t in_pitch, int32_t h, int32_t w, double k, double R,
+                        uint8_t *out_host, int64_t out_pitch, bz_precision precision, void *stream)
+{
+    if (!out_host)
+        return BZ_EINVAL;
+    uint8_t *outs[1] = {out_host};
+    return host_run(method, image_host, H, W, in_pitch, 1, &h, &w, k, R, outs, out_pitch, precision, stream);
+}
+
+bz_status binarize_host_multi(int32_t method, const uint8_t *image_host, int64_t H, int64_t W,
+                              int64_t in_pitch, int32_t n, const int32_t *h, const int32_t *w, double k,
+                              double R, uint8_t *const *out_host, int64_t out_pitch, bz_precision precision,
+                              void *stream)
+{
+    return host_run(method, image_host, H, W, in_pitch, n, h, w, k, R, out_host, out_pitch, precision,
+                    stream);
 }
 
 int64_t bz_inplace_scratch_bytes(int64_t H, int64_t W, int32_t h, int64_t band_rows)

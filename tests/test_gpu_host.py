@@ -65,6 +65,48 @@ def test_host_growing_pages_in_flight():
         np.testing.assert_array_equal(o.numpy(), ref)
 
 
+@pytest.mark.parametrize("H,W,pitch", [(3072, 4096, 4096), (500, 777, 784), (97, 600, 603)])
+def test_host_multi_windows(H, W, pitch):
+    """One upload, several windows: each output equals the oracle's."""
+    import torch
+    import paper_1905_13038_gb300 as bz
+    img = synth.document(H, W, 7 + H + W, stains=1, pitch=pitch)
+    t = torch.from_numpy(img).pin_memory()
+    windows = [(15, 15), (63, 63), (31, 127), (5, 9)]
+    if H >= 3000:
+        windows.append((255, 255))
+    outs = bz.binarize_host_multi(0, t, windows, k=0.5, W=W)
+    for (h, w), o in zip(windows, outs):
+        _, ref = oracle.binarize(0, img, h, w, 0.5, 128.0, W=W)
+        np.testing.assert_array_equal(o.numpy(), ref)
+
+
+def test_host_multi_in_flight():
+    import torch
+    import paper_1905_13038_gb300 as bz
+    s = torch.cuda.Stream()
+    pages = [torch.from_numpy(synth.document(600 + 50 * q, 700, 60 + q, stains=1)).pin_memory()
+             for q in range(4)]
+    windows = [(15, 15), (31, 31)]
+    res = [bz.binarize_host_multi(1, p, windows, k=-0.2, stream=s, sync=False) for p in pages]
+    s.synchronize()
+    for p, outs in zip(pages, res):
+        for (h, w), o in zip(windows, outs):
+            _, ref = oracle.niblack(p.numpy(), h, w, k=-0.2)
+            np.testing.assert_array_equal(o.numpy(), ref)
+
+
+def test_host_multi_rejects_bad_arguments():
+    import torch
+    import paper_1905_13038_gb300 as bz
+    t = torch.zeros((10, 16), dtype=torch.uint8)
+    with pytest.raises(bz.BinarizeError):
+        bz.binarize_host_multi(0, t, [(3, 3), (0, 3)])  # an invalid window
+    out = torch.zeros((10, 2), dtype=torch.uint8)
+    with pytest.raises(bz.BinarizeError):
+        bz.binarize_host_multi(0, t, [(3, 3), (5, 5)], outs=[out, out])  # outputs overlap
+
+
 def test_host_rejects_bad_arguments():
     import torch
     import paper_1905_13038_gb300 as bz
