@@ -144,6 +144,17 @@ bz_status binarize_precision_report(int32_t method, const uint8_t *image,
 int32_t bz_kernels_per_call(int64_t H, int64_t W, int32_t h, int32_t w,
                             bz_precision precision);
 
+/* The window kernel's tile schedule for an H x W image on a GPU with `sms`
+ * SMs, computed on the host without a device (pure arithmetic; for planning
+ * and tests).  pipe: the pipelined kernel (else the generic one); stripes:
+ * the launch starts from the stripe pre-pass.  Writes out[0..5] = tile
+ * columns (256 pixels each), interior tile rows, edge tile rows, edge tiles
+ * (listed first, alternating the first and last tile column), tiles in total
+ * and the warps resident at once (one wave).  Returns 0, or -1 for invalid
+ * arguments. */
+int32_t bz_tile_schedule(int64_t H, int64_t W, int32_t sms, int32_t pipe,
+                         int32_t stripes, int64_t *out);
+
 /* Number of pixels the most recent BZ_FP64 call on this device could not
  * decide in FP32 and evaluated in FP64, read back synchronously after the
  * stream finishes.  Diagnostic only; returns -1 when unknown. */

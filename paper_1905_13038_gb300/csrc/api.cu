@@ -784,6 +784,13 @@ int32_t bz_kernels_per_call(int64_t H, int64_t W, int32_t h, int32_t w, bz_preci
     return window_kernel_count(mode, g, make_window(h, w), 0, H);
 }
 
+int32_t bz_tile_schedule(int64_t H, int64_t W, int32_t sms, int32_t pipe, int32_t stripes, int64_t *out)
+{
+    if (!out)
+        return -1;
+    return plan_tile_schedule(H, W, sms, pipe != 0, stripes != 0, out);
+}
+
 int64_t bz_last_fp64_fallbacks(void *stream)
 {
     int dev = 0;

@@ -63,10 +63,18 @@ uint2 *launch_stripes(const Image &g, const Window &win, int64_t row0, int64_t t
 // Kernels launch_stripes enqueues for this geometry (0: no stripes).
 int stripe_kernel_count(const Window &win, int64_t tile_h, int64_t tiles_y);
 
+// Window kernel geometry: 4 warps per block, 4 blocks per SM (128 registers
+// per thread); one wave is SMs x 16 warps.
+constexpr int kWarpsPerBlock = 4;
+constexpr int kBlocksPerSM = 4;
+
 // The tile schedule of a window-kernel launch over rows [row0, row1): one-wave
 // interior tiles and, without stripes, shorter edge tiles (pipe: the edge
 // tiles take the pipelined path, else the generic one).
 TileSched make_sched(const Image &g, const Window &win, int64_t row0, int64_t row1, bool pipe, bool stripes);
+// The same from H, W and an SM count alone (no device): tiles_x, tile_h,
+// edge_h, n_edge, tiles_total and the resident warps into out[0..5].
+int plan_tile_schedule(int64_t H, int64_t W, int sms, bool pipe, bool stripes, int64_t out[6]);
 
 // Launches of the window path; mode is a bz::Mode.
 cudaError_t launch_window(int mode, const Image &g, const Window &win, const Thresh &T,

@@ -8,8 +8,6 @@
 
 namespace bz {
 
-constexpr int kWarpsPerBlock = 4;
-constexpr int kBlocksPerSM = 4;  // 128 registers per thread
 
 // AW > 0: every tile takes the pipelined path with AW anchor words per lane
 // (the host checked pipe_words); the variants are separate kernels so that
@@ -82,114 +80,6 @@ Thresh make_thresh(int method, double k, double R)
     T.eps = kEpsF32;
     T.delta64 = (float)(mag * 1.01) + 1e-30f;
     return T;
-}
-
-bool pdl_enabled()
-{
-    static const bool on = [] {
-        const char *e = getenv("BZ_PDL");
-        return !(e && atoi(e) == 0);
-    }();
-    return on;
-}
-
-// Warps resident at once on this device (one wave of k_window).
-static int64_t resident_warps()
-{
-    int dev = 0, sms = 152;
-    if (cudaGetDevice(&dev) == cudaSuccess)
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    return (int64_t)sms * kBlocksPerSM * kWarpsPerBlock;
-}
-
-int64_t window_tile_rows(int64_t H, int64_t W, int h, int w)
-{
-    (void)h;
-    (void)w;
-    // One wave of warp tiles: the shortest tiles for which every tile of the
-    // image is resident at once (SMs x 4 blocks x 4 warps).  Measured on
-    // GB300: on the 4096 x 3072 page this gives 21 rows (8 % faster than 24,
-    // while 20 rows spills into a second wave); on small pages it gives
-    // 1-4 rows, which halves the latency (the launch is latency-bound and
-    // every warp's work shrinks).  BZ_TILE_ROWS overrides it (tuning).
-    static const int64_t env = [] {
-        const char *e = getenv("BZ_TILE_ROWS");
-        return e ? (int64_t)atoll(e) : (int64_t)0;
-    }();
-    if (env > 0)
-        return env < H ? env : H;
-    const int64_t tiles_x = (W + kTileCols - 1) / kTileCols;
-    int64_t bands = resident_warps() / tiles_x;
-    if (bands < 1)
-        bands = 1;
-    int64_t th = (H + bands - 1) / bands;
-    if (th < 1)
-        th = 1;
-    return th;
-}
-
-// Edge-tile height as a fraction of the interior height: the measured time
-// per row of an edge tile is about 1.2x an interior row's on the pipelined
-// path and 1.3-2x on the generic path (GB300, 4096 x 3072 page).  Table 1
-// methods (generic path), Wolf / Rais / Phansalkar at 15², 31², 63²: 0.5
-// gave 778 us summed over the nine calls, 0.6 788, 0.7 795, uniform tiles
-// 940.  BZ_EDGE_FRAC overrides it (tuning; >= 1 disables the balanced
-// schedule).
-static double edge_fraction(bool pipe)
-{
-    static const double env = [] {
-        const char *e = getenv("BZ_EDGE_FRAC");
-        return e ? atof(e) : 0.0;
-    }();
-    if (env > 0.0)
-        return env;
-    return pipe ? 0.82 : 0.5;
-}
-
-// The tile schedule of a launch over rows [row0, row1): one-wave interior
-// tiles, and for launches without stripe warm-up and with at least three
-// tile columns, shorter edge tiles as long as the whole grid stays one wave.
-TileSched make_sched(const Image &g, const Window &win, int64_t row0, int64_t row1, bool pipe,
-                     bool stripes)
-{
-    TileSched S;
-    const int64_t rows = row1 - row0;
-    S.tiles_x = (g.W + kTileCols - 1) / kTileCols;
-    S.tile_h = window_tile_rows(rows, g.W, win.h, win.w);
-    S.edge_h = S.tile_h;
-    S.n_edge = 0;
-    S.row0 = row0;
-    S.row1 = row1;
-    // without stripes the image is usually not in L2 yet (the stripe
-    // pre-pass has just read it otherwise).  BZ_PREFETCH=0 turns it off.
-    static const bool pf = [] {
-        const char *e = getenv("BZ_PREFETCH");
-        return !(e && atoi(e) == 0);
-    }();
-    S.prefetch = (pf && !stripes) ? 1 : 0;
-    const int64_t uniform = S.tiles_x * ((rows + S.tile_h - 1) / S.tile_h);
-    S.tiles_total = uniform;
-    const double f = edge_fraction(pipe);
-    if (!stripes && S.tiles_x >= 3 && f < 1.0 && S.tile_h > 4) {
-        // the shortest interior tiles (at most two rows taller than the
-        // uniform ones) whose grid, with edge tiles of f times their height,
-        // still fits in one wave
-        const int64_t cap = uniform > resident_warps() ? uniform : resident_warps();
-        for (int64_t th = S.tile_h; th <= S.tile_h + 2; th++) {
-            int64_t eh = (int64_t)((double)th * f + 0.5);
-            eh = eh < 1 ? 1 : eh;
-            const int64_t ne = 2 * ((rows + eh - 1) / eh);
-            const int64_t total = ne + (S.tiles_x - 2) * ((rows + th - 1) / th);
-            if (eh < th && total <= cap) {
-                S.tile_h = th;
-                S.edge_h = eh;
-                S.n_edge = ne;
-                S.tiles_total = total;
-                break;
-            }
-        }
-    }
-    return S;
 }
 
 template <int MODE, bool VEC, typename S2T, bool WARMB>

@@ -1,0 +1,157 @@
+// Host-side planning of the window kernel's launches: the one-wave tile
+// height, the balanced tile schedule (shorter edge tiles), and the tuning
+// switches read from the environment.  Pure host code; the kernels that
+// consume the schedule live in k_window.cu and k_table1.cu.
+#include <stdlib.h>
+
+#include "bz_internal.h"
+
+namespace bz {
+
+bool pdl_enabled()
+{
+    static const bool on = [] {
+        const char *e = getenv("BZ_PDL");
+        return !(e && atoi(e) == 0);
+    }();
+    return on;
+}
+
+// Warps resident at once on this device (one wave of k_window).
+static int64_t resident_warps()
+{
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return (int64_t)sms * kBlocksPerSM * kWarpsPerBlock;
+}
+
+// The shortest tile height for which every 256-column warp tile of an
+// H x W image is resident at once with `resident` warps.
+static int64_t one_wave_rows(int64_t H, int64_t W, int64_t resident)
+{
+    const int64_t tiles_x = (W + kTileCols - 1) / kTileCols;
+    int64_t bands = resident / tiles_x;
+    if (bands < 1)
+        bands = 1;
+    int64_t th = (H + bands - 1) / bands;
+    if (th < 1)
+        th = 1;
+    return th;
+}
+
+int64_t window_tile_rows(int64_t H, int64_t W, int h, int w)
+{
+    (void)h;
+    (void)w;
+    // One wave of warp tiles: the shortest tiles for which every tile of the
+    // image is resident at once (SMs x 4 blocks x 4 warps).  Measured on
+    // GB300: on the 4096 x 3072 page this gives 21 rows (8 % faster than 24,
+    // while 20 rows spills into a second wave); on small pages it gives
+    // 1-4 rows, which halves the latency (the launch is latency-bound and
+    // every warp's work shrinks).  BZ_TILE_ROWS overrides it (tuning).
+    static const int64_t env = [] {
+        const char *e = getenv("BZ_TILE_ROWS");
+        return e ? (int64_t)atoll(e) : (int64_t)0;
+    }();
+    if (env > 0)
+        return env < H ? env : H;
+    return one_wave_rows(H, W, resident_warps());
+}
+
+// Edge-tile height as a fraction of the interior height: the measured time
+// per row of an edge tile is about 1.2x an interior row's on the pipelined
+// path and 1.3-2x on the generic path (GB300, 4096 x 3072 page).  Table 1
+// methods (generic path), Wolf / Rais / Phansalkar at 15², 31², 63²: 0.5
+// gave 778 us summed over the nine calls, 0.6 788, 0.7 795, uniform tiles
+// 940.  BZ_EDGE_FRAC overrides it (tuning; >= 1 disables the balanced
+// schedule).
+static double default_edge_fraction(bool pipe)
+{
+    return pipe ? 0.82 : 0.5;
+}
+
+static double edge_fraction(bool pipe)
+{
+    static const double env = [] {
+        const char *e = getenv("BZ_EDGE_FRAC");
+        return e ? atof(e) : 0.0;
+    }();
+    if (env > 0.0)
+        return env;
+    return default_edge_fraction(pipe);
+}
+
+// The schedule of rows [row0, row1) of a W-column image from its one-wave
+// tile height: uniform, or, without stripe warm-up and with at least three
+// tile columns, the shortest interior tiles (at most two rows taller than
+// the uniform ones) whose grid, with edge tiles of f times their height,
+// still fits in `resident` warps (pure host arithmetic).
+static TileSched plan_sched(int64_t row0, int64_t row1, int64_t W, int64_t tile_h, int64_t resident, double f,
+                            bool stripes)
+{
+    TileSched S;
+    const int64_t rows = row1 - row0;
+    S.tiles_x = (W + kTileCols - 1) / kTileCols;
+    S.tile_h = tile_h;
+    S.edge_h = tile_h;
+    S.n_edge = 0;
+    S.row0 = row0;
+    S.row1 = row1;
+    S.prefetch = 0;
+    const int64_t uniform = S.tiles_x * ((rows + tile_h - 1) / tile_h);
+    S.tiles_total = uniform;
+    if (!stripes && S.tiles_x >= 3 && f < 1.0 && tile_h > 4) {
+        const int64_t cap = uniform > resident ? uniform : resident;
+        for (int64_t th = tile_h; th <= tile_h + 2; th++) {
+            int64_t eh = (int64_t)((double)th * f + 0.5);
+            eh = eh < 1 ? 1 : eh;
+            const int64_t ne = 2 * ((rows + eh - 1) / eh);
+            const int64_t total = ne + (S.tiles_x - 2) * ((rows + th - 1) / th);
+            if (eh < th && total <= cap) {
+                S.tile_h = th;
+                S.edge_h = eh;
+                S.n_edge = ne;
+                S.tiles_total = total;
+                break;
+            }
+        }
+    }
+    return S;
+}
+
+// The tile schedule of a launch over rows [row0, row1) (plan_sched with this
+// device's resident warps and the tuning overrides).
+TileSched make_sched(const Image &g, const Window &win, int64_t row0, int64_t row1, bool pipe,
+                     bool stripes)
+{
+    TileSched S = plan_sched(row0, row1, g.W, window_tile_rows(row1 - row0, g.W, win.h, win.w),
+                             resident_warps(), edge_fraction(pipe), stripes);
+    // without stripes the image is usually not in L2 yet (the stripe
+    // pre-pass has just read it otherwise).  BZ_PREFETCH=0 turns it off.
+    static const bool pf = [] {
+        const char *e = getenv("BZ_PREFETCH");
+        return !(e && atoi(e) == 0);
+    }();
+    S.prefetch = (pf && !stripes) ? 1 : 0;
+    return S;
+}
+
+// Pure form for planning and tests: the schedule on a GPU with `sms` SMs.
+int plan_tile_schedule(int64_t H, int64_t W, int sms, bool pipe, bool stripes, int64_t out[6])
+{
+    if (H < 1 || W < 1 || sms < 1)
+        return -1;
+    const int64_t resident = (int64_t)sms * kBlocksPerSM * kWarpsPerBlock;
+    const TileSched S =
+        plan_sched(0, H, W, one_wave_rows(H, W, resident), resident, default_edge_fraction(pipe), stripes);
+    out[0] = S.tiles_x;
+    out[1] = S.tile_h;
+    out[2] = S.edge_h;
+    out[3] = S.n_edge;
+    out[4] = S.tiles_total;
+    out[5] = resident;
+    return 0;
+}
+
+}  // namespace bz
