@@ -10,8 +10,9 @@ Parity status: window sums, counts, FP64 thresholds, packing and quantiles are
 pinned by the tests in ``tests/test_oracle_pins.py`` (three independent sum
 routes, closed forms, the exact 128-bit Sauvola decision, brute-force
 quantiles, hand-derived golden cases).  The FP32 threshold helper
-(``threshold_f32``) is parity unpinned: it only grades the FP32 fast path by
-tolerance.
+(``threshold_f32``), which only grades the FP32 fast path by tolerance, is
+pinned to the FP64 threshold within its own rounding-error bound
+(``tests/test_oracle_f32_pin.py``).
 """
 from __future__ import annotations
 
@@ -144,7 +145,8 @@ def threshold(method: int, S1, S2, n, k: float, R: float = 128.0) -> np.ndarray:
 
 
 def threshold_f32(method: int, S1, S2, n, k: float, R: float = 128.0) -> np.ndarray:
-    """The same formula evaluated in FP32 (parity unpinned; tolerance only)."""
+    """The same formula evaluated in FP32 (grades the FP32 path by tolerance;
+    pinned to the FP64 threshold within its own rounding-error bound)."""
     S1 = np.ascontiguousarray(S1, np.uint32)
     S2 = np.ascontiguousarray(S2, np.uint64)
     n = np.ascontiguousarray(n, np.uint32)
