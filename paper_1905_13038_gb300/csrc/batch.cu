@@ -22,7 +22,6 @@
 namespace bz {
 
 constexpr int kBatchWarps = 4;   // warps per block, window kernel
-constexpr int kQuantNT = 64;     // threads per block, quantile kernel
 
 template <int MODE>
 __global__ void __launch_bounds__(32 * kBatchWarps)
@@ -71,21 +70,20 @@ __global__ void __launch_bounds__(32 * kBatchWarps)
     }
 }
 
-// NT threads per block; U16: every job uses 16-bit counters (twice the
-// threads for the same shared memory), else each job picks its counter width.
-template <int NT, bool U16>
-__global__ void __launch_bounds__(NT) k_batch_quantile(BatchHeader *hdr, const QJobDev *jobs)
+// One warp per block; each warp pops quantile tiles (32 columns x a row band)
+// and runs the single-image tile routine in its own shared-memory arrays.
+__global__ void __launch_bounds__(32) k_batch_quantile(BatchHeader *hdr, const QJobDev *jobs)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ unsigned long long t_sh;
+    QWarpSmem &S = *reinterpret_cast<QWarpSmem *>(smem);
+    const int lane = threadIdx.x & 31;
     const int64_t total = hdr->q_tiles;
     const int nj = hdr->n_q;
     for (;;) {
-        __syncthreads();
-        if (threadIdx.x == 0)
-            t_sh = atomicAdd(&hdr->q_next, 1ull);
-        __syncthreads();
-        const unsigned long long t = t_sh;
+        unsigned long long t = 0;
+        if (lane == 0)
+            t = atomicAdd(&hdr->q_next, 1ull);
+        t = __shfl_sync(0xFFFFFFFFu, t, 0);
         if ((int64_t)t >= total)
             break;
         int lo = 0, hi = nj - 1;
@@ -99,20 +97,20 @@ __global__ void __launch_bounds__(NT) k_batch_quantile(BatchHeader *hdr, const Q
         const QJobDev &J = jobs[lo];
         const int64_t local = (int64_t)t - J.tile_begin;
         const int64_t tx = local % J.tiles_x, ty = local / J.tiles_x;
-        const int64_t x0 = tx * NT, y0 = ty * J.tile_h;
+        const int64_t x0 = tx * kQCols, y0 = ty * J.tile_h;
         const int64_t y1 = y0 + J.tile_h < J.g.H ? y0 + J.tile_h : J.g.H;
-        if (!U16 && J.ct32)
-            quantile_tile<uint32_t, NT>(J.g, J.win, J.q_num, J.q_den, J.offset, J.out, J.out_pitch,
-                                        nullptr, x0, y0, y1, smem);
+        // the batch takes the generic read-ahead width (one instantiation
+        // keeps the persistent kernel small); results do not depend on it
+        if (J.win.w >= 32)
+            quantile_warp_tile<6, true>(J.g, J.win, J.q_num, J.q_den, J.offset, J.out, J.out_pitch,
+                                        nullptr, x0, y0, y1, S, lane);
         else
-            quantile_tile<uint16_t, NT>(J.g, J.win, J.q_num, J.q_den, J.offset, J.out, J.out_pitch,
-                                        nullptr, x0, y0, y1, smem);
+            quantile_warp_tile<2, false>(J.g, J.win, J.q_num, J.q_den, J.offset, J.out, J.out_pitch,
+                                         nullptr, x0, y0, y1, S, lane);
     }
 }
 
-constexpr int kQuantNT16 = 128;  // threads per block when every job fits 16-bit counters
-static size_t batch_quant_smem() { return quantile_smem_bytes<kQuantNT>(4, 511); }
-static size_t batch_quant_smem16() { return quantile_smem_bytes<kQuantNT16>(2, 511); }
+static size_t batch_quant_smem() { return sizeof(QWarpSmem); }
 
 // ------------------------------------------------------------------ host --
 bz_status validate_job(const bz_job &j)
@@ -165,7 +163,7 @@ BatchSlot::~BatchSlot()
 
 void BatchSlot::release()
 {
-    for (int m = 0; m < 6; m++)
+    for (int m = 0; m < 3; m++)
         if (exec[m]) {
             cudaGraphExecDestroy(exec[m]);
             exec[m] = nullptr;
@@ -221,7 +219,7 @@ static bz_status ensure_capacity(BatchSlot &s, int n_win, int n_q)
         s.d_table = nullptr;
         s.h_table = nullptr;
     }
-    for (int m = 0; m < 6; m++)
+    for (int m = 0; m < 3; m++)
         if (s.exec[m]) {
             cudaGraphExecDestroy(s.exec[m]);
             s.exec[m] = nullptr;
@@ -239,23 +237,25 @@ static bz_status ensure_capacity(BatchSlot &s, int n_win, int n_q)
     return BZ_OK;
 }
 
-template <int MODE, bool U16>
+template <int MODE>
 static cudaError_t capture_graph(BatchSlot &s, cudaGraphExec_t *out)
 {
-    constexpr int NTq = U16 ? kQuantNT16 : kQuantNT;
     cudaStream_t cs = s.cap_stream;
     BatchHeader *hdr = (BatchHeader *)s.d_table;
     WinJobDev *wj = (WinJobDev *)(hdr + 1);
     QJobDev *qj = (QJobDev *)(wj + s.cap_win);
     const size_t bytes = table_bytes(s.cap_win, s.cap_q);
-    const size_t qsmem = U16 ? batch_quant_smem16() : batch_quant_smem();
-    cudaError_t e = cudaFuncSetAttribute(k_batch_quantile<NTq, U16>,
+    const size_t qsmem = batch_quant_smem();
+    cudaError_t e = cudaFuncSetAttribute(k_batch_quantile,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qsmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_batch_quantile, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess)
         return e;
     int occ_w = 0, occ_q = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_w, k_batch_window<MODE>, 32 * kBatchWarps, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_q, k_batch_quantile<NTq, U16>, NTq, qsmem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_q, k_batch_quantile, 32, qsmem);
     if (occ_w < 1)
         occ_w = 1;
     if (occ_q < 1)
@@ -268,7 +268,7 @@ static cudaError_t capture_graph(BatchSlot &s, cudaGraphExec_t *out)
     if (s.fallbacks)
         cudaMemsetAsync(s.fallbacks, 0, sizeof(unsigned long long), cs);
     k_batch_window<MODE><<<s.num_sms * occ_w, 32 * kBatchWarps, 0, cs>>>(hdr, wj, s.fallbacks);
-    k_batch_quantile<NTq, U16><<<s.num_sms * occ_q, NTq, qsmem, cs>>>(hdr, qj);
+    k_batch_quantile<<<s.num_sms * occ_q, 32, qsmem, cs>>>(hdr, qj);
     e = cudaStreamEndCapture(cs, &graph);
     if (e != cudaSuccess)
         return e;
@@ -324,10 +324,6 @@ bz_status run_batch(BatchSlot &s, const bz_job *jobs, int32_t n, bz_precision pr
         return (int64_t)jobs[a].w * (quant_tile_rows(jobs[a].H, jobs[a].h) + jobs[a].h) >
                (int64_t)jobs[b].w * (quant_tile_rows(jobs[b].H, jobs[b].h) + jobs[b].h);
     });
-    bool u16 = true;  // every quantile job fits 16-bit counters
-    for (size_t a = 0; a < qi.size(); a++)
-        u16 = u16 && (int64_t)jobs[qi[a]].h * jobs[qi[a]].w <= 65535;
-    const int NTq = u16 ? kQuantNT16 : kQuantNT;
     int64_t tb = 0;
     for (size_t a = 0; a < wi.size(); a++) {
         const bz_job &j = jobs[wi[a]];
@@ -354,11 +350,10 @@ bz_status run_batch(BatchSlot &s, const bz_job *jobs, int32_t n, bz_precision pr
         d.q_num = j.q_num;
         d.q_den = j.q_den;
         d.offset = j.offset;
-        d.ct32 = (int64_t)j.h * j.w > 65535;
         d.out = j.out;
         d.out_pitch = j.out_pitch;
         d.tile_h = quant_tile_rows(j.H, j.h);
-        d.tiles_x = (j.W + NTq - 1) / NTq;
+        d.tiles_x = (j.W + kQCols - 1) / kQCols;
         d.tile_begin = tb;
         tb += d.tiles_x * ((j.H + d.tile_h - 1) / d.tile_h);
     }
@@ -368,17 +363,11 @@ bz_status run_batch(BatchSlot &s, const bz_job *jobs, int32_t n, bz_precision pr
     hdr->win_next = 0;
     hdr->q_next = 0;
 
-    const int gi = 2 * mode + (u16 ? 1 : 0);
+    const int gi = mode;
     if (!s.exec[gi]) {
-        cudaError_t e;
-        if (u16)
-            e = mode == 0   ? capture_graph<MODE_FP64, true>(s, &s.exec[gi])
-                : mode == 1 ? capture_graph<MODE_FP32, true>(s, &s.exec[gi])
-                            : capture_graph<MODE_FP64_DIRECT, true>(s, &s.exec[gi]);
-        else
-            e = mode == 0   ? capture_graph<MODE_FP64, false>(s, &s.exec[gi])
-                : mode == 1 ? capture_graph<MODE_FP32, false>(s, &s.exec[gi])
-                            : capture_graph<MODE_FP64_DIRECT, false>(s, &s.exec[gi]);
+        const cudaError_t e = mode == 0   ? capture_graph<MODE_FP64>(s, &s.exec[gi])
+                              : mode == 1 ? capture_graph<MODE_FP32>(s, &s.exec[gi])
+                                          : capture_graph<MODE_FP64_DIRECT>(s, &s.exec[gi]);
         if (e != cudaSuccess) {
             s.exec[gi] = nullptr;
             cudaGetLastError();
@@ -472,21 +461,23 @@ template <int MODE>
 static cudaError_t noalloc_launch(NoAllocTable *dev, int nsm, cudaStream_t stream)
 {
     const size_t qsmem = batch_quant_smem();
-    cudaError_t e = cudaFuncSetAttribute(k_batch_quantile<kQuantNT, false>,
+    cudaError_t e = cudaFuncSetAttribute(k_batch_quantile,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)qsmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_batch_quantile, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess)
         return e;
     int occ_w = 0, occ_q = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_w, k_batch_window<MODE>, 32 * kBatchWarps, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_q, k_batch_quantile<kQuantNT, false>, kQuantNT,
-                                                  qsmem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_q, k_batch_quantile, 32, qsmem);
     if (occ_w < 1)
         occ_w = 1;
     if (occ_q < 1)
         occ_q = 1;
     k_batch_window<MODE><<<nsm * occ_w, 32 * kBatchWarps, 0, stream>>>(&dev->hdr, dev->win,
                                                                        &dev->fallbacks);
-    k_batch_quantile<kQuantNT, false><<<nsm * occ_q, kQuantNT, qsmem, stream>>>(&dev->hdr, dev->q);
+    k_batch_quantile<<<nsm * occ_q, 32, qsmem, stream>>>(&dev->hdr, dev->q);
     return cudaGetLastError();
 }
 
@@ -570,11 +561,10 @@ extern "C" bz_status binarize_batch_noalloc(const bz_job *jobs, int32_t n, bz_pr
         d.q_num = j.q_num;
         d.q_den = j.q_den;
         d.offset = j.offset;
-        d.ct32 = (int64_t)j.h * j.w > 65535;
         d.out = j.out;
         d.out_pitch = j.out_pitch;
         d.tile_h = quant_tile_rows(j.H, j.h);
-        d.tiles_x = (j.W + kQuantNT - 1) / kQuantNT;
+        d.tiles_x = (j.W + kQCols - 1) / kQCols;
         d.tile_begin = tb;
         tb += d.tiles_x * ((j.H + d.tile_h - 1) / d.tile_h);
     }

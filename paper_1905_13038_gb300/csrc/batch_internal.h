@@ -27,7 +27,7 @@ struct WinJobDev {
 struct QJobDev {
     Image g;
     Window win;
-    int32_t q_num, q_den, offset, ct32;
+    int32_t q_num, q_den, offset;
     uint8_t *out;
     int64_t out_pitch;
     int64_t tiles_x, tile_h, tile_begin;
@@ -45,9 +45,8 @@ struct BatchSlot {
     void *h_table = nullptr;
     cudaStream_t cap_stream = nullptr;
     cudaEvent_t done = nullptr;
-    // one graph per precision x quantile variant (2 * mode + v; v = 1: the
-    // batch's quantile jobs all fit 16-bit counters)
-    cudaGraphExec_t exec[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    // one graph per precision
+    cudaGraphExec_t exec[3] = {nullptr, nullptr, nullptr};
     unsigned long long *fallbacks = nullptr;
     ~BatchSlot();
     void release();

@@ -1,42 +1,51 @@
-// Local-quantile kernel: one block per (column strip, row band) tile.
+// Local-quantile kernel: one warp per (32-column strip, row band) tile.
+#include <stddef.h>
+
 #include "bz_internal.h"
 #include "bz_quantile.cuh"
 
 namespace bz {
 
-template <typename CT, int NT>
-__global__ void __launch_bounds__(NT)
+template <int NPF, bool CORE>
+__global__ void __launch_bounds__(32)
     k_quantile(Image g, Window win, int32_t q_num, int32_t q_den, int32_t offset, uint8_t *out,
                int64_t out_pitch, uint8_t *Qout, int64_t tiles_x, int64_t tile_h)
 {
     extern __shared__ __align__(16) unsigned char smem[];
+    QWarpSmem &S = *reinterpret_cast<QWarpSmem *>(smem);
     const int64_t tx = blockIdx.x % tiles_x, ty = blockIdx.x / tiles_x;
-    const int64_t x0 = tx * NT, y0 = ty * tile_h;
+    const int64_t x0 = tx * kQCols, y0 = ty * tile_h;
     const int64_t y1 = y0 + tile_h < g.H ? y0 + tile_h : g.H;
-    quantile_tile<CT, NT>(g, win, q_num, q_den, offset, out, out_pitch, Qout, x0, y0, y1, smem);
+    quantile_warp_tile<NPF, CORE>(g, win, q_num, q_den, offset, out, out_pitch, Qout, x0, y0, y1, S,
+                       threadIdx.x & 31);
 }
 
-template <typename CT, int NT>
+template <int NPF, bool CORE>
 static cudaError_t launch_q(const Image &g, const Window &win, int32_t q_num, int32_t q_den,
                             int32_t offset, uint8_t *out, int64_t out_pitch, uint8_t *Q,
                             cudaStream_t stream)
 {
-    const size_t smem = quantile_smem_bytes<NT>(sizeof(CT), win.w);
-    cudaError_t e = cudaFuncSetAttribute(k_quantile<CT, NT>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const auto kernel = k_quantile<NPF, CORE>;
+    const size_t smem = sizeof(QWarpSmem);
+    cudaError_t e =
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
-    // One wave: as many row bands as the resident-block slots allow for the
-    // column strips (the histograms in shared memory cap residency at a few
-    // blocks per SM, so a second, partial wave would leave most SMs idle).
+    // eight warps' arrays per SM need the whole shared-memory carve-out
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess)
+        return e;
+    // One wave: as many row bands as the resident warps allow for the column
+    // strips (the histograms cap residency at a few warps per SM, so a
+    // second, partial wave would leave most SMs idle).
     int dev = 0, sms = 152, per_sm = 1;
     if (cudaGetDevice(&dev) == cudaSuccess)
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_quantile<CT, NT>, NT, smem) !=
-            cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 32, smem) != cudaSuccess ||
         per_sm < 1)
         per_sm = 1;
-    const int64_t tiles_x = (g.W + NT - 1) / NT;
+    const int64_t tiles_x = (g.W + kQCols - 1) / kQCols;
     int64_t bands = ((int64_t)sms * per_sm) / tiles_x;
     if (bands < 1)
         bands = 1;
@@ -44,8 +53,8 @@ static cudaError_t launch_q(const Image &g, const Window &win, int32_t q_num, in
     if (tile_h < 1)
         tile_h = 1;
     const int64_t tiles_y = (g.H + tile_h - 1) / tile_h;
-    k_quantile<CT, NT><<<(unsigned)(tiles_x * tiles_y), NT, smem, stream>>>(
-        g, win, q_num, q_den, offset, out, out_pitch, Q, tiles_x, tile_h);
+    kernel<<<(unsigned)(tiles_x * tiles_y), 32, smem, stream>>>(g, win, q_num, q_den, offset, out,
+                                                                   out_pitch, Q, tiles_x, tile_h);
     return cudaGetLastError();
 }
 
@@ -53,9 +62,13 @@ cudaError_t launch_quantile(const Image &g, const Window &win, int32_t q_num, in
                             int32_t offset, uint8_t *out, int64_t out_pitch, uint8_t *Q,
                             cudaStream_t stream)
 {
-    if ((int64_t)win.h * win.w <= 65535)
-        return launch_q<uint16_t, 128>(g, win, q_num, q_den, offset, out, out_pitch, Q, stream);
-    return launch_q<uint32_t, 64>(g, win, q_num, q_den, offset, out, out_pitch, Q, stream);
+    switch (quantile_prefetch(win.w)) {
+    case 2:
+        return win.w >= 32 ? launch_q<2, true>(g, win, q_num, q_den, offset, out, out_pitch, Q, stream)
+                           : launch_q<2, false>(g, win, q_num, q_den, offset, out, out_pitch, Q, stream);
+    case 4: return launch_q<4, true>(g, win, q_num, q_den, offset, out, out_pitch, Q, stream);
+    default: return launch_q<6, true>(g, win, q_num, q_den, offset, out, out_pitch, Q, stream);
+    }
 }
 
 }  // namespace bz
