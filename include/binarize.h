@@ -378,9 +378,18 @@ bz_status binarize_batch(const bz_job *jobs_host, int32_t n,
  * is part of the library image (about 150 KB, held by every GPU that loads
  * the library until the process exits), and it calls no allocation routine.
  *   - n <= BZ_NOALLOC_MAX_JOBS; larger n returns BZ_EINVAL, nothing launched.
- *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress, with that device current); make that first
- *     call before any stream capture on the device.
+ *   - The array is placed on a device when the library's CUDA module is
+ *     loaded there.  Under CUDA's default lazy module loading that happens at
+ *     the first call on the device (which also looks up the array's device
+ *     address with cudaGetSymbolAddress and sets the kernels' attributes), so
+ *     a caller that reserves all of its device memory afterwards must make
+ *     one call, or any other library call, first; with
+ *     CUDA_MODULE_LOADING=EAGER the array is placed when the context is
+ *     created.  Later calls place nothing and allocate nothing.
+ *   - Not for stream capture: each call stages the work list in one static
+ *     host buffer that the next call overwrites, so a captured copy would
+ *     replay another call's list.  A call on a capturing stream returns
+ *     BZ_EINVAL and enqueues nothing.
  *   - Every call on a device shares the one work list: calls whose work
  *     overlaps on the GPU (for instance on two streams) race and corrupt each
  *     other's list.  Order them on one stream or synchronise in between.
@@ -409,6 +418,81 @@ bz_status bz_server_wait(bz_server *srv, uint64_t ticket, int32_t timeout_ms);
 bz_status bz_server_cancel(bz_server *srv, uint64_t ticket);
 /* Cancels queued requests, waits for the in-flight ones, frees the server. */
 bz_status bz_server_destroy(bz_server *srv);
+
+/* ---------------------------------------------------------------------- */
+/* Autotuning of launch parameters (no counterpart in the paper: how the  */
+/* work of Algorithm 1 and Sec. 3.4 is split over the GPU).               */
+/* ---------------------------------------------------------------------- */
+/* Tuned: the window kernel's tile height, edge-tile fraction and stripe
+ * pre-pass (Sauvola / Niblack in every binarize precision), the quantile
+ * kernel's row-band height, and the batched kernels' tile rows (multiples of
+ * each job's window height).  Every candidate computes the same bits; only
+ * the work split and so the time changes.  Candidates are timed with CUDA
+ * events on the call's stream and the fastest is kept in a JSON cache keyed
+ * by GPU name and SM count, kernel, precision (or quantile class: q < 1/4,
+ * 1/4 <= q <= 3/4, q > 3/4), window buckets (next power of two of h and of w)
+ * and image-size bucket (floor(2 log2(H W))).
+ *   Environment: BZ_TUNE unset - launches use cached entries and never tune
+ *   by themselves; BZ_TUNE=0 - the cache is ignored (built-in heuristics);
+ *   BZ_TUNE=1 - a launch without a cached entry tunes itself first
+ *   (synchronously).  BZ_TILE_ROWS, BZ_EDGE_FRAC and BZ_STRIPES, when set,
+ *   take precedence over the cache.  The cache file is BZ_TUNE_CACHE, else
+ *   $XDG_CACHE_HOME/paper_1905_13038_gb300/tune.json, else
+ *   $HOME/.cache/paper_1905_13038_gb300/tune.json; a missing or malformed
+ *   file reads as an empty cache and is rewritten whole after each tuning. */
+
+/* Explicit tuning: performs the same binarization as binarize_sauvola
+ * (method 0) / binarize_niblack (method 1) / binarize_quantile /
+ * binarize_batch with the same arguments and errors, tuning first (the call
+ * synchronizes `stream`), stores the winner and returns it: tile_h (0 when
+ * the call takes a path without tunable parameters, the small-page kernel),
+ * edge fraction (1 = uniform tiles), stripes (0/1), us = measured
+ * microseconds per call; the batch returns its window and quantile tile
+ * multipliers.  Each output pointer may be NULL. */
+bz_status bz_autotune_window(int32_t method, const uint8_t *image, int64_t H,
+                             int64_t W, int64_t in_pitch, int32_t h, int32_t w,
+                             double k, double R, uint8_t *out, int64_t out_pitch,
+                             bz_precision precision, void *stream,
+                             int32_t *tile_h, float *edge, int32_t *stripes,
+                             float *us);
+bz_status bz_autotune_quantile(const uint8_t *image, int64_t H, int64_t W,
+                               int64_t in_pitch, int32_t h, int32_t w,
+                               int32_t q_num, int32_t q_den, int32_t offset,
+                               uint8_t *out, int64_t out_pitch, void *stream,
+                               int32_t *tile_h, float *us);
+bz_status bz_autotune_batch(const bz_job *jobs_host, int32_t n,
+                            bz_precision precision, void *stream,
+                            int32_t *win_mult, int32_t *quant_mult, float *us);
+
+/* Cache access (host only, no GPU needed).  Keys are built by bz_tune_key
+ * from a GPU tag ("<name>/<SMs>"), a kernel ("window", "quantile",
+ * "batch"), a class (window: 0 BZ_FP64, 1 BZ_FP32, 2 BZ_FP64_DIRECT;
+ * quantile: the q class above; batch: the precision), h, w, H, W; it writes
+ * the NUL-terminated key to buf (len bytes) and returns its length, or -1.
+ * bz_tune_get: 1 and the fields when the key is cached, 0 when not, -1 on a
+ * NULL key.  bz_tune_set: stores an entry in memory (0, or -1 on a bad
+ * field: tile_h < 0, edge outside [0, 1], stripes outside [-1, 64]).
+ * bz_tune_load: replaces the in-memory cache by the file's (path NULL: the
+ * default path) and returns the number of entries, -1 when the file cannot
+ * be read, -2 when it is malformed (the cache is then empty).  bz_tune_save:
+ * writes the cache (path NULL: the path last loaded), 0 or -1.
+ * bz_tune_window_plan: the window-kernel plan a binarize launch of an
+ * H x W image would use on a GPU tagged `gpu` with `sms` SMs, cache
+ * included: out[0..5] = tile_h, edge_h, edge tiles, tiles, stripes, resident
+ * warps; returns 1 when a cached entry applied, 0 for the heuristics, -1 on
+ * bad arguments. */
+int32_t bz_tune_key(const char *gpu, const char *kernel, int32_t cls, int32_t h,
+                    int32_t w, int64_t H, int64_t W, char *buf, int32_t len);
+int32_t bz_tune_get(const char *key, int32_t *tile_h, float *edge,
+                    int32_t *stripes, float *us);
+int32_t bz_tune_set(const char *key, int32_t tile_h, float edge,
+                    int32_t stripes, float us);
+int32_t bz_tune_load(const char *path);
+int32_t bz_tune_save(const char *path);
+void bz_tune_clear(void);
+int32_t bz_tune_window_plan(const char *gpu, int32_t precision, int64_t H,
+                            int64_t W, int32_t h, int32_t w, int32_t sms,
+                            int64_t *out);
 
 #ifdef __cplusplus
 }

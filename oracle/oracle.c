@@ -25,8 +25,9 @@
  *   Packed output: bit (j & 7) of byte (j >> 3) of the row, LSB first,
  *     padding bits 0.
  *
- * Readings where the paper is silent are listed in the design notes; the
- * canonical floating-point threshold evaluation order is one of them:
+ * The paper does not fix a floating-point evaluation order for the
+ * threshold; this file evaluates it in IEEE binary64, round to nearest, every
+ * operation rounded and none contracted, in this order:
  *     nd = n; m = S1/nd; s = sqrt(V/(nd*nd));
  *     Sauvola t = m*(1 + k*(s/R - 1));   Niblack t = m + k*s.
  * In exact arithmetic this equals the Sec. 1 definition since s^2 = S2/n - m^2.

@@ -135,10 +135,15 @@ bz_status validate_job(const bz_job &j)
     return BZ_OK;
 }
 
-static int64_t batch_tile_rows(int64_t H, int h)
+// Tile rows of a batched job: `mult` window heights (in a batch the
+// parallelism comes from many images, so tiles are tall), at least 48 rows
+// (window jobs) or 64 (quantile jobs).  The multipliers are 3 and 2 unless
+// the autotuner's cache holds others for this GPU and precision.
+constexpr int kBatchWinMult = 3, kBatchQuantMult = 2;
+
+static int64_t batch_tile_rows(int64_t H, int h, int mult = kBatchWinMult)
 {
-    // in a batch the parallelism comes from many images: favour tall tiles
-    int64_t th = 3 * (int64_t)h;
+    int64_t th = (int64_t)mult * h;
     if (th < 48)
         th = 48;
     if (th > H)
@@ -146,9 +151,9 @@ static int64_t batch_tile_rows(int64_t H, int h)
     return th;
 }
 
-static int64_t quant_tile_rows(int64_t H, int h)
+static int64_t quant_tile_rows(int64_t H, int h, int mult = kBatchQuantMult)
 {
-    int64_t th = 2 * (int64_t)h;
+    int64_t th = (int64_t)mult * h;
     if (th < 64)
         th = 64;
     if (th > H)
@@ -312,56 +317,59 @@ bz_status run_batch(BatchSlot &s, const bz_job *jobs, int32_t n, bz_precision pr
     BatchHeader *hdr = (BatchHeader *)s.h_table;
     WinJobDev *wj = (WinJobDev *)(hdr + 1);
     QJobDev *qj = (QJobDev *)(wj + s.cap_win);
-    // order: most expensive tiles first (longest warm-up + tile), then by size
     std::vector<int> wi, qi;
     for (int32_t i = 0; i < n; i++)
         (jobs[i].method == BZ_QUANTILE ? qi : wi).push_back(i);
-    std::stable_sort(wi.begin(), wi.end(), [&](int a, int b) {
-        return batch_tile_rows(jobs[a].H, jobs[a].h) + jobs[a].h >
-               batch_tile_rows(jobs[b].H, jobs[b].h) + jobs[b].h;
-    });
-    std::stable_sort(qi.begin(), qi.end(), [&](int a, int b) {
-        return (int64_t)jobs[a].w * (quant_tile_rows(jobs[a].H, jobs[a].h) + jobs[a].h) >
-               (int64_t)jobs[b].w * (quant_tile_rows(jobs[b].H, jobs[b].h) + jobs[b].h);
-    });
-    int64_t tb = 0;
-    for (size_t a = 0; a < wi.size(); a++) {
-        const bz_job &j = jobs[wi[a]];
-        WinJobDev &d = wj[a];
-        d.g = Image{j.image, j.H, j.W, j.in_pitch};
-        d.win = make_window(j.h, j.w);
-        d.T = make_thresh(j.method == BZ_SAUVOLA ? 0 : 1, j.k, j.method == BZ_SAUVOLA ? j.R : 128.0);
-        d.out = j.out;
-        d.out_pitch = j.out_pitch;
-        d.tile_h = batch_tile_rows(j.H, j.h);
-        d.tiles_x = (j.W + kTileCols - 1) / kTileCols;
-        d.tile_begin = tb;
-        d.vec = ((uintptr_t)j.image % 8 == 0) && (j.in_pitch % 8 == 0);
-        d.wide = (int64_t)j.h * j.w > 66051;
-        tb += d.tiles_x * ((j.H + d.tile_h - 1) / d.tile_h);
-    }
-    hdr->win_tiles = tb;
-    tb = 0;
-    for (size_t a = 0; a < qi.size(); a++) {
-        const bz_job &j = jobs[qi[a]];
-        QJobDev &d = qj[a];
-        d.g = Image{j.image, j.H, j.W, j.in_pitch};
-        d.win = make_window(j.h, j.w);
-        d.q_num = j.q_num;
-        d.q_den = j.q_den;
-        d.offset = j.offset;
-        d.out = j.out;
-        d.out_pitch = j.out_pitch;
-        d.tile_h = quant_tile_rows(j.H, j.h);
-        d.tiles_x = (j.W + kQCols - 1) / kQCols;
-        d.tile_begin = tb;
-        tb += d.tiles_x * ((j.H + d.tile_h - 1) / d.tile_h);
-    }
-    hdr->q_tiles = tb;
-    hdr->n_win = n_win;
-    hdr->n_q = n_q;
-    hdr->win_next = 0;
-    hdr->q_next = 0;
+    // the work list for tile multipliers (mw, mq), in the pinned table
+    auto fill = [&](int mw, int mq) {
+        // order: most expensive tiles first (longest warm-up + tile), then by size
+        std::stable_sort(wi.begin(), wi.end(), [&](int a, int b) {
+            return batch_tile_rows(jobs[a].H, jobs[a].h, mw) + jobs[a].h >
+                   batch_tile_rows(jobs[b].H, jobs[b].h, mw) + jobs[b].h;
+        });
+        std::stable_sort(qi.begin(), qi.end(), [&](int a, int b) {
+            return (int64_t)jobs[a].w * (quant_tile_rows(jobs[a].H, jobs[a].h, mq) + jobs[a].h) >
+                   (int64_t)jobs[b].w * (quant_tile_rows(jobs[b].H, jobs[b].h, mq) + jobs[b].h);
+        });
+        int64_t tb = 0;
+        for (size_t a = 0; a < wi.size(); a++) {
+            const bz_job &j = jobs[wi[a]];
+            WinJobDev &d = wj[a];
+            d.g = Image{j.image, j.H, j.W, j.in_pitch};
+            d.win = make_window(j.h, j.w);
+            d.T = make_thresh(j.method == BZ_SAUVOLA ? 0 : 1, j.k, j.method == BZ_SAUVOLA ? j.R : 128.0);
+            d.out = j.out;
+            d.out_pitch = j.out_pitch;
+            d.tile_h = batch_tile_rows(j.H, j.h, mw);
+            d.tiles_x = (j.W + kTileCols - 1) / kTileCols;
+            d.tile_begin = tb;
+            d.vec = ((uintptr_t)j.image % 8 == 0) && (j.in_pitch % 8 == 0);
+            d.wide = (int64_t)j.h * j.w > 66051;
+            tb += d.tiles_x * ((j.H + d.tile_h - 1) / d.tile_h);
+        }
+        hdr->win_tiles = tb;
+        tb = 0;
+        for (size_t a = 0; a < qi.size(); a++) {
+            const bz_job &j = jobs[qi[a]];
+            QJobDev &d = qj[a];
+            d.g = Image{j.image, j.H, j.W, j.in_pitch};
+            d.win = make_window(j.h, j.w);
+            d.q_num = j.q_num;
+            d.q_den = j.q_den;
+            d.offset = j.offset;
+            d.out = j.out;
+            d.out_pitch = j.out_pitch;
+            d.tile_h = quant_tile_rows(j.H, j.h, mq);
+            d.tiles_x = (j.W + kQCols - 1) / kQCols;
+            d.tile_begin = tb;
+            tb += d.tiles_x * ((j.H + d.tile_h - 1) / d.tile_h);
+        }
+        hdr->q_tiles = tb;
+        hdr->n_win = n_win;
+        hdr->n_q = n_q;
+        hdr->win_next = 0;
+        hdr->q_next = 0;
+    };
 
     const int gi = mode;
     if (!s.exec[gi]) {
@@ -374,11 +382,69 @@ bz_status run_batch(BatchSlot &s, const bz_job *jobs, int32_t n, bz_precision pr
             return BZ_ECUDA;
         }
     }
-    if (cudaGraphLaunch(s.exec[gi], stream) != cudaSuccess)
-        return BZ_ECUDA;
-    if (cudaEventRecord(s.done, stream) != cudaSuccess)
-        return BZ_ECUDA;
-    return BZ_OK;
+    auto launch = [&]() -> bz_status {
+        if (cudaGraphLaunch(s.exec[gi], stream) != cudaSuccess)
+            return BZ_ECUDA;
+        if (cudaEventRecord(s.done, stream) != cudaSuccess)
+            return BZ_ECUDA;
+        return BZ_OK;
+    };
+
+    // tile multipliers: the cached ones for this GPU and precision, found by
+    // a timed search when asked (explicit tuning call or BZ_TUNE=1)
+    int mw = kBatchWinMult, mq = kBatchQuantMult;
+    if (tune_env() != 0 || tune_forced()) {
+        const std::string key = batch_tune_key(mode);
+        TuneCfg c;
+        bool have = tune_get(key, c);
+        if (tune_now(have)) {
+            double best = -1.0;
+            const int mws[4] = {2, 3, 4, 6}, mqs[4] = {1, 2, 3, 4};
+            cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+            if (cudaEventCreate(&ev0) == cudaSuccess && cudaEventCreate(&ev1) == cudaSuccess) {
+                for (int a = 0; a < 4; a++) {
+                    for (int b = 0; b < 4; b++) {
+                        float ms = 0.0f, tot = 0.0f;
+                        bool ok = true;
+                        for (int rep = 0; rep < 3 && ok; rep++) {  // rep 0 untimed
+                            ok = cudaEventSynchronize(s.done) == cudaSuccess;
+                            fill(mws[a], mqs[b]);
+                            ok = ok && cudaEventRecord(ev0, stream) == cudaSuccess && launch() == BZ_OK &&
+                                 cudaEventRecord(ev1, stream) == cudaSuccess &&
+                                 cudaEventSynchronize(ev1) == cudaSuccess &&
+                                 cudaEventElapsedTime(&ms, ev0, ev1) == cudaSuccess;
+                            if (rep > 0)
+                                tot += ms;
+                        }
+                        if (ok && (best < 0.0 || tot / 2.0 < best)) {
+                            best = tot / 2.0;
+                            c.tile_h = mws[a];
+                            c.stripes = mqs[b];
+                            c.edge = 1.0f;
+                            c.us = (float)(best * 1e3);
+                        }
+                    }
+                }
+            }
+            if (ev0)
+                cudaEventDestroy(ev0);
+            if (ev1)
+                cudaEventDestroy(ev1);
+            cudaGetLastError();
+            if (best > 0.0) {
+                have = true;
+                tune_put(key, c, true);
+            }
+            if (cudaEventSynchronize(s.done) != cudaSuccess)
+                return BZ_ECUDA;
+        }
+        if (have && c.tile_h >= 1 && c.tile_h <= 16 && c.stripes >= 1 && c.stripes <= 16) {
+            mw = c.tile_h;
+            mq = c.stripes;
+        }
+    }
+    fill(mw, mq);
+    return launch();
 }
 
 static BatchSlot *default_slot(int device)
@@ -457,8 +523,16 @@ static void *noalloc_scratch_address(int device)
     return g_noalloc_dev[device];
 }
 
+// Per device and precision, once: kernel attributes and resident blocks per
+// SM of the two persistent kernels (guarded by g_noalloc_mu).
+struct NoAllocLaunch {
+    bool ready = false;
+    int grid_w = 0, grid_q = 0;
+};
+static NoAllocLaunch g_noalloc_launch[64][3];
+
 template <int MODE>
-static cudaError_t noalloc_launch(NoAllocTable *dev, int nsm, cudaStream_t stream)
+static cudaError_t noalloc_prepare(NoAllocLaunch &L, int nsm)
 {
     const size_t qsmem = batch_quant_smem();
     cudaError_t e = cudaFuncSetAttribute(k_batch_quantile,
@@ -471,13 +545,18 @@ static cudaError_t noalloc_launch(NoAllocTable *dev, int nsm, cudaStream_t strea
     int occ_w = 0, occ_q = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_w, k_batch_window<MODE>, 32 * kBatchWarps, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_q, k_batch_quantile, 32, qsmem);
-    if (occ_w < 1)
-        occ_w = 1;
-    if (occ_q < 1)
-        occ_q = 1;
-    k_batch_window<MODE><<<nsm * occ_w, 32 * kBatchWarps, 0, stream>>>(&dev->hdr, dev->win,
-                                                                       &dev->fallbacks);
-    k_batch_quantile<<<nsm * occ_q, 32, qsmem, stream>>>(&dev->hdr, dev->q);
+    L.grid_w = nsm * (occ_w < 1 ? 1 : occ_w);
+    L.grid_q = nsm * (occ_q < 1 ? 1 : occ_q);
+    L.ready = true;
+    return cudaSuccess;
+}
+
+template <int MODE>
+static cudaError_t noalloc_launch(NoAllocTable *dev, const NoAllocLaunch &L, cudaStream_t stream)
+{
+    k_batch_window<MODE><<<L.grid_w, 32 * kBatchWarps, 0, stream>>>(&dev->hdr, dev->win,
+                                                                    &dev->fallbacks);
+    k_batch_quantile<<<L.grid_q, 32, batch_quant_smem(), stream>>>(&dev->hdr, dev->q);
     return cudaGetLastError();
 }
 
@@ -508,14 +587,35 @@ extern "C" bz_status binarize_batch_noalloc(const bz_job *jobs, int32_t n, bz_pr
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess)
         return BZ_ECUDA;
-    int nsm = 0;
-    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
+    if (dev < 0 || dev >= 64)
         return BZ_ECUDA;
+    // the static host staging copy is overwritten by the next call, so a
+    // captured copy would replay someone else's list
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing((cudaStream_t)stream, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        return BZ_ECUDA;
+    }
+    if (cap != cudaStreamCaptureStatusNone)
+        return BZ_EINVAL;
 
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
     NoAllocTable *dtab = (NoAllocTable *)noalloc_scratch_address(dev);
     if (!dtab)
         return BZ_ECUDA;
+    NoAllocLaunch &L = g_noalloc_launch[dev][mode];
+    if (!L.ready) {
+        int nsm = 0;
+        if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1)
+            return BZ_ECUDA;
+        const cudaError_t pe = mode == 0   ? noalloc_prepare<MODE_FP64>(L, nsm)
+                               : mode == 1 ? noalloc_prepare<MODE_FP32>(L, nsm)
+                                           : noalloc_prepare<MODE_FP64_DIRECT>(L, nsm);
+        if (pe != cudaSuccess) {
+            cudaGetLastError();
+            return BZ_ECUDA;
+        }
+    }
     NoAllocTable &t = g_noalloc_host;
     // window jobs first, most expensive tiles first (same order as binarize_batch)
     int nw = 0, nq = 0;
@@ -588,8 +688,8 @@ extern "C" bz_status binarize_batch_noalloc(const bz_job *jobs, int32_t n, bz_pr
     if (nq > 0 && cudaMemcpyAsync(dtab->q, t.q, sizeof(QJobDev) * (size_t)nq,
                                   cudaMemcpyHostToDevice, (cudaStream_t)stream) != cudaSuccess)
         return BZ_ECUDA;
-    const cudaError_t e = mode == 0   ? noalloc_launch<MODE_FP64>(dtab, nsm, (cudaStream_t)stream)
-                          : mode == 1 ? noalloc_launch<MODE_FP32>(dtab, nsm, (cudaStream_t)stream)
-                                      : noalloc_launch<MODE_FP64_DIRECT>(dtab, nsm, (cudaStream_t)stream);
+    const cudaError_t e = mode == 0   ? noalloc_launch<MODE_FP64>(dtab, L, (cudaStream_t)stream)
+                          : mode == 1 ? noalloc_launch<MODE_FP32>(dtab, L, (cudaStream_t)stream)
+                                      : noalloc_launch<MODE_FP64_DIRECT>(dtab, L, (cudaStream_t)stream);
     return e == cudaSuccess ? BZ_OK : BZ_ECUDA;
 }
