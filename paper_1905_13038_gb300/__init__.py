@@ -28,6 +28,8 @@ __all__ = [
     "binarize_nick", "binarize_phansalkar", "global_stats", "binarize_precision_report_ext",
     "window_minmax", "binarize_bernsen", "haar_feature", "HAAR_FEATURES", "binarize_inplace",
     "inplace_scratch_bytes", "binarize_host", "binarize_host_multi",
+    "autotune_window", "autotune_quantile", "autotune_batch", "tune_key", "tune_get", "tune_set",
+    "tune_load", "tune_save", "tune_clear", "tune_window_plan",
 ]
 
 FP64, FP32, FP64_DIRECT = 0, 1, 2
@@ -112,6 +114,16 @@ def _load():
         "bz_server_wait": ([P, ctypes.c_uint64, i32], st),
         "bz_server_cancel": ([P, ctypes.c_uint64], st),
         "bz_server_destroy": ([P], st),
+        "bz_autotune_window": ([i32, P, i64, i64, i64, i32, i32, f64, f64, P, i64, st, P, P, P, P, P], st),
+        "bz_autotune_quantile": ([P, i64, i64, i64, i32, i32, i32, i32, i32, P, i64, P, P, P], st),
+        "bz_autotune_batch": ([ctypes.POINTER(_JobC), i32, st, P, P, P, P], st),
+        "bz_tune_key": ([ctypes.c_char_p, ctypes.c_char_p, i32, i32, i32, i64, i64, ctypes.c_char_p, i32], i32),
+        "bz_tune_get": ([ctypes.c_char_p, P, P, P, P], i32),
+        "bz_tune_set": ([ctypes.c_char_p, i32, ctypes.c_float, i32, ctypes.c_float], i32),
+        "bz_tune_load": ([ctypes.c_char_p], i32),
+        "bz_tune_save": ([ctypes.c_char_p], i32),
+        "bz_tune_clear": ([], None),
+        "bz_tune_window_plan": ([ctypes.c_char_p, i32, i64, i64, i32, i32, i32, P], i32),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -499,3 +511,86 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------- autotuner --
+def autotune_window(method: int, image, h: int, w: int, k: float = 0.5, R: float = 128.0, out=None,
+                    precision="fp64", W: int | None = None, stream=None):
+    """Binarize (method SAUVOLA or NIBLACK) after tuning the window kernel's
+    launch for this shape; returns (out, {"tile_h", "edge", "stripes", "us"})."""
+    ptr, H, W, pitch = _image(image, W)
+    out, op = _out(out, H, W, image.device)
+    th, st_, = ctypes.c_int32(), ctypes.c_int32()
+    edge, us = ctypes.c_float(), ctypes.c_float()
+    _check("bz_autotune_window", _load().bz_autotune_window(
+        method, ptr, H, W, pitch, h, w, k, R, out.data_ptr(), op, _PREC[precision], _stream(stream),
+        ctypes.byref(th), ctypes.byref(edge), ctypes.byref(st_), ctypes.byref(us)))
+    return out, {"tile_h": th.value, "edge": round(edge.value, 4), "stripes": st_.value, "us": us.value}
+
+
+def autotune_quantile(image, h: int, w: int, q_num: int = 1, q_den: int = 2, offset: int = 8, out=None,
+                      W: int | None = None, stream=None):
+    """binarize_quantile after tuning the row-band height; returns (out, {"tile_h", "us"})."""
+    ptr, H, W, pitch = _image(image, W)
+    out, op = _out(out, H, W, image.device)
+    th, us = ctypes.c_int32(), ctypes.c_float()
+    _check("bz_autotune_quantile", _load().bz_autotune_quantile(
+        ptr, H, W, pitch, h, w, q_num, q_den, offset, out.data_ptr(), op, _stream(stream),
+        ctypes.byref(th), ctypes.byref(us)))
+    return out, {"tile_h": th.value, "us": us.value}
+
+
+def autotune_batch(jobs, precision="fp64", stream=None):
+    """binarize_batch after tuning the batch tile multipliers; returns
+    {"win_mult", "quant_mult", "us"}."""
+    arr = (_JobC * len(jobs))(*[j.c for j in jobs])
+    a, b, us = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float()
+    _check("bz_autotune_batch", _load().bz_autotune_batch(arr, len(jobs), _PREC[precision], _stream(stream),
+                                                          ctypes.byref(a), ctypes.byref(b), ctypes.byref(us)))
+    return {"win_mult": a.value, "quant_mult": b.value, "us": us.value}
+
+
+def tune_key(gpu: str, kernel: str, cls: int, h: int, w: int, H: int, W: int) -> str:
+    buf = ctypes.create_string_buffer(256)
+    n = _load().bz_tune_key(gpu.encode(), kernel.encode(), cls, h, w, H, W, buf, 256)
+    if n < 0:
+        raise ValueError("bz_tune_key rejected its arguments")
+    return buf.value.decode()
+
+
+def tune_get(key: str):
+    """The cached entry of `key` as a dict, or None."""
+    th, st_ = ctypes.c_int32(), ctypes.c_int32()
+    edge, us = ctypes.c_float(), ctypes.c_float()
+    r = _load().bz_tune_get(key.encode(), ctypes.byref(th), ctypes.byref(edge), ctypes.byref(st_),
+                            ctypes.byref(us))
+    if r < 0:
+        raise ValueError("bz_tune_get: no key")
+    return None if r == 0 else {"tile_h": th.value, "edge": edge.value, "stripes": st_.value, "us": us.value}
+
+
+def tune_set(key: str, tile_h: int, edge: float, stripes: int, us: float = 0.0) -> None:
+    if _load().bz_tune_set(key.encode(), tile_h, edge, stripes, us) != 0:
+        raise ValueError("bz_tune_set rejected the entry")
+
+
+def tune_load(path: str | None = None) -> int:
+    return _load().bz_tune_load(path.encode() if path else None)
+
+
+def tune_save(path: str | None = None) -> int:
+    return _load().bz_tune_save(path.encode() if path else None)
+
+
+def tune_clear() -> None:
+    _load().bz_tune_clear()
+
+
+def tune_window_plan(gpu: str, precision, H: int, W: int, h: int, w: int, sms: int):
+    """(cached?, {"tile_h", "edge_h", "n_edge", "tiles", "stripes", "resident"})."""
+    out = (ctypes.c_int64 * 6)()
+    r = _load().bz_tune_window_plan(gpu.encode(), _PREC[precision], H, W, h, w, sms, out)
+    if r < 0:
+        raise ValueError("bz_tune_window_plan rejected its arguments")
+    names = ("tile_h", "edge_h", "n_edge", "tiles", "stripes", "resident")
+    return bool(r), dict(zip(names, list(out)))

@@ -769,6 +769,80 @@ int64_t bz_inplace_scratch_bytes(int64_t H, int64_t W, int32_t h, int64_t band_r
     return 2 * band * ((W + 7) / 8);
 }
 
+// ---- explicit tuning calls: the same work as the binarize call, with the
+// autotuner's timed search forced for it (tune.cu); the chosen configuration
+// is stored in the cache and returned.
+bz_status bz_autotune_window(int32_t method, const uint8_t *image, int64_t H, int64_t W, int64_t in_pitch,
+                             int32_t h, int32_t w, double k, double R, uint8_t *out, int64_t out_pitch,
+                             bz_precision precision, void *stream, int32_t *tile_h, float *edge,
+                             int32_t *stripes, float *us)
+{
+    if (method != 0 && method != 1)
+        return BZ_EINVAL;
+    bz_status st;
+    {
+        TuneForce force;
+        st = run_threshold(method, image, H, W, in_pitch, h, w, k, method == 0 ? R : 128.0, out, out_pitch,
+                           precision, stream);
+    }
+    if (st != BZ_OK)
+        return st;
+    const int mode = precision == BZ_FP64 ? MODE_FP64 : (precision == BZ_FP32 ? MODE_FP32 : MODE_FP64_DIRECT);
+    TuneCfg c;  // zeros: the call took a path without tunable parameters
+    tune_get(window_tune_key(mode, make_window(h, w), H, W), c);
+    if (tile_h)
+        *tile_h = c.tile_h;
+    if (edge)
+        *edge = c.edge;
+    if (stripes)
+        *stripes = c.stripes;
+    if (us)
+        *us = c.us;
+    return BZ_OK;
+}
+
+bz_status bz_autotune_quantile(const uint8_t *image, int64_t H, int64_t W, int64_t in_pitch, int32_t h,
+                               int32_t w, int32_t q_num, int32_t q_den, int32_t offset, uint8_t *out,
+                               int64_t out_pitch, void *stream, int32_t *tile_h, float *us)
+{
+    bz_status st;
+    {
+        TuneForce force;
+        st = binarize_quantile(image, H, W, in_pitch, h, w, q_num, q_den, offset, out, out_pitch, stream);
+    }
+    if (st != BZ_OK)
+        return st;
+    TuneCfg c;
+    tune_get(quantile_tune_key(q_num, q_den, make_window(h, w), H, W), c);
+    if (tile_h)
+        *tile_h = c.tile_h;
+    if (us)
+        *us = c.us;
+    return BZ_OK;
+}
+
+bz_status bz_autotune_batch(const bz_job *jobs_host, int32_t n, bz_precision precision, void *stream,
+                            int32_t *win_mult, int32_t *quant_mult, float *us)
+{
+    bz_status st;
+    {
+        TuneForce force;
+        st = binarize_batch(jobs_host, n, precision, stream);
+    }
+    if (st != BZ_OK)
+        return st;
+    const int mode = precision == BZ_FP64 ? 0 : (precision == BZ_FP32 ? 1 : 2);
+    TuneCfg c;
+    tune_get(batch_tune_key(mode), c);
+    if (win_mult)
+        *win_mult = c.tile_h;
+    if (quant_mult)
+        *quant_mult = c.stripes;
+    if (us)
+        *us = c.us;
+    return BZ_OK;
+}
+
 int32_t bz_kernels_per_call(int64_t H, int64_t W, int32_t h, int32_t w, bz_precision precision)
 {
     if (H < 1 || W < 1 || h < 1 || w < 1)

@@ -3,6 +3,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
+#include <string>
+
 #include "../../include/binarize.h"
 #include "bz_window.cuh"
 
@@ -114,6 +117,69 @@ cudaError_t launch_minmax(const Image &g, const Window &win, int32_t contrast_li
 cudaError_t launch_quantile(const Image &g, const Window &win, int32_t q_num, int32_t q_den,
                             int32_t offset, uint8_t *out, int64_t out_pitch, uint8_t *Q,
                             cudaStream_t stream);
+
+// ---- autotuner (tune.cu) ----------------------------------------------
+// A launch configuration: tile_h (0 = heuristic), edge fraction (0 =
+// heuristic, 1 = uniform tiles), stripes (-1 = heuristic, 0 off, 1 on), and
+// the measured microseconds per call.  The batch entry stores its window and
+// quantile tile multipliers in tile_h and stripes.
+struct TuneCfg {
+    int32_t tile_h = 0;
+    float edge = 0.0f;
+    int32_t stripes = -1;
+    float us = 0.0f;
+};
+// The configuration the launch planners of this thread use (or null): set
+// for the duration of one launch by a TuneScope.
+const TuneCfg *tune_override();
+struct TuneScope {
+    explicit TuneScope(const TuneCfg *c);
+    ~TuneScope();
+    TuneScope(const TuneScope &) = delete;
+    TuneScope &operator=(const TuneScope &) = delete;
+
+  private:
+    const TuneCfg *prev_;
+};
+int tune_env();  // BZ_TUNE: -1 unset, 0 off, 1 tune on a miss
+// An explicit tuning call: every tunable launch of this thread searches and
+// stores its configuration while one of these lives.
+struct TuneForce {
+    TuneForce();
+    ~TuneForce();
+    TuneForce(const TuneForce &) = delete;
+    TuneForce &operator=(const TuneForce &) = delete;
+
+  private:
+    bool prev_;
+};
+bool tune_forced();
+bool tune_now(bool have);
+int dim_bucket(int v);
+int size_bucket(int64_t H, int64_t W);
+std::string tune_key(const char *gpu, const char *kernel, int cls, int h, int w, int64_t H, int64_t W);
+std::string device_tag();
+bool tune_get(const std::string &key, TuneCfg &c);
+void tune_put(const std::string &key, const TuneCfg &c, bool save);
+std::string window_tune_key(int mode, const Window &win, int64_t rows, int64_t W);
+std::string quantile_tune_key(int32_t q_num, int32_t q_den, const Window &win, int64_t H, int64_t W);
+std::string batch_tune_key(int mode);
+// Timed searches: `launch` runs the call once with the configuration of the
+// current TuneScope; the fastest configuration goes to `best`.
+bool tune_window(int mode, const Image &g, const Window &win, int64_t row0, int64_t row1, bool pipe,
+                 const std::function<cudaError_t()> &launch, cudaStream_t stream, TuneCfg &best);
+bool tune_quantile(const Image &g, const std::function<cudaError_t()> &launch, cudaStream_t stream,
+                   TuneCfg &best);
+
+// Planner pieces the tuner reads (plan.cu, k_stripes.cu, k_quantile.cu).
+int64_t one_wave_tile_rows(int64_t rows, int64_t W);
+double default_edge_fraction(bool pipe);
+bool stripes_allowed(int h);
+int64_t quantile_band_rows(int64_t H, int64_t W);
+// Window-kernel plan of an H x W image on a GPU with `sms` SMs under the
+// current TuneScope / environment: tile_h, edge_h, n_edge, tiles_total,
+// stripes (0/1), resident warps into out[0..5].
+int plan_window_launch(int64_t H, int64_t W, const Window &win, int sms, bool pipe, int64_t out[6]);
 
 // Library-owned per-device scratch: FP64-fallback counter.
 unsigned long long *fallback_counter(int device);

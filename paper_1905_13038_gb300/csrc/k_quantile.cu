@@ -36,39 +36,70 @@ static cudaError_t launch_q(const Image &g, const Window &win, int32_t q_num, in
                              cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess)
         return e;
-    // One wave: as many row bands as the resident warps allow for the column
-    // strips (the histograms cap residency at a few warps per SM, so a
-    // second, partial wave would leave most SMs idle).
-    int dev = 0, sms = 152, per_sm = 1;
-    if (cudaGetDevice(&dev) == cudaSuccess)
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 32, smem) != cudaSuccess ||
-        per_sm < 1)
-        per_sm = 1;
     const int64_t tiles_x = (g.W + kQCols - 1) / kQCols;
-    int64_t bands = ((int64_t)sms * per_sm) / tiles_x;
-    if (bands < 1)
-        bands = 1;
-    int64_t tile_h = (g.H + bands - 1) / bands;
-    if (tile_h < 1)
-        tile_h = 1;
+    const TuneCfg *t = tune_override();
+    int64_t tile_h = (t && t->tile_h > 0) ? t->tile_h : quantile_band_rows(g.H, g.W);
+    tile_h = tile_h < g.H ? tile_h : g.H;
     const int64_t tiles_y = (g.H + tile_h - 1) / tile_h;
     kernel<<<(unsigned)(tiles_x * tiles_y), 32, smem, stream>>>(g, win, q_num, q_den, offset, out,
                                                                    out_pitch, Q, tiles_x, tile_h);
     return cudaGetLastError();
 }
 
+// One wave: as many row bands as the resident warps allow for the column
+// strips (the histograms cap residency at a few warps per SM, so a second,
+// partial wave would leave most SMs idle).
+int64_t quantile_band_rows(int64_t H, int64_t W)
+{
+    static int per_sm = [] {
+        int v = 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_quantile<2, false>, 32, sizeof(QWarpSmem)) !=
+                cudaSuccess ||
+            v < 1) {
+            cudaGetLastError();
+            v = 1;
+        }
+        return v;
+    }();
+    int dev = 0, sms = 152;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t tiles_x = (W + kQCols - 1) / kQCols;
+    int64_t bands = ((int64_t)sms * per_sm) / tiles_x;
+    if (bands < 1)
+        bands = 1;
+    const int64_t tile_h = (H + bands - 1) / bands;
+    return tile_h < 1 ? 1 : tile_h;
+}
+
 cudaError_t launch_quantile(const Image &g, const Window &win, int32_t q_num, int32_t q_den,
                             int32_t offset, uint8_t *out, int64_t out_pitch, uint8_t *Q,
                             cudaStream_t stream)
 {
-    switch (quantile_prefetch(win.w)) {
-    case 2:
-        return win.w >= 32 ? launch_q<2, true>(g, win, q_num, q_den, offset, out, out_pitch, Q, stream)
-                           : launch_q<2, false>(g, win, q_num, q_den, offset, out, out_pitch, Q, stream);
-    case 4: return launch_q<4, true>(g, win, q_num, q_den, offset, out, out_pitch, Q, stream);
-    default: return launch_q<6, true>(g, win, q_num, q_den, offset, out, out_pitch, Q, stream);
+    auto run = [&]() -> cudaError_t {
+        switch (quantile_prefetch(win.w)) {
+        case 2:
+            return win.w >= 32 ? launch_q<2, true>(g, win, q_num, q_den, offset, out, out_pitch, Q, stream)
+                               : launch_q<2, false>(g, win, q_num, q_den, offset, out, out_pitch, Q, stream);
+        case 4: return launch_q<4, true>(g, win, q_num, q_den, offset, out, out_pitch, Q, stream);
+        default: return launch_q<6, true>(g, win, q_num, q_den, offset, out, out_pitch, Q, stream);
+        }
+    };
+    if (tune_env() == 0 && !tune_forced())
+        return run();
+    const std::string key = quantile_tune_key(q_num, q_den, win, g.H, g.W);
+    TuneCfg c;
+    bool have = tune_get(key, c);
+    if (tune_now(have)) {
+        TuneCfg b;
+        if (tune_quantile(g, run, stream, b)) {
+            c = b;
+            have = true;
+            tune_put(key, c, true);
+        }
     }
+    TuneScope scope(have ? &c : nullptr);
+    return run();
 }
 
 }  // namespace bz

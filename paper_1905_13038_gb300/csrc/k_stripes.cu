@@ -267,8 +267,14 @@ static int stripe_group()
 // own warm-up reads h rows for tile_h output rows.  Measured on GB300 (4096 x
 // 3072 page, 21-row tiles): 63 x 63 64 us per call without stripes (the edge
 // columns then also get the balanced schedule) against 88 us with them;
-// 255 x 255 143 us without against 78 us with.  BZ_STRIPES=0/1 forces it
-// (tuning).
+// 255 x 255 143 us without against 78 us with.
+// BZ_STRIPES=0/1 forces it (tuning), then a tuned configuration (only for
+// windows of 48 rows or more, the range the pre-pass is tested on).
+bool stripes_allowed(int h)
+{
+    return h >= 48;
+}
+
 static bool use_stripes(int h, int64_t tile_h)
 {
     static const int env = [] {
@@ -277,6 +283,9 @@ static bool use_stripes(int h, int64_t tile_h)
     }();
     if (env >= 0)
         return env != 0;
+    const TuneCfg *t = tune_override();
+    if (t && t->stripes >= 0)
+        return t->stripes != 0 && stripes_allowed(h);
     return h >= 48 && h >= 5 * tile_h;
 }
 

@@ -144,25 +144,61 @@ static cudaError_t launch_m(const Image &g, const Window &win, const Thresh &T, 
                 : launch_t<MODE, false, uint32_t, false>(g, win, T, o, row0, row1, stream);
 }
 
+// Binarize launches on the window kernel read their tile height, edge-tile
+// fraction and stripe choice from the autotuner's cache (tune.cu); the
+// window-sum export and the precision report keep the heuristics.
+static bool window_tunable(int mode, const Image &g, const Window &win, int64_t row0, int64_t row1)
+{
+    return (mode == MODE_FP64 || mode == MODE_FP32 || mode == MODE_FP64_DIRECT) &&
+           !small_path_applies(mode, g, win, row0, row1);
+}
+
 cudaError_t launch_window_rows(int mode, const Image &g, const Window &win, const Thresh &T,
                                const Outputs &o, int64_t row0, int64_t row1, cudaStream_t stream)
 {
     if (row0 < 0 || row1 > g.H || row0 >= row1)
         return cudaErrorInvalidValue;
-    switch (mode) {
-    case MODE_FP64: return launch_m<MODE_FP64>(g, win, T, o, row0, row1, stream);
-    case MODE_FP32: return launch_m<MODE_FP32>(g, win, T, o, row0, row1, stream);
-    case MODE_FP64_DIRECT: return launch_m<MODE_FP64_DIRECT>(g, win, T, o, row0, row1, stream);
-    case MODE_SUMS: return launch_m<MODE_SUMS>(g, win, T, o, row0, row1, stream);
-    case MODE_REPORT: return launch_m<MODE_REPORT>(g, win, T, o, row0, row1, stream);
-    default: return cudaErrorInvalidValue;
+    auto run = [&]() -> cudaError_t {
+        switch (mode) {
+        case MODE_FP64: return launch_m<MODE_FP64>(g, win, T, o, row0, row1, stream);
+        case MODE_FP32: return launch_m<MODE_FP32>(g, win, T, o, row0, row1, stream);
+        case MODE_FP64_DIRECT: return launch_m<MODE_FP64_DIRECT>(g, win, T, o, row0, row1, stream);
+        case MODE_SUMS: return launch_m<MODE_SUMS>(g, win, T, o, row0, row1, stream);
+        case MODE_REPORT: return launch_m<MODE_REPORT>(g, win, T, o, row0, row1, stream);
+        default: return cudaErrorInvalidValue;
+        }
+    };
+    if (!window_tunable(mode, g, win, row0, row1) || (tune_env() == 0 && !tune_forced()))
+        return run();
+    const std::string key = window_tune_key(mode, win, row1 - row0, g.W);
+    TuneCfg c;
+    bool have = tune_get(key, c);
+    if (tune_now(have)) {
+        const bool vec = ((uintptr_t)g.img % 8 == 0) && (g.pitch % 8 == 0);
+        const bool pipe = pipe_words(mode, vec, (int64_t)win.h * win.w <= 66051, g, win) > 0;
+        TuneCfg b;
+        if (tune_window(mode, g, win, row0, row1, pipe, run, stream, b)) {
+            c = b;
+            have = true;
+            tune_put(key, c, true);
+            // the timed runs added to the FP64-fallback counter: count this
+            // call's own launch only
+            if (o.fallbacks && cudaMemsetAsync(o.fallbacks, 0, sizeof(unsigned long long), stream) != cudaSuccess)
+                return cudaGetLastError();
+        }
     }
+    TuneScope scope(have ? &c : nullptr);
+    return run();
 }
 
 int window_kernel_count(int mode, const Image &g, const Window &win, int64_t row0, int64_t row1)
 {
     if (small_path_applies(mode, g, win, row0, row1))
         return 1;
+    TuneCfg c;
+    const bool have = window_tunable(mode, g, win, row0, row1) && tune_env() != 0 &&
+                      tune_get(window_tune_key(mode, win, row1 - row0, g.W), c);
+    TuneScope scope(have ? &c : nullptr);
     const int64_t tile_h = window_tile_rows(row1 - row0, g.W, win.h, win.w);
     const int64_t tiles_y = (row1 - row0 + tile_h - 1) / tile_h;
     return 1 + stripe_kernel_count(win, tile_h, tiles_y);

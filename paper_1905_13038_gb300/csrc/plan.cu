@@ -40,23 +40,36 @@ static int64_t one_wave_rows(int64_t H, int64_t W, int64_t resident)
     return th;
 }
 
-int64_t window_tile_rows(int64_t H, int64_t W, int h, int w)
+int64_t one_wave_tile_rows(int64_t rows, int64_t W)
 {
-    (void)h;
-    (void)w;
-    // One wave of warp tiles: the shortest tiles for which every tile of the
-    // image is resident at once (SMs x 4 blocks x 4 warps).  Measured on
-    // GB300: on the 4096 x 3072 page this gives 21 rows (8 % faster than 24,
-    // while 20 rows spills into a second wave); on small pages it gives
-    // 1-4 rows, which halves the latency (the launch is latency-bound and
-    // every warp's work shrinks).  BZ_TILE_ROWS overrides it (tuning).
+    return one_wave_rows(rows, W, resident_warps());
+}
+
+// One wave of warp tiles: the shortest tiles for which every tile of the
+// image is resident at once (SMs x 4 blocks x 4 warps).  Measured on GB300:
+// on the 4096 x 3072 page this gives 21 rows (8 % faster than 24, while 20
+// rows spills into a second wave); on small pages it gives 1-4 rows, which
+// halves the latency (the launch is latency-bound and every warp's work
+// shrinks).  BZ_TILE_ROWS overrides it, then a tuned configuration.
+static int64_t tile_rows_for(int64_t H, int64_t W, int64_t resident)
+{
     static const int64_t env = [] {
         const char *e = getenv("BZ_TILE_ROWS");
         return e ? (int64_t)atoll(e) : (int64_t)0;
     }();
     if (env > 0)
         return env < H ? env : H;
-    return one_wave_rows(H, W, resident_warps());
+    const TuneCfg *t = tune_override();
+    if (t && t->tile_h > 0)
+        return t->tile_h < H ? t->tile_h : H;
+    return one_wave_rows(H, W, resident);
+}
+
+int64_t window_tile_rows(int64_t H, int64_t W, int h, int w)
+{
+    (void)h;
+    (void)w;
+    return tile_rows_for(H, W, resident_warps());
 }
 
 // Edge-tile height as a fraction of the interior height: the measured time
@@ -66,7 +79,7 @@ int64_t window_tile_rows(int64_t H, int64_t W, int h, int w)
 // gave 778 us summed over the nine calls, 0.6 788, 0.7 795, uniform tiles
 // 940.  BZ_EDGE_FRAC overrides it (tuning; >= 1 disables the balanced
 // schedule).
-static double default_edge_fraction(bool pipe)
+double default_edge_fraction(bool pipe)
 {
     return pipe ? 0.82 : 0.5;
 }
@@ -79,6 +92,9 @@ static double edge_fraction(bool pipe)
     }();
     if (env > 0.0)
         return env;
+    const TuneCfg *t = tune_override();
+    if (t && t->edge > 0.0f)
+        return t->edge;
     return default_edge_fraction(pipe);
 }
 
@@ -135,6 +151,24 @@ TileSched make_sched(const Image &g, const Window &win, int64_t row0, int64_t ro
     }();
     S.prefetch = (pf && !stripes) ? 1 : 0;
     return S;
+}
+
+int plan_window_launch(int64_t H, int64_t W, const Window &win, int sms, bool pipe, int64_t out[6])
+{
+    if (H < 1 || W < 1 || sms < 1)
+        return -1;
+    const int64_t resident = (int64_t)sms * kBlocksPerSM * kWarpsPerBlock;
+    const int64_t th = tile_rows_for(H, W, resident);
+    const int64_t tiles_y = (H + th - 1) / th;
+    const bool st = stripe_kernel_count(win, th, tiles_y) > 0;
+    const TileSched S = plan_sched(0, H, W, th, resident, edge_fraction(pipe), st);
+    out[0] = S.tile_h;
+    out[1] = S.edge_h;
+    out[2] = S.n_edge;
+    out[3] = S.tiles_total;
+    out[4] = st ? 1 : 0;
+    out[5] = resident;
+    return 0;
 }
 
 // Pure form for planning and tests: the schedule on a GPU with `sms` SMs.
