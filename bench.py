@@ -282,9 +282,11 @@ def extra_quantile(bz, synth, dev, stream):
     res = {}
     for (h, w) in ((31, 31), (101, 101)):
         for (qn, qd) in ((1, 2), (1, 10)):
+            _, cfg = bz.autotune_quantile(img, h, w, qn, qd, 8, out=out, stream=stream)
             ms = time_events(lambda: bz.binarize_quantile(img, h, w, qn, qd, 8, out=out, stream=stream), 3, stream)
             res[f"{h}x{w}_q{qn}/{qd}"] = {"ms": round(ms, 3), "gpix_s": round(2048 * 2048 / (ms * 1e-3) / 1e9, 2),
-                                          "hbm_frac": hbm_frac(1.125, 2048 * 2048, ms)}
+                                          "hbm_frac": hbm_frac(1.125, 2048 * 2048, ms),
+                                          "tuned_band_rows": cfg["tile_h"]}
     return res
 
 
@@ -464,23 +466,30 @@ def extra_inplace(bz, imgs, dev, stream, bands=(0, 1024)):
     return res
 
 
-def extra_serve(bz, synth, dev, n_req=2000, seed=5, rates=(0.1, 0.3, 0.5, 0.7, 0.9, 1.0, 1.2)):
-    """Served path: requests over pre-staged device images (crops of two
-    portrait 3366 x 4760 and two landscape 4760 x 3366 pages, area log-uniform 0.1-16 Mpix, aspect 1:sqrt(2)
-    portrait or landscape, method uniform over Sauvola/Niblack/median, odd
-    window uniform in [15, 255]) arriving as a Poisson process.  The
-    saturation rate is measured first (all requests submitted at once), then
-    Poisson arrivals at the given multiples of it.  Latency = submit ->
+def extra_serve(bz, synth, dev, n_req=10000, seed=5, rates=(0.1, 0.3, 0.5, 0.7, 0.9, 1.0, 1.2)):
+    """Served path: 10,000 requests over pre-staged device images (crops of
+    28 distinct 16-Mpix device pages, 14 portrait 3366 x 4760 and 14 landscape
+    4760 x 3366, 448 MB in all, so that requests find their images in HBM
+    rather than L2; area log-uniform 0.1-16 Mpix, aspect 1:sqrt(2) portrait or
+    landscape, method uniform over Sauvola/Niblack/median, odd window uniform
+    in [15, 255]) arriving as a Poisson process.  The saturation rate is
+    measured first (all requests submitted at once), then Poisson arrivals at
+    the given multiples of it, then saturation for each method's requests
+    alone (the served time split by method).  Latency = submit ->
     bz_server_wait returns.  A second mode ingests from pinned host memory:
     the image is uploaded per request and the output downloaded."""
     import concurrent.futures as cf
     import numpy as np
     import torch
     rng = np.random.default_rng(seed)
-    portrait = [torch.from_numpy(synth.document(4760, 3366, synth.BASE_SEED + 7 + 1000 * p, stains=3)).to(dev)
-                for p in range(2)]
-    landscape = [torch.from_numpy(synth.document(3366, 4760, synth.BASE_SEED + 9 + 1000 * p, stains=3)).to(dev)
-                 for p in range(2)]
+    # 2 + 2 generated pages, each copied into 7 device allocations of its own
+    gen_p = [torch.from_numpy(synth.document(4760, 3366, synth.BASE_SEED + 7 + 1000 * p, stains=3)).to(dev)
+             for p in range(2)]
+    gen_l = [torch.from_numpy(synth.document(3366, 4760, synth.BASE_SEED + 9 + 1000 * p, stains=3)).to(dev)
+             for p in range(2)]
+    portrait = [gen_p[c % 2].clone() for c in range(14)]
+    landscape = [gen_l[c % 2].clone() for c in range(14)]
+    del gen_p, gen_l
     jobs = []
     px_total = 0
     for q in range(n_req):
@@ -489,7 +498,7 @@ def extra_serve(bz, synth, dev, n_req=2000, seed=5, rates=(0.1, 0.3, 0.5, 0.7, 0
             H = int(round((area * 2 ** 0.5) ** 0.5)); W = int(round(area / H))
         else:
             W = int(round((area * 2 ** 0.5) ** 0.5)); H = int(round(area / W))
-        src = (portrait if H >= W else landscape)[q % 2]
+        src = (portrait if H >= W else landscape)[q % 14]
         PH, PW = src.shape
         H, W = max(1, min(H, PH)), max(1, min(W, PW))
         win = int(rng.integers(7, 128)) * 2 + 1
@@ -505,15 +514,18 @@ def extra_serve(bz, synth, dev, n_req=2000, seed=5, rates=(0.1, 0.3, 0.5, 0.7, 0
     budget = 8 << 30
     pool = cf.ThreadPoolExecutor(max_workers=192)
 
-    def run(rate):
+    def run(rate, jl=None):
+        jl = jobs if jl is None else jl
+        nj = len(jl)
+        px_run = sum(int(j.c.H) * int(j.c.W) for j in jl)
         srv = bz.Server(hbm_budget_bytes=budget, max_slots=64)
-        t_sub = np.zeros(n_req)
-        t_done = np.zeros(n_req)
+        t_sub = np.zeros(nj)
+        t_done = np.zeros(nj)
         futs = []
-        gaps = rng.exponential(1.0 / rate, n_req) if rate else np.zeros(n_req)
+        gaps = rng.exponential(1.0 / rate, nj) if rate else np.zeros(nj)
         t0 = time.perf_counter()
         nxt = t0
-        for q, job in enumerate(jobs):
+        for q, job in enumerate(jl):
             nxt += gaps[q]
             while True:
                 now = time.perf_counter()
@@ -534,14 +546,24 @@ def extra_serve(bz, synth, dev, n_req=2000, seed=5, rates=(0.1, 0.3, 0.5, 0.7, 0
         lat = (t_done - t_sub) * 1e3
         return {"rate_req_s": round(rate, 1) if rate else None, "p50_ms": round(float(np.percentile(lat, 50)), 3),
                 "p99_ms": round(float(np.percentile(lat, 99)), 3),
-                "gpix_s": round(px_total / (t1 - t0) / 1e9, 2), "ok": int(sum(1 for x in sts if x == 0))}
+                "gpix_s": round(px_run / (t1 - t0) / 1e9, 2), "ok": int(sum(1 for x in sts if x == 0))}
 
     torch.cuda.synchronize()
     sat = run(0)  # everything at once: saturation throughput
     sat_rate = n_req / (px_total / (sat["gpix_s"] * 1e9))
-    res = {"requests": n_req, "mpix_total": round(px_total / 1e6, 1), "saturation": sat}
+    res = {"requests": n_req, "mpix_total": round(px_total / 1e6, 1),
+           "image_pool": "28 distinct 16-Mpix device pages (448 MB, > 3x L2)", "saturation": sat}
     for f in rates:
         res[f"load_{f}"] = run(f * sat_rate)
+    # saturation of each method's requests alone: where the served time goes
+    by_method = {}
+    for name, m in (("sauvola", bz.SAUVOLA), ("niblack", bz.NIBLACK), ("median", bz.QUANTILE)):
+        jl = [j for j in jobs if j.c.method == m]
+        px_m = sum(int(j.c.H) * int(j.c.W) for j in jl)
+        r = run(0, jl)
+        by_method[name] = {"requests": len(jl), "mpix": round(px_m / 1e6, 1), "gpix_s": r["gpix_s"],
+                           "seconds": round(px_m / (r["gpix_s"] * 1e9), 3)}
+    res["saturation_by_method"] = by_method
 
     # host ingest: the first n_host requests with their images in pinned host
     # memory; each request copies its image to the device, is served, and
@@ -603,20 +625,32 @@ def extra_batch(bz, synth, dev, stream, count=256):
     windows 15/31/63/127, Sauvola or Niblack): one graph launch vs per-image calls."""
     import torch
     specs = synth.batch_specs(count)
-    # 16 distinct A4 pages at 300 dpi (139 MB, more than L2); job b binarizes
-    # a crop of page b % 16 (generating 256 full pages would dominate the
+    # every job has an image allocation of its own (the 256 images hold
+    # ~467 MB, more than three times L2), cut at a random offset from one of
+    # 16 distinct A4 pages at 300 dpi (generating 256 pages would dominate the
     # benchmark's run time)
     pages = [torch.from_numpy(synth.document(3508, 2480, synth.BASE_SEED + 3 + 1000 * p, stains=3)).to(dev)
              for p in range(16)]
+    rng = np.random.default_rng(11)
+    images = []
+    for b, sp in enumerate(specs):
+        y = int(rng.integers(0, 3508 - sp["H"] + 1))
+        x = int(rng.integers(0, 2480 - sp["W"] + 1))
+        # pitched like any GPU image allocation: rows 64-byte aligned
+        buf = torch.empty((sp["H"], (sp["W"] + 63) // 64 * 64), dtype=torch.uint8, device=dev)
+        buf[:, :sp["W"]].copy_(pages[b % 16][y:y + sp["H"], x:x + sp["W"]])
+        images.append(buf[:, :sp["W"]])
+    del pages
     jobs = []
     px = 0
     for b, sp in enumerate(specs):
-        img = pages[b % 16][:sp["H"], :sp["W"]]
+        img = images[b]
         if sp["method"] == 0:
             jobs.append(bz.Job(img, bz.SAUVOLA, sp["h"], sp["w"], k=0.5, R=128.0))
         else:
             jobs.append(bz.Job(img, bz.NIBLACK, sp["h"], sp["w"], k=-0.2))
         px += sp["H"] * sp["W"]
+    tuned = bz.autotune_batch(jobs, stream=stream)
     ms_batch = time_events(lambda: bz.binarize_batch(jobs, stream=stream), 3, stream)
     # FP32 batch against the FP64 batch: differing output bits
     jobs32 = [bz.Job(j.image, j.c.method, j.c.h, j.c.w, k=j.c.k, R=j.c.R) for j in jobs]
@@ -636,8 +670,11 @@ def extra_batch(bz, synth, dev, stream, count=256):
             else:
                 bz.binarize_niblack(j.image, j.c.h, j.c.w, -0.2, out=j.out, stream=stream)
     ms_single = time_events(per_image, 3, stream)
-    extra_batch.pages = pages
+    extra_batch.images = images
     return {"images": count, "mpix": round(px / 1e6, 1),
+            "inputs": f"{count} distinct device images (rows 64-byte aligned), {px / 1e6:.0f} Mpix (> 3x L2)",
+            "tuned": {"api": "bz_autotune_batch", "win_tile_mult": tuned["win_mult"],
+                      "quant_tile_mult": tuned["quant_mult"]},
             "batched_graph": {"ms": round(ms_batch, 3), "gpix_s": round(px / (ms_batch * 1e-3) / 1e9, 2)},
             "batched_graph_fp32": {"ms": round(ms_batch32, 3), "gpix_s": round(px / (ms_batch32 * 1e-3) / 1e9, 2),
                                    "flips_vs_fp64": flips},
@@ -676,6 +713,19 @@ def main():
             b = (s * len(WINDOWS) + wi) % N_BUFFERS
             bz.binarize_sauvola(imgs[b], h, w, K_SAUVOLA, R_SAUVOLA, out=outs[b], precision=prec,
                                 stream=stream)
+
+    # the library's autotuner picks each window's launch configuration (tile
+    # height, edge tiles, stripe pre-pass) by timing candidates on the device
+    # with a cold L2; the timed launches below read the choice from its cache
+    import tempfile
+    bz.tune_load(os.path.join(tempfile.mkdtemp(prefix="bz_tune_"), "tune.json"))
+    tuned = {}
+    with torch.cuda.stream(stream):
+        for (h, w) in WINDOWS:
+            _, cfg = bz.autotune_window(bz.SAUVOLA, imgs[0], h, w, K_SAUVOLA, R_SAUVOLA, out=outs[0],
+                                        precision=prec, stream=stream)
+            tuned[f"{h}x{w}"] = cfg
+    torch.cuda.synchronize(dev)
 
     # warm-up (also allocates the library's per-device scratch)
     with torch.cuda.stream(stream):
@@ -802,6 +852,7 @@ def main():
                     "d2h_bytes_per_step": len(WINDOWS) * H * ((W + 7) // 8),
                     "api": "binarize_host_multi (pinned host page in once per step, four packed outputs back)"},
             "per_window": per_window,
+            "tuned": {"api": "bz_autotune_window (candidates timed on the device, cold L2)", "windows": tuned},
             "fp64_fallbacks_last_launch": fb,
             "other_rows": extras,
         }

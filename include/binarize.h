@@ -409,15 +409,39 @@ typedef struct bz_server bz_server;
 bz_status bz_server_create(int64_t hbm_budget_bytes, int32_t max_slots,
                            bz_server **out);
 /* Queues a job; its buffers must stay valid until bz_server_wait returns
- * BZ_OK, BZ_ECANCELLED or BZ_ETIMEOUT for the ticket. */
+ * BZ_OK or BZ_ECANCELLED for the ticket, or BZ_ETIMEOUT for a request that
+ * had not started (see bz_server_wait). */
 bz_status bz_server_submit(bz_server *srv, const bz_job *job,
                            bz_precision precision, uint64_t *ticket);
-/* Waits for a ticket; timeout_ms < 0 waits forever.  On timeout the
- * request is cancelled (or has completed) and BZ_ETIMEOUT is returned. */
+/* Waits for a ticket; timeout_ms < 0 waits forever.  Returns the request's
+ * status (and forgets the ticket) when it finished within the timeout.
+ * Otherwise BZ_ETIMEOUT, without waiting further: a request that had not
+ * started is dropped and its buffers are free; a request already running
+ * cannot be recalled from the GPU, so it is cancelled but keeps its ticket,
+ * and its buffers stay in use until a later bz_server_wait on the same ticket
+ * returns BZ_ECANCELLED (a wait may time out again meanwhile) or until
+ * bz_server_destroy returns. */
 bz_status bz_server_wait(bz_server *srv, uint64_t ticket, int32_t timeout_ms);
 bz_status bz_server_cancel(bz_server *srv, uint64_t ticket);
 /* Cancels queued requests, waits for the in-flight ones, frees the server. */
 bz_status bz_server_destroy(bz_server *srv);
+
+/* Test of the certified FP32 threshold (Sec. 1 threshold, Table 1 forms):
+ * the largest ratio |t32 - t64| / E over all pixels, where t64 is the
+ * canonical FP64 threshold and t32, E the FP32 threshold and certified error
+ * bound the BZ_FP64 kernels evaluate, taken over every evaluation form they
+ * use (the two variance roundings and, for Sauvola with 0 <= k <= 1, the
+ * form m (1 - k + (k/R) s)).  A ratio below 1 shows, for that image and
+ * window, that every pixel the FP32 filter decides is decided as the FP64
+ * threshold decides it.  method: 0 Sauvola, 1 Niblack, 3..7 Wolf, Feng,
+ * Rais, NICK, Phansalkar; params as for binarize_precision_report_ext
+ * ({k, R, ...}; Sauvola and Niblack read params[0] = k, params[1] = R).
+ * max_ratio_dev: one device double, which the call raises to the ratio with
+ * an atomic maximum (initialise it to 0).  Asynchronous on `stream`. */
+bz_status binarize_bound_report(int32_t method, const uint8_t *image, int64_t H,
+                                int64_t W, int64_t in_pitch, int32_t h,
+                                int32_t w, const double *params,
+                                double *max_ratio_dev, void *stream);
 
 /* ---------------------------------------------------------------------- */
 /* Autotuning of launch parameters (no counterpart in the paper: how the  */

@@ -29,7 +29,7 @@ __all__ = [
     "window_minmax", "binarize_bernsen", "haar_feature", "HAAR_FEATURES", "binarize_inplace",
     "inplace_scratch_bytes", "binarize_host", "binarize_host_multi",
     "autotune_window", "autotune_quantile", "autotune_batch", "tune_key", "tune_get", "tune_set",
-    "tune_load", "tune_save", "tune_clear", "tune_window_plan",
+    "tune_load", "tune_save", "tune_clear", "tune_window_plan", "bound_report",
 ]
 
 FP64, FP32, FP64_DIRECT = 0, 1, 2
@@ -114,6 +114,7 @@ def _load():
         "bz_server_wait": ([P, ctypes.c_uint64, i32], st),
         "bz_server_cancel": ([P, ctypes.c_uint64], st),
         "bz_server_destroy": ([P], st),
+        "binarize_bound_report": ([i32, P, i64, i64, i64, i32, i32, P, P, P], st),
         "bz_autotune_window": ([i32, P, i64, i64, i64, i32, i32, f64, f64, P, i64, st, P, P, P, P, P], st),
         "bz_autotune_quantile": ([P, i64, i64, i64, i32, i32, i32, i32, i32, P, i64, P, P, P], st),
         "bz_autotune_batch": ([ctypes.POINTER(_JobC), i32, st, P, P, P, P], st),
@@ -494,7 +495,8 @@ class Server:
 
     def wait(self, ticket: int, timeout_ms: int = -1) -> int:
         st = _load().bz_server_wait(self._h, ticket, timeout_ms)
-        self._jobs.pop(ticket, None)
+        if st != 6:  # after BZ_ETIMEOUT a running request still uses its buffers
+            self._jobs.pop(ticket, None)
         return st
 
     def cancel(self, ticket: int) -> int:
@@ -511,6 +513,19 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def bound_report(method: int, image, h: int, w: int, params, W: int | None = None, stream=None) -> float:
+    """max over pixels of |t32 - t64| / certified bound (binarize_bound_report)."""
+    import torch
+    ptr, H, W, pitch = _image(image, W)
+    prm = (ctypes.c_double * 8)(*(list(params) + [0.0] * (8 - len(params))))
+    r = torch.zeros(1, dtype=torch.float64, device=image.device)
+    s = _stream(stream)
+    _check("binarize_bound_report", _load().binarize_bound_report(method, ptr, H, W, pitch, h, w, prm,
+                                                                  r.data_ptr(), s))
+    torch.cuda.synchronize(image.device)
+    return float(r.item())
 
 
 # ---------------------------------------------------------------- autotuner --

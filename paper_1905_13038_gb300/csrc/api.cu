@@ -769,6 +769,31 @@ int64_t bz_inplace_scratch_bytes(int64_t H, int64_t W, int32_t h, int64_t band_r
     return 2 * band * ((W + 7) / 8);
 }
 
+bz_status binarize_bound_report(int32_t method, const uint8_t *image, int64_t H, int64_t W, int64_t in_pitch,
+                                int32_t h, int32_t w, const double *params, double *max_ratio_dev, void *stream)
+{
+    bz_status st = check_image(image, H, W, in_pitch, h, w);
+    if (st != BZ_OK)
+        return st;
+    if (!params || !max_ratio_dev)
+        return BZ_EINVAL;
+    Outputs o{};
+    o.maxratio_bits = (unsigned long long *)max_ratio_dev;
+    if (method == METHOD_SAUVOLA || method == METHOD_NIBLACK) {
+        const double k = params[0], R = method == METHOD_SAUVOLA ? params[1] : 128.0;
+        if (!finite_params(method, k, R))
+            return BZ_EINVAL;
+        const Thresh T = make_thresh(method, k, R);
+        return launch_window(MODE_REPORT, Image{image, H, W, in_pitch}, make_window(h, w), T, o,
+                             (cudaStream_t)stream) == cudaSuccess
+                   ? BZ_OK
+                   : BZ_ECUDA;
+    }
+    if (method < METHOD_WOLF || method > METHOD_PHANSALKAR)
+        return BZ_EINVAL;
+    return run_ext(method, image, H, W, in_pitch, h, w, params, MODE_REPORT, o, stream);
+}
+
 // ---- explicit tuning calls: the same work as the binarize call, with the
 // autotuner's timed search forced for it (tune.cu); the chosen configuration
 // is stored in the cache and returned.

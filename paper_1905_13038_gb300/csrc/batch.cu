@@ -23,17 +23,22 @@ namespace bz {
 
 constexpr int kBatchWarps = 4;   // warps per block, window kernel
 
-template <int MODE>
-__global__ void __launch_bounds__(32 * kBatchWarps)
-    k_batch_window(BatchHeader *hdr, const WinJobDev *jobs, unsigned long long *fallbacks)
+// Window tiles of kernel class CLS (see BatchHeader): tiles popped from the
+// class's cursor, the job found by binary search over its segment.
+template <int MODE, int CLS>
+__global__ void __launch_bounds__(32 * kBatchWarps, CLS < 2 ? kBlocksPerSM : 1)
+    k_batch_window(BatchHeader *hdr, const WinJobDev *jobs_all, unsigned long long *fallbacks)
 {
+    constexpr bool kPipe = CLS < 2 && (MODE == MODE_FP64 || MODE == MODE_FP32);
+    __shared__ uint4 slots[kBatchWarps][kPipe ? 416 : 1];  // 6.5 KB per warp (pipelined path)
     const int lane = threadIdx.x & 31;
-    const int64_t total = hdr->win_tiles;
-    const int nj = hdr->n_win;
+    const WinJobDev *jobs = jobs_all + hdr->cls_begin[CLS];
+    const int64_t total = hdr->cls_tiles[CLS];
+    const int nj = hdr->cls_n[CLS];
     for (;;) {
         unsigned long long t = 0;
         if (lane == 0)
-            t = atomicAdd(&hdr->win_next, 1ull);
+            t = atomicAdd(&hdr->cls_next[CLS], 1ull);
         t = __shfl_sync(0xFFFFFFFFu, t, 0);
         if ((int64_t)t >= total)
             break;
@@ -54,7 +59,10 @@ __global__ void __launch_bounds__(32 * kBatchWarps)
         o.bits = J.out;
         o.out_pitch = J.out_pitch;
         o.fallbacks = fallbacks;
-        if (J.vec) {
+        if (kPipe) {
+            window_tile<MODE, true, uint32_t, kPipe ? CLS + 1 : 0>(J.g, J.win, J.T, o, x0, y0, y1, lane,
+                                                                   slots[threadIdx.x >> 5]);
+        } else if (J.vec) {
             if (J.wide)
                 window_tile<MODE, true, unsigned long long, 0>(J.g, J.win, J.T, o, x0, y0, y1, lane,
                                                             nullptr);
@@ -161,6 +169,94 @@ static int64_t quant_tile_rows(int64_t H, int h, int mult = kBatchQuantMult)
     return th;
 }
 
+static int batch_mode_of(int precision_mode)
+{
+    return precision_mode == 0 ? MODE_FP64 : (precision_mode == 1 ? MODE_FP32 : MODE_FP64_DIRECT);
+}
+
+// Kernel class of a window job (see BatchHeader).
+static int window_class(const bz_job &j, int precision_mode)
+{
+    const bool vec = ((uintptr_t)j.image % 8 == 0) && (j.in_pitch % 8 == 0);
+    const bool s2_32 = (int64_t)j.h * j.w <= 66051;
+    const int aw = pipe_words(batch_mode_of(precision_mode), vec, s2_32, Image{j.image, j.H, j.W, j.in_pitch},
+                              make_window(j.h, j.w));
+    return aw == 1 ? 0 : (aw == 2 ? 1 : 2);
+}
+
+// The window jobs order[0 .. n) of `jobs` into `out`: grouped by kernel
+// class, most expensive tiles (longest warm-up + tile) first within a class,
+// with tile rows mult * h (batch_tile_rows); fills the header's class
+// fields.  Reorders `order`; allocates nothing.
+static void fill_window_jobs(const bz_job *jobs, int *order, int n, int precision_mode, int mult,
+                             WinJobDev *out, BatchHeader *hdr)
+{
+    std::sort(order, order + n, [&](int a, int b) {
+        const int ca = window_class(jobs[a], precision_mode), cb = window_class(jobs[b], precision_mode);
+        if (ca != cb)
+            return ca < cb;
+        const int64_t wa = batch_tile_rows(jobs[a].H, jobs[a].h, mult) + jobs[a].h;
+        const int64_t wb = batch_tile_rows(jobs[b].H, jobs[b].h, mult) + jobs[b].h;
+        return wa != wb ? wa > wb : a < b;
+    });
+    for (int c = 0; c < kWinClasses; c++) {
+        hdr->cls_begin[c] = 0;
+        hdr->cls_n[c] = 0;
+        hdr->cls_tiles[c] = 0;
+        hdr->cls_next[c] = 0;
+    }
+    int c_prev = -1;
+    int64_t tb = 0;
+    for (int a = 0; a < n; a++) {
+        const bz_job &j = jobs[order[a]];
+        const int c = window_class(j, precision_mode);
+        if (c != c_prev) {
+            hdr->cls_begin[c] = a;
+            tb = 0;
+            c_prev = c;
+        }
+        WinJobDev &d = out[a];
+        d.g = Image{j.image, j.H, j.W, j.in_pitch};
+        d.win = make_window(j.h, j.w);
+        d.T = make_thresh(j.method == BZ_SAUVOLA ? 0 : 1, j.k, j.method == BZ_SAUVOLA ? j.R : 128.0);
+        d.out = j.out;
+        d.out_pitch = j.out_pitch;
+        d.tile_h = batch_tile_rows(j.H, j.h, mult);
+        d.tiles_x = (j.W + kTileCols - 1) / kTileCols;
+        d.tile_begin = tb;
+        d.vec = ((uintptr_t)j.image % 8 == 0) && (j.in_pitch % 8 == 0);
+        d.wide = (int64_t)j.h * j.w > 66051;
+        tb += d.tiles_x * ((j.H + d.tile_h - 1) / d.tile_h);
+        hdr->cls_n[c]++;
+        hdr->cls_tiles[c] = tb;
+    }
+}
+
+// Grids of the persistent kernels: SMs x resident blocks of each.
+template <int MODE>
+static void batch_grids(int nsm, size_t qsmem, int grid_w[kWinClasses], int &grid_q)
+{
+    int occ[kWinClasses] = {0, 0, 0}, occ_q = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[0], k_batch_window<MODE, 0>, 32 * kBatchWarps, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[1], k_batch_window<MODE, 1>, 32 * kBatchWarps, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[2], k_batch_window<MODE, 2>, 32 * kBatchWarps, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_q, k_batch_quantile, 32, qsmem);
+    for (int c = 0; c < kWinClasses; c++)
+        grid_w[c] = nsm * (occ[c] < 1 ? 1 : occ[c]);
+    grid_q = nsm * (occ_q < 1 ? 1 : occ_q);
+}
+
+template <int MODE>
+static void launch_batch_kernels(BatchHeader *hdr, const WinJobDev *wj, const QJobDev *qj,
+                                 unsigned long long *fallbacks, const int grid_w[kWinClasses], int grid_q,
+                                 size_t qsmem, cudaStream_t stream)
+{
+    k_batch_window<MODE, 0><<<grid_w[0], 32 * kBatchWarps, 0, stream>>>(hdr, wj, fallbacks);
+    k_batch_window<MODE, 1><<<grid_w[1], 32 * kBatchWarps, 0, stream>>>(hdr, wj, fallbacks);
+    k_batch_window<MODE, 2><<<grid_w[2], 32 * kBatchWarps, 0, stream>>>(hdr, wj, fallbacks);
+    k_batch_quantile<<<grid_q, 32, qsmem, stream>>>(hdr, qj);
+}
+
 BatchSlot::~BatchSlot()
 {
     release();
@@ -258,13 +354,8 @@ static cudaError_t capture_graph(BatchSlot &s, cudaGraphExec_t *out)
                                  cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess)
         return e;
-    int occ_w = 0, occ_q = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_w, k_batch_window<MODE>, 32 * kBatchWarps, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_q, k_batch_quantile, 32, qsmem);
-    if (occ_w < 1)
-        occ_w = 1;
-    if (occ_q < 1)
-        occ_q = 1;
+    int grid_w[kWinClasses], grid_q = 0;
+    batch_grids<MODE>(s.num_sms, qsmem, grid_w, grid_q);
     cudaGraph_t graph = nullptr;
     e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess)
@@ -272,8 +363,7 @@ static cudaError_t capture_graph(BatchSlot &s, cudaGraphExec_t *out)
     cudaMemcpyAsync(s.d_table, s.h_table, bytes, cudaMemcpyHostToDevice, cs);
     if (s.fallbacks)
         cudaMemsetAsync(s.fallbacks, 0, sizeof(unsigned long long), cs);
-    k_batch_window<MODE><<<s.num_sms * occ_w, 32 * kBatchWarps, 0, cs>>>(hdr, wj, s.fallbacks);
-    k_batch_quantile<<<s.num_sms * occ_q, 32, qsmem, cs>>>(hdr, qj);
+    launch_batch_kernels<MODE>(hdr, wj, qj, s.fallbacks, grid_w, grid_q, qsmem, cs);
     e = cudaStreamEndCapture(cs, &graph);
     if (e != cudaSuccess)
         return e;
@@ -322,32 +412,13 @@ bz_status run_batch(BatchSlot &s, const bz_job *jobs, int32_t n, bz_precision pr
         (jobs[i].method == BZ_QUANTILE ? qi : wi).push_back(i);
     // the work list for tile multipliers (mw, mq), in the pinned table
     auto fill = [&](int mw, int mq) {
-        // order: most expensive tiles first (longest warm-up + tile), then by size
-        std::stable_sort(wi.begin(), wi.end(), [&](int a, int b) {
-            return batch_tile_rows(jobs[a].H, jobs[a].h, mw) + jobs[a].h >
-                   batch_tile_rows(jobs[b].H, jobs[b].h, mw) + jobs[b].h;
-        });
+        fill_window_jobs(jobs, wi.data(), (int)wi.size(), mode, mw, wj, hdr);
+        // quantile jobs: most expensive tiles first (longest warm-up + tile)
         std::stable_sort(qi.begin(), qi.end(), [&](int a, int b) {
             return (int64_t)jobs[a].w * (quant_tile_rows(jobs[a].H, jobs[a].h, mq) + jobs[a].h) >
                    (int64_t)jobs[b].w * (quant_tile_rows(jobs[b].H, jobs[b].h, mq) + jobs[b].h);
         });
         int64_t tb = 0;
-        for (size_t a = 0; a < wi.size(); a++) {
-            const bz_job &j = jobs[wi[a]];
-            WinJobDev &d = wj[a];
-            d.g = Image{j.image, j.H, j.W, j.in_pitch};
-            d.win = make_window(j.h, j.w);
-            d.T = make_thresh(j.method == BZ_SAUVOLA ? 0 : 1, j.k, j.method == BZ_SAUVOLA ? j.R : 128.0);
-            d.out = j.out;
-            d.out_pitch = j.out_pitch;
-            d.tile_h = batch_tile_rows(j.H, j.h, mw);
-            d.tiles_x = (j.W + kTileCols - 1) / kTileCols;
-            d.tile_begin = tb;
-            d.vec = ((uintptr_t)j.image % 8 == 0) && (j.in_pitch % 8 == 0);
-            d.wide = (int64_t)j.h * j.w > 66051;
-            tb += d.tiles_x * ((j.H + d.tile_h - 1) / d.tile_h);
-        }
-        hdr->win_tiles = tb;
         tb = 0;
         for (size_t a = 0; a < qi.size(); a++) {
             const bz_job &j = jobs[qi[a]];
@@ -365,9 +436,8 @@ bz_status run_batch(BatchSlot &s, const bz_job *jobs, int32_t n, bz_precision pr
             tb += d.tiles_x * ((j.H + d.tile_h - 1) / d.tile_h);
         }
         hdr->q_tiles = tb;
-        hdr->n_win = n_win;
         hdr->n_q = n_q;
-        hdr->win_next = 0;
+        hdr->pad0 = 0;
         hdr->q_next = 0;
     };
 
@@ -527,7 +597,8 @@ static void *noalloc_scratch_address(int device)
 // SM of the two persistent kernels (guarded by g_noalloc_mu).
 struct NoAllocLaunch {
     bool ready = false;
-    int grid_w = 0, grid_q = 0;
+    int grid_w[kWinClasses] = {0, 0, 0};
+    int grid_q = 0;
 };
 static NoAllocLaunch g_noalloc_launch[64][3];
 
@@ -542,11 +613,7 @@ static cudaError_t noalloc_prepare(NoAllocLaunch &L, int nsm)
                                  cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess)
         return e;
-    int occ_w = 0, occ_q = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_w, k_batch_window<MODE>, 32 * kBatchWarps, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_q, k_batch_quantile, 32, qsmem);
-    L.grid_w = nsm * (occ_w < 1 ? 1 : occ_w);
-    L.grid_q = nsm * (occ_q < 1 ? 1 : occ_q);
+    batch_grids<MODE>(nsm, qsmem, L.grid_w, L.grid_q);
     L.ready = true;
     return cudaSuccess;
 }
@@ -554,9 +621,8 @@ static cudaError_t noalloc_prepare(NoAllocLaunch &L, int nsm)
 template <int MODE>
 static cudaError_t noalloc_launch(NoAllocTable *dev, const NoAllocLaunch &L, cudaStream_t stream)
 {
-    k_batch_window<MODE><<<L.grid_w, 32 * kBatchWarps, 0, stream>>>(&dev->hdr, dev->win,
-                                                                    &dev->fallbacks);
-    k_batch_quantile<<<L.grid_q, 32, batch_quant_smem(), stream>>>(&dev->hdr, dev->q);
+    launch_batch_kernels<MODE>(&dev->hdr, dev->win, dev->q, &dev->fallbacks, L.grid_w, L.grid_q,
+                               batch_quant_smem(), stream);
     return cudaGetLastError();
 }
 
@@ -617,33 +683,13 @@ extern "C" bz_status binarize_batch_noalloc(const bz_job *jobs, int32_t n, bz_pr
         }
     }
     NoAllocTable &t = g_noalloc_host;
-    // window jobs first, most expensive tiles first (same order as binarize_batch)
+    // window jobs by kernel class, most expensive tiles first (as binarize_batch)
     int nw = 0, nq = 0;
     for (int32_t i = 0; i < n; i++)
         if (jobs[i].method != BZ_QUANTILE)
             g_noalloc_order[nw++] = i;
-    std::sort(g_noalloc_order, g_noalloc_order + nw, [&](int a, int b) {
-        const int64_t ca = batch_tile_rows(jobs[a].H, jobs[a].h) + jobs[a].h;
-        const int64_t cb = batch_tile_rows(jobs[b].H, jobs[b].h) + jobs[b].h;
-        return ca != cb ? ca > cb : a < b;
-    });
+    fill_window_jobs(jobs, g_noalloc_order, nw, mode, kBatchWinMult, t.win, &t.hdr);
     int64_t tb = 0;
-    for (int a = 0; a < nw; a++) {
-        const bz_job &j = jobs[g_noalloc_order[a]];
-        WinJobDev &d = t.win[a];
-        d.g = Image{j.image, j.H, j.W, j.in_pitch};
-        d.win = make_window(j.h, j.w);
-        d.T = make_thresh(j.method == BZ_SAUVOLA ? 0 : 1, j.k, j.method == BZ_SAUVOLA ? j.R : 128.0);
-        d.out = j.out;
-        d.out_pitch = j.out_pitch;
-        d.tile_h = batch_tile_rows(j.H, j.h);
-        d.tiles_x = (j.W + kTileCols - 1) / kTileCols;
-        d.tile_begin = tb;
-        d.vec = ((uintptr_t)j.image % 8 == 0) && (j.in_pitch % 8 == 0);
-        d.wide = (int64_t)j.h * j.w > 66051;
-        tb += d.tiles_x * ((j.H + d.tile_h - 1) / d.tile_h);
-    }
-    t.hdr.win_tiles = tb;
     for (int32_t i = 0; i < n; i++)
         if (jobs[i].method == BZ_QUANTILE)
             g_noalloc_order[nq++] = i;
@@ -669,14 +715,12 @@ extern "C" bz_status binarize_batch_noalloc(const bz_job *jobs, int32_t n, bz_pr
         tb += d.tiles_x * ((j.H + d.tile_h - 1) / d.tile_h);
     }
     t.hdr.q_tiles = tb;
-    t.hdr.n_win = nw;
     t.hdr.n_q = nq;
     // everything that must start at zero for this call: the two work-list
     // cursors and the fallback counter (the array keeps the previous call's
     // contents otherwise)
-    t.hdr.win_next = 0;
-    t.hdr.q_next = 0;
-    t.hdr.pad = 0;
+    t.hdr.q_next = 0;  // the window cursors were reset by fill_window_jobs
+    t.hdr.pad0 = 0;
     t.fallbacks = 0;
     // Only the used part of the list is copied.  The source is pageable host
     // memory: the copy has consumed it when cudaMemcpyAsync returns, so the

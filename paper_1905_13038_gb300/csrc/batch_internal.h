@@ -7,11 +7,20 @@
 
 namespace bz {
 
+// Window jobs go to one of three persistent kernels (kernel classes): 0 and
+// 1 the single-image pipelined path with one or two anchor words per lane
+// (pipe_words), 2 the generic row routine; each class has its own segment of
+// the job array and its own tile cursor, so that each kernel gets its own
+// register allocation as the single-image kernels do.
+constexpr int kWinClasses = 3;
+
 struct BatchHeader {
-    int32_t n_win, n_q;
-    int64_t win_tiles, q_tiles;
-    unsigned long long win_next, q_next;  // work-list cursors (reset by the host copy)
-    int64_t pad;
+    int32_t n_q, pad0;
+    int64_t q_tiles;
+    unsigned long long q_next;  // work-list cursors (reset by the host copy)
+    int32_t cls_begin[kWinClasses], cls_n[kWinClasses];  // job segment of each class
+    int64_t cls_tiles[kWinClasses];                       // tiles of each class
+    unsigned long long cls_next[kWinClasses];
 };
 
 struct WinJobDev {

@@ -73,8 +73,9 @@ struct Outputs {
     uint64_t *S2;
     uint32_t *n;
     unsigned long long *fallbacks;  // optional FP64-fallback counter
-    unsigned long long *flips;      // MODE_REPORT
+    unsigned long long *flips;      // MODE_REPORT (each may be null)
     unsigned long long *maxdt_bits; // MODE_REPORT (double bits, >= 0)
+    unsigned long long *maxratio_bits;  // MODE_REPORT: max |t32 - t64| / certified bound (double bits)
 };
 
 template <typename T>
@@ -342,6 +343,10 @@ __device__ __forceinline__ float v_float(uint32_t n, uint64_t S2, uint32_t S1)
 // Sauvola and Niblack: FP32 threshold, and in MODE_FP64 the certified bound
 // (undecided pixels go to the out-of-line FP64 decision); in MODE_REPORT the
 // FP32-vs-FP64 flips and the largest |t32 - t64|.
+// In MODE_REPORT also the largest ratio |t32 - t64| / bound over the two
+// variance roundings the kernels use, (V / n) / n here and V (1 / n^2) on the
+// pipelined path, each with its own certified bound: below 1 means that
+// every FP32 decision the FP64 mode keeps equals the canonical FP64 one.
 template <int METHOD, int MODE, bool INTERIOR, typename S2T>
 __device__ __forceinline__ void ext_row8(const ExtF &F, const ThreshExt &T, const Global &G, uint2 P,
                                          uint32_t off1, const uint32_t (&p1)[kColsPerLane], S2T off2,
@@ -349,7 +354,7 @@ __device__ __forceinline__ void ext_row8(const ExtF &F, const ThreshExt &T, cons
                                          const uint32_t (&cols)[kColsPerLane], float inv_nw,
                                          float inv_rows, const float (&inv_cols)[kColsPerLane],
                                          int64_t j0, int64_t W, uint32_t &byte, uint32_t &undecided,
-                                         unsigned long long &nflip, double &maxdt)
+                                         unsigned long long &nflip, double &maxdt, double &maxratio)
 {
 #pragma unroll
     for (int m = 0; m < kColsPerLane; m++) {
@@ -373,6 +378,11 @@ __device__ __forceinline__ void ext_row8(const ExtF &F, const ThreshExt &T, cons
                 nflip += (b64 != bit);
                 const double dt = fabs((double)t - t64);
                 maxdt = dt > maxdt ? dt : maxdt;
+                const float varB = v_float<S2T>(n, S2, S1) * (inv_n * inv_n);
+                float bndB;
+                const float tB = ext_t32<METHOD>(F, mu, varB, inv_n, bndB);
+                const double ra = dt / (double)bnd, rb = fabs((double)tB - t64) / (double)bndB;
+                maxratio = fmax(maxratio, fmax(ra, rb));
             }
         }
     }
@@ -583,7 +593,7 @@ __device__ __forceinline__ void window_rows(const Image &g, const Window &win, c
     }
 
     unsigned long long nfb = 0, nflip = 0;
-    double maxdt = 0.0;
+    double maxdt = 0.0, maxratio = 0.0;
 
     uint2 nA = make_uint2(0, 0), nB = nA, nC = nA, nD = nA, nP = nA;
     uint32_t nd1 = 0, nd2 = 0;
@@ -689,7 +699,7 @@ __device__ __forceinline__ void window_rows(const Image &g, const Window &win, c
         } else if (EXT) {
 #define BZ_EXT_ROW(M_)                                                                             \
     ext_row8<M_, MODE, INTERIOR, S2T>(F, TX, G, P, off1, p1, off2, p2, nw, nrow, cols, inv_nw, inv_rows, \
-                                      inv_cols, j0, W, byte, undecided, nflip, maxdt)
+                                      inv_cols, j0, W, byte, undecided, nflip, maxdt, maxratio)
             switch (T.method) {
             case METHOD_WOLF: BZ_EXT_ROW(METHOD_WOLF); break;
             case METHOD_FENG: BZ_EXT_ROW(METHOD_FENG); break;
@@ -737,6 +747,22 @@ __device__ __forceinline__ void window_rows(const Image &g, const Window &win, c
                         nflip += (b64 != bit);
                         const double dt = fabs((double)t - t64);
                         maxdt = dt > maxdt ? dt : maxdt;
+                        // the certified bound of every evaluation form the FP64
+                        // mode uses: general t with var = (V / n) / n (this
+                        // routine) and var = V (1 / n^2) (pipelined path), and
+                        // the Sauvola form m (alpha + beta s) with the latter
+                        const float magA = fmaf(fmaf(T.abeta, mu, T.agamma), s, T.aalpha * mu);
+                        const double rA = dt / (double)fmaf(T.eps, magA, T.delta64);
+                        const float sB = sqrt_approx(v_float<S2T>(n, S2, S1) * (inv_n * inv_n));
+                        const float tB = fmaf(fmaf(T.beta, mu, T.gamma), sB, T.alpha * mu);
+                        const float magB = fmaf(fmaf(T.abeta, mu, T.agamma), sB, T.aalpha * mu);
+                        const double rB = fabs((double)tB - t64) / (double)fmaf(T.eps, magB, T.delta64);
+                        double rS = 0.0;
+                        if (simple) {
+                            const float tS = mu * fmaf(T.beta, sB, T.alpha);
+                            rS = fabs((double)tS - t64) / (double)fmaf(T.eps, tS, T.delta64);
+                        }
+                        maxratio = fmax(maxratio, fmax(rA, fmax(rB, rS)));
                     }
                 }
             }
@@ -777,17 +803,22 @@ __device__ __forceinline__ void window_rows(const Image &g, const Window &win, c
     }
     if (MODE == MODE_REPORT) {
         unsigned long long v = nflip;
-        double mx = maxdt;
+        double mx = maxdt, mr = maxratio;
 #pragma unroll
         for (int d = 16; d >= 1; d >>= 1) {
             v += __shfl_xor_sync(0xFFFFFFFFu, v, d);
             const double y = __shfl_xor_sync(0xFFFFFFFFu, mx, d);
             mx = y > mx ? y : mx;
+            const double z = __shfl_xor_sync(0xFFFFFFFFu, mr, d);
+            mr = z > mr ? z : mr;
         }
         if (lane == 0) {
-            if (v)
+            if (v && o.flips)
                 atomicAdd(o.flips, v);
-            atomicMax(o.maxdt_bits, (unsigned long long)__double_as_longlong(mx));
+            if (o.maxdt_bits)
+                atomicMax(o.maxdt_bits, (unsigned long long)__double_as_longlong(mx));
+            if (o.maxratio_bits)
+                atomicMax(o.maxratio_bits, (unsigned long long)__double_as_longlong(mr));
         }
     }
 }

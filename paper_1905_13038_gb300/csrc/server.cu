@@ -8,8 +8,12 @@
 // idle batch slot on that slot's own stream (the batched persistent kernels
 // of batch.cu).  Several batches are in flight at once on different streams,
 // so requests that arrive while others run are admitted as soon as budget and
-// a slot free up, and their work overlaps on the device.  Completion is
-// detected with CUDA events; bz_server_wait blocks on a condition variable.
+// a slot free up, and their work overlaps on the device.  The scheduler
+// holds the server lock only to pick requests and to retire finished
+// batches; batches are built and launched outside it.  Each launch ends with
+// a host callback on its stream that wakes the scheduler (the callback only
+// sets a flag and signals), and completion is confirmed with the lane's CUDA
+// event; bz_server_wait blocks on a condition variable.
 //
 // Host-side fault injection for tests (environment variable BZ_FAULT):
 //   "launch"     every batch launch reports BZ_ECUDA without touching the GPU
@@ -43,10 +47,15 @@ struct ExecLane {
     BatchSlot slot;
     cudaStream_t stream = nullptr;
     cudaEvent_t ev = nullptr;
-    bool busy = false;
+    bool busy = false;      // a batch was handed to this lane
+    bool launched = false;  // ... and launched (event recorded, callback queued)
     bool failed = false;
+    bool signalled = false;  // the stream's callback ran
     std::vector<uint64_t> tickets;
+    std::vector<bz_job> jobs;
+    bz_precision prec = BZ_FP64;
     std::chrono::steady_clock::time_point ready_at;
+    bz_server *srv = nullptr;
 };
 
 }  // namespace bz
@@ -77,16 +86,16 @@ static int64_t job_bytes(const bz_job &j)
     return j.H * j.in_pitch + j.H * j.out_pitch;
 }
 
-// Completes the lanes whose event fired; called with srv->mu held.
+// Completes the lanes whose batch finished; called with srv->mu held.
 static void reap(bz_server *srv)
 {
     const auto now = std::chrono::steady_clock::now();
     for (ExecLane *L : srv->lanes) {
-        if (!L->busy)
+        if (!L->busy || (!L->launched && !L->failed))
             continue;
         bz_status result = BZ_OK;
         if (!L->failed) {
-            const cudaError_t q = cudaEventQuery(L->ev);
+            const cudaError_t q = cudaEventQuery(L->ev);  // never blocks
             if (q == cudaErrorNotReady)
                 continue;
             if (q != cudaSuccess)
@@ -110,25 +119,28 @@ static void reap(bz_server *srv)
             srv->inflight -= 1;
         }
         L->tickets.clear();
+        L->jobs.clear();
         L->busy = false;
+        L->launched = false;
         L->failed = false;
+        L->signalled = false;
         L->ready_at = {};
     }
 }
 
-// Admits queued requests into idle lanes; called with srv->mu held.
-static void admit(bz_server *srv)
+// Hands queued requests to idle lanes (FIFO under the budget and the slot
+// cap); called with srv->mu held.  Returns the lanes to launch.
+static std::vector<ExecLane *> pick(bz_server *srv)
 {
+    std::vector<ExecLane *> ready;
     for (ExecLane *L : srv->lanes) {
         if (L->busy)
             continue;
         if (srv->queue.empty())
-            return;
-        std::vector<bz_job> batch;
-        std::vector<uint64_t> tickets;
+            break;
         bz_precision prec = BZ_FP64;
         bool have_prec = false;
-        // FIFO admission; requests of another precision wait for a later batch
+        // requests of another precision wait for a later batch
         for (auto it = srv->queue.begin(); it != srv->queue.end();) {
             Request &r = srv->reqs[*it];
             if (have_prec && r.prec != prec) {
@@ -142,24 +154,30 @@ static void admit(bz_server *srv)
             r.state = RS_RUNNING;
             srv->inflight_bytes += r.bytes;
             srv->inflight += 1;
-            batch.push_back(r.job);
-            tickets.push_back(*it);
+            L->jobs.push_back(r.job);
+            L->tickets.push_back(*it);
             it = srv->queue.erase(it);
         }
-        if (batch.empty())
-            return;
-        L->tickets = tickets;
+        if (L->jobs.empty())
+            break;
+        L->prec = prec;
         L->busy = true;
+        L->launched = false;
         L->failed = false;
-        if (srv->fault_launch) {
-            L->failed = true;
-            continue;
-        }
-        const bz_status st = run_batch(L->slot, batch.data(), (int32_t)batch.size(), prec,
-                                       L->stream);
-        if (st != BZ_OK || cudaEventRecord(L->ev, L->stream) != cudaSuccess)
-            L->failed = true;
+        L->signalled = false;
+        ready.push_back(L);
     }
+    return ready;
+}
+
+// Host callback at the end of a lane's batch: wake the scheduler (no CUDA
+// call here).
+static void CUDART_CB lane_done(void *arg)
+{
+    ExecLane *L = static_cast<ExecLane *>(arg);
+    std::lock_guard<std::mutex> lk(L->srv->mu);
+    L->signalled = true;
+    L->srv->cv_work.notify_one();
 }
 
 static void scheduler(bz_server *srv)
@@ -168,17 +186,39 @@ static void scheduler(bz_server *srv)
     std::unique_lock<std::mutex> lk(srv->mu);
     for (;;) {
         reap(srv);
-        admit(srv);
+        std::vector<ExecLane *> ready = pick(srv);
         srv->cv_done.notify_all();
+        if (!ready.empty()) {
+            // build and launch outside the lock: submitters and waiters
+            // proceed meanwhile (a lane's fields belong to the scheduler
+            // while it is busy and not yet launched)
+            lk.unlock();
+            for (ExecLane *L : ready) {
+                bool ok = !srv->fault_launch;
+                if (ok)
+                    ok = run_batch(L->slot, L->jobs.data(), (int32_t)L->jobs.size(), L->prec, L->stream) ==
+                             BZ_OK &&
+                         cudaEventRecord(L->ev, L->stream) == cudaSuccess &&
+                         cudaLaunchHostFunc(L->stream, lane_done, L) == cudaSuccess;
+                lk.lock();
+                if (ok)
+                    L->launched = true;
+                else
+                    L->failed = true;
+                lk.unlock();
+            }
+            lk.lock();
+            continue;  // reap failed launches and pick again
+        }
         bool any_busy = false;
         for (ExecLane *L : srv->lanes)
             any_busy |= L->busy;
         if (srv->stop && srv->queue.empty() && !any_busy)
             break;
-        if (any_busy)
-            srv->cv_work.wait_for(lk, std::chrono::microseconds(20));
-        else
-            srv->cv_work.wait_for(lk, std::chrono::milliseconds(5));
+        // woken by a submission, a completion callback (which sets its flag
+        // and signals under the lock, so no wake-up is lost) or shutdown; the
+        // timeout paces BZ_FAULT=slow and bounds anything unforeseen
+        srv->cv_work.wait_for(lk, std::chrono::milliseconds(srv->fault_slow_ms > 0 ? 1 : 50));
     }
     srv->cv_done.notify_all();
 }
@@ -213,6 +253,7 @@ bz_status bz_server_create(int64_t hbm_budget_bytes, int32_t max_slots, bz_serve
     const int nlanes = 4;  // batches in flight at once (independent streams)
     for (int i = 0; i < nlanes; i++) {
         ExecLane *L = new ExecLane();
+        L->srv = srv;
         if (cudaStreamCreateWithFlags(&L->stream, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&L->ev, cudaEventDisableTiming) != cudaSuccess) {
             delete L;
@@ -287,30 +328,29 @@ bz_status bz_server_wait(bz_server *srv, uint64_t ticket, int32_t timeout_ms)
     if (it == srv->reqs.end())
         return BZ_EINVAL;
     auto done = [&] { return srv->reqs[ticket].state == RS_DONE; };
-    bool timed_out = false;
     if (timeout_ms < 0) {
         srv->cv_done.wait(lk, done);
     } else if (!srv->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), done)) {
-        timed_out = true;
         Request &r = srv->reqs[ticket];
         if (r.state == RS_QUEUED) {
+            // never started: dropped, its buffers are free now
             for (auto q = srv->queue.begin(); q != srv->queue.end(); ++q)
                 if (*q == ticket) {
                     srv->queue.erase(q);
                     break;
                 }
-            r.state = RS_DONE;
-            r.result = BZ_ECANCELLED;
-        } else {
-            // running: its buffers are in use until the GPU finishes
-            r.cancelled = true;
-            srv->cv_done.wait(lk, done);
+            srv->reqs.erase(ticket);
+            return BZ_ETIMEOUT;
         }
+        // running: the GPU work cannot be recalled.  The request is
+        // cancelled and keeps its ticket: its buffers stay in use until a
+        // later wait on the ticket returns BZ_ECANCELLED (or the server is
+        // destroyed)
+        r.cancelled = true;
+        return BZ_ETIMEOUT;
     }
     const bz_status result = srv->reqs[ticket].result;
     srv->reqs.erase(ticket);
-    if (timed_out)
-        return BZ_ETIMEOUT;
     return result;
 }
 

@@ -9,7 +9,9 @@
 //   batch    tile rows of the batched window and quantile kernels, as
 //            multiples of each job's window height.
 // Candidates are timed with CUDA events on the caller's stream (one
-// untimed run, then the mean of a few), the fastest is stored under a key of
+// untimed run, then the mean of a few, each after reading a buffer larger
+// than L2 so that the input comes from HBM as it does for a stream of
+// distinct images), the fastest is stored under a key of
 // GPU name and SM count, kernel, precision (or quantile class), window-size
 // buckets (next power of two of h and w) and image-size bucket (half octaves
 // of H x W), and the cache is written back to its file.
@@ -343,8 +345,57 @@ void tune_put(const std::string &key, const TuneCfg &c, bool save)
 }
 
 // --------------------------------------------------------- the searches --
+// A device buffer larger than L2, read before each timed run (k_l2_evict) so
+// that a candidate is timed with its input coming from HBM and with L2
+// holding clean lines, as in a stream of distinct images (null when it
+// cannot be had: the runs are then timed warm).  One per device, allocated
+// and zeroed by the first tuning call on it.
+__global__ void k_l2_evict(const uint4 *p, size_t n, unsigned *sink)
+{
+    uint32_t acc = 0;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const uint4 v = __ldcg(p + i);
+        acc ^= v.x ^ v.y ^ v.z ^ v.w;
+    }
+    if (acc == 0x9E3779B9u)  // never for the zeroed buffer; keeps the loads
+        atomicAdd(sink, 1u);
+}
+
+static void *l2_flush_buffer(size_t &bytes)
+{
+    static std::mutex mu;
+    static void *bufs[64] = {nullptr};
+    static size_t sizes[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(mu);
+    if (!bufs[dev]) {
+        int l2 = 0;
+        cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev);
+        const size_t want = (size_t)(l2 > 0 ? l2 : (128 << 20)) * 5 / 4;
+        if (cudaMalloc(&bufs[dev], want + 256) != cudaSuccess) {
+            cudaGetLastError();
+            bufs[dev] = nullptr;
+            return nullptr;
+        }
+        if (cudaMemset(bufs[dev], 0, want + 256) != cudaSuccess) {
+            cudaFree(bufs[dev]);
+            cudaGetLastError();
+            bufs[dev] = nullptr;
+            return nullptr;
+        }
+        sizes[dev] = want;
+    }
+    bytes = sizes[dev];
+    return bufs[dev];
+}
+
 // Mean device time of `launch` (a callable returning cudaError_t) on
-// `stream`: one untimed run, then `reps` timed ones.  Negative on error.
+// `stream`: one untimed run, then `reps` timed ones, each after an L2 flush.
+// Negative on error.
 template <typename F>
 static double time_on(cudaStream_t stream, int reps, F &&launch)
 {
@@ -355,20 +406,30 @@ static double time_on(cudaStream_t stream, int reps, F &&launch)
         cudaGetLastError();
         return -1.0;
     }
-    double ms = -1.0;
-    if (launch() == cudaSuccess && cudaEventRecord(a, stream) == cudaSuccess) {
-        bool ok = true;
-        for (int r = 0; r < reps && ok; r++)
-            ok = launch() == cudaSuccess;
+    size_t fbytes = 0;
+    void *fbuf = l2_flush_buffer(fbytes);
+    double total = 0.0;
+    bool ok = launch() == cudaSuccess;
+    int sms = 152;
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess)
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    for (int r = 0; r < reps && ok; r++) {
+        if (fbuf) {
+            k_l2_evict<<<sms * 4, 256, 0, stream>>>((const uint4 *)fbuf, fbytes / 16,
+                                                    (unsigned *)((char *)fbuf + fbytes));
+            ok = cudaGetLastError() == cudaSuccess;
+        }
         float t = 0.0f;
-        if (ok && cudaEventRecord(b, stream) == cudaSuccess && cudaEventSynchronize(b) == cudaSuccess &&
-            cudaEventElapsedTime(&t, a, b) == cudaSuccess)
-            ms = (double)t / reps;
+        ok = ok && cudaEventRecord(a, stream) == cudaSuccess && launch() == cudaSuccess &&
+             cudaEventRecord(b, stream) == cudaSuccess && cudaEventSynchronize(b) == cudaSuccess &&
+             cudaEventElapsedTime(&t, a, b) == cudaSuccess;
+        total += t;
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     cudaGetLastError();
-    return ms;
+    return ok ? total / reps : -1.0;
 }
 
 static void push_unique(std::vector<int64_t> &v, int64_t x, int64_t lo, int64_t hi)

@@ -135,11 +135,23 @@ def test_server_budget_cancel_timeout_and_faults(monkeypatch):
         assert srv.wait(t, 60000) == 5  # BZ_ECUDA
     finally:
         srv.close()
+    # late completions: a wait on a running request times out without
+    # waiting for the GPU; the request is cancelled and keeps its ticket until
+    # a later wait reports BZ_ECANCELLED.  A request still queued when its wait
+    # times out is dropped (its ticket is then unknown).
     monkeypatch.setenv("BZ_FAULT", "slow:1500")
-    srv = bz.Server(hbm_budget_bytes=1 << 30, max_slots=4)
+    srv = bz.Server(hbm_budget_bytes=1 << 30, max_slots=1)
     try:
-        t = srv.submit(jobs[0])
-        assert srv.wait(t, 50) == 6  # BZ_ETIMEOUT, after the request completed
+        t0 = srv.submit(jobs[0])
+        t1 = srv.submit(jobs[1])
+        import time
+        time.sleep(0.2)  # t0 is running (slowly), t1 waits for the one slot
+        start = time.perf_counter()
+        assert srv.wait(t0, 50) == 6  # BZ_ETIMEOUT
+        assert srv.wait(t1, 50) == 6  # BZ_ETIMEOUT, dropped while queued
+        assert time.perf_counter() - start < 1.0  # neither waited for the GPU
+        assert srv.wait(t1, 0) == 1  # BZ_EINVAL: no such ticket any more
+        assert srv.wait(t0, 60000) == 8  # BZ_ECANCELLED once the GPU is done
     finally:
         srv.close()
     monkeypatch.delenv("BZ_FAULT")

@@ -1,5 +1,6 @@
 """The certified FP32 threshold relies on sqrt.approx.f32 being within 2^-22
-relative of the correctly rounded square root; measure it on the GPU."""
+relative of the correctly rounded square root; measure it on the GPU at every
+float of the variance range the kernels can produce."""
 import os
 import subprocess
 
