@@ -32,8 +32,10 @@
  * caller (for instance a torch tensor); the library neither frees nor keeps
  * it past the completion of the work on `stream` (a cudaStream_t passed as
  * void*, NULL = legacy default stream).  The image has H rows of in_pitch
- * >= W bytes; out has H rows of out_pitch >= ceil(W/8) bytes.  Only the
- * first ceil(W/8) bytes of each output row are written.  Image and output
+ * >= W bytes, all H * in_pitch of them readable: the kernels may read a row's
+ * bytes past column W (never using them) when they load aligned 8-byte words.
+ * out has H rows of out_pitch >= ceil(W/8) bytes.  Only the first ceil(W/8)
+ * bytes of each output row are written.  Image and output
  * must not overlap (Sec. 3.2 assumptions): overlap -> BZ_EOVERLAP.
  *
  * Errors.  Argument errors are reported synchronously and nothing is
@@ -442,6 +444,17 @@ bz_status binarize_bound_report(int32_t method, const uint8_t *image, int64_t H,
                                 int64_t W, int64_t in_pitch, int32_t h,
                                 int32_t w, const double *params,
                                 double *max_ratio_dev, void *stream);
+
+/* Debug build (libbinarize_debug.so, compiled with -DBZ_DEBUG; no
+ * counterpart in the paper): every global load and store of the window,
+ * small-page, stripe, quantile, min/max, Haar, batch and Table 1 kernels is
+ * checked against the extent of its buffer; an access outside sets a status
+ * bit (1 image load, 2 output store, 4 library scratch), records the first
+ * offending address and is skipped, without trapping.  bz_debug_status
+ * synchronizes with the device, returns the accumulated bits and address
+ * (clearing them when reset != 0) and returns 0; in the normal build it
+ * returns 1 with status 0.  -1 on a NULL argument or a CUDA error. */
+int32_t bz_debug_status(uint32_t *status, uint64_t *first_addr, int32_t reset);
 
 /* ---------------------------------------------------------------------- */
 /* Autotuning of launch parameters (no counterpart in the paper: how the  */

@@ -29,7 +29,8 @@ __all__ = [
     "window_minmax", "binarize_bernsen", "haar_feature", "HAAR_FEATURES", "binarize_inplace",
     "inplace_scratch_bytes", "binarize_host", "binarize_host_multi",
     "autotune_window", "autotune_quantile", "autotune_batch", "tune_key", "tune_get", "tune_set",
-    "tune_load", "tune_save", "tune_clear", "tune_window_plan", "bound_report",
+    "tune_load", "tune_save", "tune_clear", "tune_window_plan", "bound_report", "use_library",
+    "debug_status",
 ]
 
 FP64, FP32, FP64_DIRECT = 0, 1, 2
@@ -73,14 +74,27 @@ class _HaarC(ctypes.Structure):
                 ("col_len", ctypes.c_int32 * 4), ("col_wt", ctypes.c_int32 * 4)]
 
 
+_lib_path = None  # None: the normal build (libbinarize.so)
+
+
+def use_library(debug: bool = False) -> str:
+    """Route every following call to the normal library or to the
+    bounds-checked debug build (built on first use); returns its path."""
+    global _lib, _lib_path
+    _lib_path = _build.build(debug=True) if debug else None
+    _lib = None
+    return _lib_path or _build.LIB
+
+
 def _load():
     global _lib
     if _lib is not None:
         return _lib
-    if not os.path.exists(_build.LIB):
-        raise RuntimeError(f"{_build.LIB} is missing: build the CUDA library first "
+    path = _lib_path or _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build the CUDA library first "
                            "(paper_1905_13038_gb300.build() or __graft_entry__.build())")
-    lib = ctypes.CDLL(_build.LIB)
+    lib = ctypes.CDLL(path)
     P, i64, i32, f64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
     st = ctypes.c_int
     sig = {
@@ -114,6 +128,7 @@ def _load():
         "bz_server_wait": ([P, ctypes.c_uint64, i32], st),
         "bz_server_cancel": ([P, ctypes.c_uint64], st),
         "bz_server_destroy": ([P], st),
+        "bz_debug_status": ([P, P, i32], i32),
         "binarize_bound_report": ([i32, P, i64, i64, i64, i32, i32, P, P, P], st),
         "bz_autotune_window": ([i32, P, i64, i64, i64, i32, i32, f64, f64, P, i64, st, P, P, P, P, P], st),
         "bz_autotune_quantile": ([P, i64, i64, i64, i32, i32, i32, i32, i32, P, i64, P, P, P], st),
@@ -513,6 +528,16 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def debug_status(reset: bool = True):
+    """(status bits, first offending address) of the bounds-checked build, or
+    None from the normal build (bz_debug_status)."""
+    st, addr = ctypes.c_uint32(), ctypes.c_uint64()
+    r = _load().bz_debug_status(ctypes.byref(st), ctypes.byref(addr), 1 if reset else 0)
+    if r < 0:
+        raise RuntimeError("bz_debug_status failed")
+    return None if r == 1 else (st.value, addr.value)
 
 
 def bound_report(method: int, image, h: int, w: int, params, W: int | None = None, stream=None) -> float:

@@ -37,7 +37,7 @@ bz_status check_out(const uint8_t *image, int64_t H, int64_t W, int64_t in_pitch
     const int64_t wb = (W + 7) / 8;
     if (!out || out_pitch < wb || out_pitch > (INT64_MAX / H))
         return BZ_EINVAL;
-    if (ranges_overlap(image, span_bytes(H, in_pitch, W), out, span_bytes(H, out_pitch, wb)))
+    if (ranges_overlap(image, span_bytes(H, in_pitch, in_pitch), out, span_bytes(H, out_pitch, wb)))
         return BZ_EOVERLAP;
     return BZ_OK;
 }
@@ -98,6 +98,8 @@ static bz_status run_threshold(int method, const uint8_t *image, int64_t H, int6
     Outputs o{};
     o.bits = out;
     o.out_pitch = out_pitch;
+    o.bits_bytes = dbg_extent(H, out_pitch, (W + 7) / 8);
+    o.bits_bytes = dbg_extent(H, out_pitch, (W + 7) / 8);
     if (mode == MODE_FP64) {
         int dev = 0;
         if (cudaGetDevice(&dev) != cudaSuccess)
@@ -183,6 +185,8 @@ static bz_status run_ext_binarize(int method, const uint8_t *image, int64_t H, i
     Outputs o{};
     o.bits = out;
     o.out_pitch = out_pitch;
+    o.bits_bytes = dbg_extent(H, out_pitch, (W + 7) / 8);
+    o.bits_bytes = dbg_extent(H, out_pitch, (W + 7) / 8);
     if (mode == MODE_FP64) {
         int dev = 0;
         if (cudaGetDevice(&dev) != cudaSuccess)
@@ -258,7 +262,7 @@ bz_status window_sums(const uint8_t *image, int64_t H, int64_t W, int64_t in_pit
     bz_status st = check_image(image, H, W, in_pitch, h, w);
     if (st != BZ_OK)
         return st;
-    const size_t img_bytes = (size_t)((H - 1) * in_pitch + W);
+    const size_t img_bytes = (size_t)(H * in_pitch);
     const size_t HW = (size_t)(H * W);
     if ((S1 && ranges_overlap(image, img_bytes, S1, HW * 4)) ||
         (S2 && ranges_overlap(image, img_bytes, S2, HW * 8)) ||
@@ -269,6 +273,7 @@ bz_status window_sums(const uint8_t *image, int64_t H, int64_t W, int64_t in_pit
     o.S1 = S1;
     o.S2 = S2;
     o.n = n;
+    o.sums_n = H * W;
     Thresh T = make_thresh(0, 0.5, 128.0);
     return launch_window(MODE_SUMS, g, make_window(h, w), T, o, (cudaStream_t)stream) ==
                    cudaSuccess
@@ -284,7 +289,7 @@ bz_status window_quantile(const uint8_t *image, int64_t H, int64_t W, int64_t in
         return st;
     if (!Q || q_den < 1 || q_num < 0 || q_num > q_den)
         return BZ_EINVAL;
-    if (ranges_overlap(image, (size_t)((H - 1) * in_pitch + W), Q, (size_t)(H * W)))
+    if (ranges_overlap(image, (size_t)(H * in_pitch), Q, (size_t)(H * W)))
         return BZ_EOVERLAP;
     Image g{image, H, W, in_pitch};
     return launch_quantile(g, make_window(h, w), q_num, q_den, 0, nullptr, 0, Q,
@@ -367,7 +372,7 @@ bz_status global_stats(const uint8_t *image, int64_t H, int64_t W, int64_t in_pi
     if (!image || !stats_dev || H < 1 || W < 1 || H > 2147483647LL || W > 2147483647LL ||
         in_pitch < W || in_pitch > (INT64_MAX / H) || !global_size_ok(H, W))
         return BZ_EINVAL;
-    const size_t img_bytes = (size_t)((H - 1) * in_pitch + W);
+    const size_t img_bytes = (size_t)(H * in_pitch);
     if (ranges_overlap(image, img_bytes, stats_dev, 3 * sizeof(double)) ||
         (sums_dev && ranges_overlap(image, img_bytes, sums_dev, 3 * sizeof(uint64_t))))
         return BZ_EOVERLAP;
@@ -413,7 +418,7 @@ bz_status window_minmax(const uint8_t *image, int64_t H, int64_t W, int64_t in_p
         return st;
     if (!mn || !mx)
         return BZ_EINVAL;
-    const size_t img_bytes = (size_t)((H - 1) * in_pitch + W);
+    const size_t img_bytes = (size_t)(H * in_pitch);
     const size_t HW = (size_t)(H * W);
     if (ranges_overlap(image, img_bytes, mn, HW) || ranges_overlap(image, img_bytes, mx, HW) ||
         ranges_overlap(mn, HW, mx, HW))
@@ -471,7 +476,7 @@ bz_status haar_feature(const uint8_t *image, int64_t H, int64_t W, int64_t in_pi
     // |feature| <= 255 h w max|f| max|g| must stay below 2^31
     if (255.0 * h * w * fmax * gmax > 2147483647.0)
         return BZ_EINVAL;
-    const size_t img_bytes = (size_t)((H - 1) * in_pitch + W);
+    const size_t img_bytes = (size_t)(H * in_pitch);
     if (ranges_overlap(image, img_bytes, out, (size_t)(H * W) * sizeof(int32_t)))
         return BZ_EOVERLAP;
     HaarDev hd{};
@@ -559,6 +564,7 @@ bz_status binarize_inplace(int32_t method, uint8_t *image, int64_t H, int64_t W,
         o.bits = scratch + (int64_t)slot * band * cw;
         o.out_pitch = cw;
         o.out_row0 = r0;
+        o.bits_bytes = (size_t)band * cw;
         o.fallbacks = fb;
         if (launch_window_rows(mode, g, win, T, o, r0, r1, s) != cudaSuccess)
             st = BZ_ECUDA;
@@ -713,6 +719,7 @@ static bz_status host_run(int32_t method, const uint8_t *image_host, int64_t H, 
         Outputs o{};
         o.bits = sl.out + plane * (size_t)q;
         o.out_pitch = cw;
+        o.bits_bytes = plane;
         o.fallbacks = fb;
         ok = launch_window(mode, Image{sl.img, H, W, dpitch}, make_window(hv[q], wv[q]), T, o, hs->comp) ==
              cudaSuccess;
@@ -888,6 +895,25 @@ int32_t bz_tile_schedule(int64_t H, int64_t W, int32_t sms, int32_t pipe, int32_
     if (!out)
         return -1;
     return plan_tile_schedule(H, W, sms, pipe != 0, stripes != 0, out);
+}
+
+int32_t bz_debug_status(uint32_t *status, uint64_t *first_addr, int32_t reset)
+{
+    if (!status || !first_addr)
+        return -1;
+    unsigned st = 0;
+    unsigned long long addr = 0;
+    int r = 0;
+    for (auto fn : {dbg_status_window, dbg_status_small, dbg_status_stripes, dbg_status_quantile, dbg_status_minmax,
+                    dbg_status_haar, dbg_status_batch, dbg_status_table1}) {
+        const int e = fn(&st, &addr, reset != 0);
+        if (e < 0)
+            return -1;
+        r = e;  // 1 throughout in a normal build
+    }
+    *status = st;
+    *first_addr = addr;
+    return r;
 }
 
 int64_t bz_last_fp64_fallbacks(void *stream)

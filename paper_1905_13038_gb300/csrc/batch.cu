@@ -58,6 +58,7 @@ __global__ void __launch_bounds__(32 * kBatchWarps, CLS < 2 ? kBlocksPerSM : 1)
         Outputs o{};
         o.bits = J.out;
         o.out_pitch = J.out_pitch;
+        o.bits_bytes = dbg_extent(J.g.H, J.out_pitch, (J.g.W + 7) / 8);
         o.fallbacks = fallbacks;
         if (kPipe) {
             window_tile<MODE, true, uint32_t, kPipe ? CLS + 1 : 0>(J.g, J.win, J.T, o, x0, y0, y1, lane,
@@ -625,6 +626,9 @@ static cudaError_t noalloc_launch(NoAllocTable *dev, const NoAllocLaunch &L, cud
                                batch_quant_smem(), stream);
     return cudaGetLastError();
 }
+
+// Bounds-check status of this file's kernels (debug build; 1 otherwise).
+BZ_DEBUG_ACCESSOR(dbg_status_batch)
 
 }  // namespace bz
 

@@ -181,6 +181,18 @@ int64_t quantile_band_rows(int64_t H, int64_t W);
 // stripes (0/1), resident warps into out[0..5].
 int plan_window_launch(int64_t H, int64_t W, const Window &win, int sms, bool pipe, int64_t out[6]);
 
+// Bounds-check status of each kernel file (bz_debug.cuh): ORs its status
+// into *status, keeps the first offending address, clears it with reset;
+// returns 0, 1 when the library is not a debug build, -1 on a CUDA error.
+int dbg_status_window(unsigned *status, unsigned long long *addr, bool reset);
+int dbg_status_small(unsigned *status, unsigned long long *addr, bool reset);
+int dbg_status_stripes(unsigned *status, unsigned long long *addr, bool reset);
+int dbg_status_quantile(unsigned *status, unsigned long long *addr, bool reset);
+int dbg_status_minmax(unsigned *status, unsigned long long *addr, bool reset);
+int dbg_status_haar(unsigned *status, unsigned long long *addr, bool reset);
+int dbg_status_batch(unsigned *status, unsigned long long *addr, bool reset);
+int dbg_status_table1(unsigned *status, unsigned long long *addr, bool reset);
+
 // Library-owned per-device scratch: FP64-fallback counter.
 unsigned long long *fallback_counter(int device);
 

@@ -96,6 +96,7 @@ __device__ __forceinline__ void quantile_warp_tile(const Image &g, const Window 
     const int64_t j = x0 + lane;
     const bool live = j < g.W;
     const int H = (int)g.H;
+    [[maybe_unused]] const size_t img_ext = dbg_image_extent(g);
 
     __syncwarp();  // the previous tile of this warp is done with the arrays
     {
@@ -168,15 +169,19 @@ __device__ __forceinline__ void quantile_warp_tile(const Image &g, const Window 
             const uint8_t *p = g.img + (int64_t)ra * g.pitch;
 #pragma unroll
             for (int t = 0; t < NPF; t++)
-                pin[t] = (lmask >> t & 1u) ? (uint32_t)p[lane_off + 32 * t] : 256u;
+                pin[t] = ((lmask >> t & 1u) && BZ_DBG_IN(p + lane_off + 32 * t, 1, g.img, img_ext, kDbgImage))
+                             ? (uint32_t)p[lane_off + 32 * t]
+                             : 256u;
         }
         if (s >= h && rb >= 0) {
             const uint8_t *p = g.img + (int64_t)rb * g.pitch;
 #pragma unroll
             for (int t = 0; t < NPF; t++)
-                pout[t] = (lmask >> t & 1u) ? (uint32_t)p[lane_off + 32 * t] : 256u;
+                pout[t] = ((lmask >> t & 1u) && BZ_DBG_IN(p + lane_off + 32 * t, 1, g.img, img_ext, kDbgImage))
+                              ? (uint32_t)p[lane_off + 32 * t]
+                              : 256u;
         }
-        if (s >= h - 1 && live)
+        if (s >= h - 1 && live && BZ_DBG_IN(g.img + (y0 + s - h + 1) * g.pitch + j, 1, g.img, img_ext, kDbgImage))
             pc = g.img[(y0 + s - h + 1) * g.pitch + j];
     };
     auto commit = [&](uint16_t *dst, const uint32_t *v, int row) {
@@ -188,7 +193,8 @@ __device__ __forceinline__ void quantile_warp_tile(const Image &g, const Window 
         const uint8_t *p = g.img + (int64_t)row * g.pitch;
         for (int k = 32 * NPF + lane; k < span; k += 32) {
             const int64_t col = span0 + k;
-            dst[k] = (col >= 0 && col < g.W) ? (uint16_t)p[col] : (uint16_t)256;
+            dst[k] = (col >= 0 && col < g.W && BZ_DBG_IN(p + col, 1, g.img, img_ext, kDbgImage)) ? (uint16_t)p[col]
+                                                                                           : (uint16_t)256;
         }
     };
 
@@ -383,14 +389,15 @@ __device__ __forceinline__ void quantile_warp_tile(const Image &g, const Window 
         uint32_t bit = 0;
         if (live) {
             bit = (I <= Q - offset) ? 0u : 1u;
-            if (Qout)
+            if (Qout && BZ_DBG_IN(Qout + i * g.W + j, 1, Qout, (size_t)(g.H * g.W), kDbgOutput))
                 Qout[i * g.W + j] = (uint8_t)Q;
         }
         if (out) {
             const uint32_t word = __ballot_sync(0xFFFFFFFFu, bit);
             if (lane < 4) {
                 const int64_t c8 = x0 + 8 * lane;
-                if (c8 < g.W)
+                if (c8 < g.W && BZ_DBG_IN(out + i * out_pitch + (c8 >> 3), 1, out,
+                                          dbg_extent(g.H, out_pitch, (g.W + 7) / 8), kDbgOutput))
                     out[i * out_pitch + (c8 >> 3)] = (uint8_t)(word >> (8 * lane));
             }
         }

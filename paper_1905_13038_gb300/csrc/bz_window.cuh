@@ -24,6 +24,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "bz_debug.cuh"
+
 namespace bz {
 
 constexpr int kColsPerLane = 8;
@@ -36,6 +38,13 @@ struct Image {
     const uint8_t *img;
     int64_t H, W, pitch;
 };
+
+// Bytes of an image buffer: H rows of pitch bytes (the C ABI's contract;
+// aligned 8-byte loads may read a row's padding past column W).
+__host__ __device__ inline size_t dbg_image_extent(const Image &g)
+{
+    return (size_t)(g.H * g.pitch);
+}
 
 struct Window {
     int h, w, l, r, o, u;
@@ -69,6 +78,8 @@ struct Outputs {
     uint8_t *bits;        // packed output (binarize modes)
     int64_t out_pitch;
     int64_t out_row0;     // image row i is output row i - out_row0
+    size_t bits_bytes;    // extent of `bits` (bounds checks of the debug build)
+    int64_t sums_n;       // elements of S1, S2 and n (debug build)
     uint32_t *S1;         // MODE_SUMS (each may be null)
     uint64_t *S2;
     uint32_t *n;
@@ -147,10 +158,12 @@ __device__ __forceinline__ int32_t byte_at(uint2 v, int m)
 // sel = byte_perm selector for offset k & 3.
 template <bool VEC>
 __device__ __forceinline__ uint2 ld8(const uint8_t *rp, int64_t col, bool fast, int k, unsigned sel,
-                                     int64_t W)
+                                     int64_t W, const uint8_t *base = nullptr, size_t ext = 0)
 {
     if (VEC && fast) {
         const uint8_t *p = rp + (col - k);
+        if (!BZ_DBG_IN(p, k ? 16 : 8, base, ext, kDbgImage))
+            return make_uint2(0u, 0u);
         const uint2 a = __ldg(reinterpret_cast<const uint2 *>(p));
         if (k == 0)
             return a;
@@ -175,12 +188,14 @@ __device__ __forceinline__ uint2 ld8(const uint8_t *rp, int64_t col, bool fast, 
 // row, as (sum, sum of squares); words of 4 columns, lane-strided.
 template <bool VEC>
 __device__ __forceinline__ void anchor_words(const uint8_t *rp, int64_t a4, int64_t c0, int64_t end,
-                                             int64_t W, int lane, uint32_t &s1, uint32_t &s2)
+                                             int64_t W, int lane, uint32_t &s1, uint32_t &s2,
+                                             const uint8_t *base = nullptr, size_t ext = 0)
 {
     for (int64_t c4 = a4 + 4 * lane; c4 < end; c4 += 128) {
         uint32_t wd;
         if (VEC && c4 >= 0 && c4 + 4 <= W) {
-            wd = __ldg(reinterpret_cast<const uint32_t *>(rp + c4));
+            wd = BZ_DBG_IN(rp + c4, 4, base, ext, kDbgImage) ? __ldg(reinterpret_cast<const uint32_t *>(rp + c4))
+                                                             : 0u;
         } else {
             wd = 0;
 #pragma unroll
@@ -301,16 +316,22 @@ __device__ __forceinline__ void warm8(uint2 A, uint2 B, int32_t *E1, uint32_t *E
 // The third word is only needed when k4 > 0; when k4 == 0 the second word is
 // read again, so no byte past p + 8 is touched.  Requires image base and
 // pitch to be multiples of 4 and the 8 bytes to lie inside the row.
-__device__ __forceinline__ uint2 ld8_w3(const uint8_t *p, int k4, unsigned sel)
+__device__ __forceinline__ uint2 ld8_w3(const uint8_t *p, int k4, unsigned sel, const uint8_t *base = nullptr,
+                                        size_t ext = 0)
 {
+    if (!BZ_DBG_IN(p - k4, k4 ? 12 : 8, base, ext, kDbgImage))
+        return make_uint2(0u, 0u);
     const uint32_t *q = reinterpret_cast<const uint32_t *>(p - k4);
     const uint32_t w0 = __ldg(q), w1 = __ldg(q + 1), w2 = __ldg(q + (k4 ? 2 : 1));
     return make_uint2(__byte_perm(w0, w1, sel), __byte_perm(w1, w2, sel));
 }
 
 // Interior loads: 8 bytes at `p` (p - k is 8-byte aligned; k warp-uniform).
-__device__ __forceinline__ uint2 ld8_fast(const uint8_t *p, int k, unsigned sel)
+__device__ __forceinline__ uint2 ld8_fast(const uint8_t *p, int k, unsigned sel, const uint8_t *base = nullptr,
+                                          size_t ext = 0)
 {
+    if (!BZ_DBG_IN(p - k, k ? 16 : 8, base, ext, kDbgImage))
+        return make_uint2(0u, 0u);
     const uint2 a = __ldg(reinterpret_cast<const uint2 *>(p - k));
     if (k == 0)
         return a;
@@ -400,13 +421,17 @@ __device__ __forceinline__ void warm_from_stripes(const uint2 *st, int64_t W, in
 #pragma unroll
     for (int m = 0; m < kColsPerLane; m++) {
         const int64_t xa = colA + m, xb = colB + m;
-        const uint2 ca = (xa >= 0 && xa < W) ? __ldg(st + xa) : make_uint2(0u, 0u);
-        const uint2 cb = (xb >= 0 && xb < W) ? __ldg(st + xb) : make_uint2(0u, 0u);
+        const uint2 ca = (xa >= 0 && xa < W && BZ_DBG_IN(st + xa, 8, st, (size_t)W * 8, kDbgScratch))
+                             ? __ldg(st + xa)
+                             : make_uint2(0u, 0u);
+        const uint2 cb = (xb >= 0 && xb < W && BZ_DBG_IN(st + xb, 8, st, (size_t)W * 8, kDbgScratch))
+                             ? __ldg(st + xb)
+                             : make_uint2(0u, 0u);
         E1[m] = (int32_t)(ca.x - cb.x);
         E2[m] = ca.y - cb.y;
     }
     for (int64_t x = ac0 + lane; x < aend; x += 32) {
-        if (x >= 0 && x < W) {
+        if (x >= 0 && x < W && BZ_DBG_IN(st + x, 8, st, (size_t)W * 8, kDbgScratch)) {
             const uint2 c = __ldg(st + x);
             a1p += c.x;
             a2p += c.y;
@@ -427,6 +452,7 @@ __device__ __forceinline__ void window_rows(const Image &g, const Window &win, c
     const int64_t W = g.W, H = g.H;
     const int64_t j0 = x0 + (int64_t)kColsPerLane * lane;
     const int l = win.l, r = win.r, oo = win.o, u = win.u;
+    [[maybe_unused]] const size_t img_ext = dbg_image_extent(g);
 
     const int64_t colA = j0 + r, colB = j0 - l;
     const bool fastA = INTERIOR || (VEC && colA >= 0 && colA + 8 <= W);
@@ -439,11 +465,11 @@ __device__ __forceinline__ void window_rows(const Image &g, const Window &win, c
     auto load_row = [&](int64_t row, uint2 &A, uint2 &B) {
         const uint8_t *rp = g.img + row * g.pitch;
         if (INTERIOR) {
-            A = ld8_fast(rp + colA, kA, selA);
-            B = ld8_fast(rp + colB, kB, selB);
+            A = ld8_fast(rp + colA, kA, selA, g.img, img_ext);
+            B = ld8_fast(rp + colB, kB, selB, g.img, img_ext);
         } else {
-            A = ld8<VEC>(rp, colA, fastA, kA, selA, W);
-            B = ld8<VEC>(rp, colB, fastB, kB, selB, W);
+            A = ld8<VEC>(rp, colA, fastA, kA, selA, W, g.img, img_ext);
+            B = ld8<VEC>(rp, colB, fastB, kB, selB, W, g.img, img_ext);
         }
     };
 
@@ -495,7 +521,10 @@ __device__ __forceinline__ void window_rows(const Image &g, const Window &win, c
         const uint8_t *rp = g.img + row * g.pitch;
         if (one_word) {
             if (has_word) {
-                const uint32_t wd = __ldg(reinterpret_cast<const uint32_t *>(rp + c4)) & keep;
+                const uint32_t wd = (BZ_DBG_IN(rp + c4, 4, g.img, img_ext, kDbgImage)
+                                         ? __ldg(reinterpret_cast<const uint32_t *>(rp + c4))
+                                         : 0u) &
+                                    keep;
                 s1 = __dp4a(wd, 0x01010101u, s1);
                 s2 = __dp4a(wd, wd, s2);
             }
@@ -506,13 +535,16 @@ __device__ __forceinline__ void window_rows(const Image &g, const Window &win, c
             for (int k = 0; k < kAW; k++) {
                 if (c4 + 128 * k < aend) {
                     const uint32_t wd =
-                        __ldg(reinterpret_cast<const uint32_t *>(rp + c4 + 128 * k)) & keepk[k];
+                        (BZ_DBG_IN(rp + c4 + 128 * k, 4, g.img, img_ext, kDbgImage)
+                             ? __ldg(reinterpret_cast<const uint32_t *>(rp + c4 + 128 * k))
+                             : 0u) &
+                        keepk[k];
                     s1 = __dp4a(wd, 0x01010101u, s1);
                     s2 = __dp4a(wd, wd, s2);
                 }
             }
         } else {
-            anchor_words<VEC>(rp, a4, ac0, aend, W, lane, s1, s2);
+            anchor_words<VEC>(rp, a4, ac0, aend, W, lane, s1, s2, g.img, img_ext);
         }
     };
 
@@ -599,8 +631,10 @@ __device__ __forceinline__ void window_rows(const Image &g, const Window &win, c
     uint32_t nd1 = 0, nd2 = 0;
     auto load_centre = [&](int64_t i) {
         const uint8_t *prow = g.img + i * g.pitch;
+        if (INTERIOR && !BZ_DBG_IN(prow + j0, 8, g.img, img_ext, kDbgImage))
+            return make_uint2(0u, 0u);
         return INTERIOR ? __ldg(reinterpret_cast<const uint2 *>(prow + j0))
-                        : ld8<VEC>(prow, j0, fastP, 0, 0x3210u, W);
+                        : ld8<VEC>(prow, j0, fastP, 0, 0x3210u, W, g.img, img_ext);
     };
     auto prefetch = [&](int64_t i) {
         const int64_t ra = i + u, rb = i - oo;
@@ -670,11 +704,14 @@ __device__ __forceinline__ void window_rows(const Image &g, const Window &win, c
                 if (j < W) {
                     const int64_t idx = i * W + j;
                     if (o.S1)
-                        o.S1[idx] = off1 + p1[m];
+                        if (BZ_DBG_IN(o.S1 + idx, 4, o.S1, (size_t)o.sums_n * 4, kDbgOutput))
+                            o.S1[idx] = off1 + p1[m];
                     if (o.S2)
-                        o.S2[idx] = (uint64_t)(off2 + p2[m]);
+                        if (BZ_DBG_IN(o.S2 + idx, 8, o.S2, (size_t)o.sums_n * 8, kDbgOutput))
+                            o.S2[idx] = (uint64_t)(off2 + p2[m]);
                     if (o.n)
-                        o.n[idx] = nrow * (INTERIOR ? (uint32_t)win.w : cols[m]);
+                        if (BZ_DBG_IN(o.n + idx, 4, o.n, (size_t)o.sums_n * 4, kDbgOutput))
+                            o.n[idx] = nrow * (INTERIOR ? (uint32_t)win.w : cols[m]);
                 }
             }
             continue;
@@ -792,7 +829,9 @@ __device__ __forceinline__ void window_rows(const Image &g, const Window &win, c
         if (MODE != MODE_REPORT && j0 < W) {
             if (!INTERIOR && j0 + 8 > W)
                 byte &= (1u << (W - j0)) - 1u;  // padding bits are 0
-            o.bits[(i - o.out_row0) * o.out_pitch + (j0 >> 3)] = (uint8_t)byte;
+            uint8_t *dst = o.bits + (i - o.out_row0) * o.out_pitch + (j0 >> 3);
+            if (BZ_DBG_IN(dst, 1, o.bits, o.bits_bytes, kDbgOutput))
+                *dst = (uint8_t)byte;
         }
     }
 
@@ -866,6 +905,7 @@ __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &w
     const int64_t H = g.H;
     const int64_t j0 = x0 + (int64_t)kColsPerLane * lane;
     const int l = win.l, r = win.r, oo = win.o, u = win.u;
+    [[maybe_unused]] const size_t img_ext = dbg_image_extent(g);
     const int64_t colA = j0 + r, colB = j0 - l;
     // load columns (32-bit: the caller guarantees W <= 2^30) and, for EDGE,
     // the byte shifts of the A, B and centre streams as three signed bytes
@@ -889,11 +929,11 @@ __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &w
     const unsigned selA = (unsigned)kA * 0x1111u + 0x3210u;
     const unsigned selB = (unsigned)kB * 0x1111u + 0x3210u;
     auto ldA = [&](const uint8_t *rp) {
-        const uint2 v = ld8_w3(rp + pA, kA, selA);
+        const uint2 v = ld8_w3(rp + pA, kA, selA, g.img, img_ext);
         return EDGE ? shift8(v, shift_of(0)) : v;
     };
     auto ldB = [&](const uint8_t *rp) {
-        const uint2 v = ld8_w3(rp + pB, kB, selB);
+        const uint2 v = ld8_w3(rp + pB, kB, selB, g.img, img_ext);
         return EDGE ? shift8(v, shift_of(1)) : v;
     };
     const float inv_w = __frcp_rn((float)win.w);
@@ -926,7 +966,10 @@ __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &w
     auto anchor_row = [&](const uint8_t *rp, uint32_t &s1, uint32_t &s2) {
 #pragma unroll
         for (int q = 0; q < AW; q++) {
-            const uint32_t wd = __ldg(reinterpret_cast<const uint32_t *>(rp + aoff[q])) & keep[q];
+            const uint32_t wd = (BZ_DBG_IN(rp + aoff[q], 4, g.img, img_ext, kDbgImage)
+                                     ? __ldg(reinterpret_cast<const uint32_t *>(rp + aoff[q]))
+                                     : 0u) &
+                                keep[q];
             s1 = __dp4a(wd, 0x01010101u, s1);
             s2 = __dp4a(wd, wd, s2);
         }
@@ -1208,16 +1251,18 @@ __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &w
             nfb += cnt;
             __syncwarp();  // the list is rewritten by the next row
         }
-        if (!EDGE)
-            o.bits[(i - o.out_row0) * o.out_pitch + (j0 >> 3)] = (uint8_t)byte;
-        else if (vmask)
-            o.bits[(i - o.out_row0) * o.out_pitch + (j0 >> 3)] = (uint8_t)(byte & vmask);
+        uint8_t *dst = o.bits + (i - o.out_row0) * o.out_pitch + (j0 >> 3);
+        if ((!EDGE || vmask) && BZ_DBG_IN(dst, 1, o.bits, o.bits_bytes, kDbgOutput))
+            *dst = (uint8_t)(EDGE ? (byte & vmask) : byte);
     };
 
     auto centre = [&](int64_t i) {
         if (EDGE)
-            return shift8(ld8_w3(g.img + i * g.pitch + pP, pP & 3, (unsigned)(pP & 3) * 0x1111u + 0x3210u),
+            return shift8(ld8_w3(g.img + i * g.pitch + pP, pP & 3, (unsigned)(pP & 3) * 0x1111u + 0x3210u,
+                                 g.img, img_ext),
                           shift_of(2));
+        if (!BZ_DBG_IN(g.img + i * g.pitch + j0, 8, g.img, img_ext, kDbgImage))
+            return make_uint2(0u, 0u);
         return __ldg(reinterpret_cast<const uint2 *>(g.img + i * g.pitch + j0));
     };
 

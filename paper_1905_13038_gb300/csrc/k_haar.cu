@@ -36,9 +36,10 @@ __device__ __forceinline__ void haar_load24(const Image &g, int64_t row, int64_t
     const int64_t a4 = xb >= 0 ? (xb & ~(int64_t)3) : -((-xb + 3) & ~(int64_t)3);
     if (VEC4 && a4 >= 0 && a4 + 28 <= g.W) {
         uint32_t wd[7];
+        const bool ok = BZ_DBG_IN(rp + a4, 28, g.img, dbg_image_extent(g), kDbgImage);
 #pragma unroll
         for (int q = 0; q < 7; q++)
-            wd[q] = __ldg(reinterpret_cast<const uint32_t *>(rp + a4) + q);
+            wd[q] = ok ? __ldg(reinterpret_cast<const uint32_t *>(rp + a4) + q) : 0u;
         const unsigned sh = 8u * (unsigned)(xb - a4);
 #pragma unroll
         for (int q = 0; q < 6; q++)
@@ -137,7 +138,8 @@ __global__ void __launch_bounds__(32 * kHaarWarps)
                 for (int k = 0; k < 5; k++)
                     if (k < hd.n_ct)
                         f += (uint32_t)hd.ct_c[k] * P[jj + hd.ct_b[k]];
-                out[i * g.W + x0 + jj] = (int32_t)f;
+                if (BZ_DBG_IN(out + i * g.W + x0 + jj, 4, out, (size_t)(g.H * g.W) * 4, kDbgOutput))
+                    out[i * g.W + x0 + jj] = (int32_t)f;
             }
         }
     }
@@ -158,5 +160,8 @@ cudaError_t launch_haar(const Image &g, const Window &win, const HaarDev &hd, in
         k_haar<false><<<(unsigned)blocks, 32 * kHaarWarps, 0, stream>>>(g, win, hd, out, tiles_x, tiles);
     return cudaGetLastError();
 }
+
+// Bounds-check status of this file's kernels (debug build; 1 otherwise).
+BZ_DEBUG_ACCESSOR(dbg_status_haar)
 
 }  // namespace bz

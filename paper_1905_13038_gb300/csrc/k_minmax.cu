@@ -45,7 +45,9 @@ __device__ __forceinline__ uint32_t mm_load(const Image &g, int64_t row, int64_t
 {
     const uint8_t *rp = g.img + row * g.pitch;
     if (VEC4 && xw >= 0 && xw + 4 <= g.W)
-        return __ldg(reinterpret_cast<const uint32_t *>(rp + xw));
+        return BZ_DBG_IN(rp + xw, 4, g.img, dbg_image_extent(g), kDbgImage)
+                   ? __ldg(reinterpret_cast<const uint32_t *>(rp + xw))
+                   : 0u;
     uint32_t v = 0;
 #pragma unroll
     for (int b = 0; b < 4; b++) {
@@ -239,7 +241,8 @@ __global__ void __launch_bounds__(kMmThreads)
                                              mm_bytes(rmax, 4 * p + delta + second));
 #pragma unroll
                 for (int e = 0; e < 4; e++) {
-                    if (j0 + e < g.W) {
+                    if (j0 + e < g.W && BZ_DBG_IN(mn_out + row * g.W + j0 + e, 1, mn_out, (size_t)(g.H * g.W), kDbgOutput) &&
+                        BZ_DBG_IN(mx_out + row * g.W + j0 + e, 1, mx_out, (size_t)(g.H * g.W), kDbgOutput)) {
                         mn_out[row * g.W + j0 + e] = (uint8_t)(lo >> (8 * e));
                         mx_out[row * g.W + j0 + e] = (uint8_t)(hi >> (8 * e));
                     }
@@ -271,7 +274,9 @@ __global__ void __launch_bounds__(kMmThreads)
                 }
                 if (j0 + 8 > g.W)
                     byte &= (1u << (g.W - j0)) - 1u;  // padding bits are 0
-                bits[row * out_pitch + (j0 >> 3)] = (uint8_t)byte;
+                if (BZ_DBG_IN(bits + row * out_pitch + (j0 >> 3), 1, bits,
+                              dbg_extent(g.H, out_pitch, (g.W + 7) / 8), kDbgOutput))
+                    bits[row * out_pitch + (j0 >> 3)] = (uint8_t)byte;
             }
         }
         __syncwarp();  // the scratch rows are rewritten by the next row
@@ -321,5 +326,8 @@ cudaError_t launch_minmax(const Image &g, const Window &win, int32_t contrast_li
     return vec4 ? launch_mm_t<MM_EXTREMA, true>(g, win, contrast_limit, mn, mx, bits, out_pitch, stream)
                 : launch_mm_t<MM_EXTREMA, false>(g, win, contrast_limit, mn, mx, bits, out_pitch, stream);
 }
+
+// Bounds-check status of this file's kernels (debug build; 1 otherwise).
+BZ_DEBUG_ACCESSOR(dbg_status_minmax)
 
 }  // namespace bz

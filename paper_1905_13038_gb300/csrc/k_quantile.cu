@@ -102,4 +102,7 @@ cudaError_t launch_quantile(const Image &g, const Window &win, int32_t q_num, in
     return run();
 }
 
+// Bounds-check status of this file's kernels (debug build; 1 otherwise).
+BZ_DEBUG_ACCESSOR(dbg_status_quantile)
+
 }  // namespace bz

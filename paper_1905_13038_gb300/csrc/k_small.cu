@@ -35,7 +35,10 @@ __global__ void __launch_bounds__(kSmThreads)
     for (int idx = tid; idx < nrows * ncols; idx += kSmThreads) {
         const int rr = idx / ncols, cc = idx - rr * ncols;
         const int64_t gy = ry0 + rr, gx = rx0 + cc;
-        R[rr][cc] = (gy >= 0 && gy < g.H && gx >= 0 && gx < g.W) ? g.img[gy * g.pitch + gx] : (uint8_t)0;
+        R[rr][cc] = (gy >= 0 && gy < g.H && gx >= 0 && gx < g.W &&
+                     BZ_DBG_IN(g.img + gy * g.pitch + gx, 1, g.img, dbg_image_extent(g), kDbgImage))
+                        ? g.img[gy * g.pitch + gx]
+                        : (uint8_t)0;
     }
     __syncthreads();
 
@@ -118,7 +121,9 @@ __global__ void __launch_bounds__(kSmThreads)
         }
         byte |= bit << m;
     }
-    o.bits[(gy - o.out_row0) * o.out_pitch + (gx0 >> 3)] = (uint8_t)byte;  // padding bits stay 0
+    uint8_t *dst = o.bits + (gy - o.out_row0) * o.out_pitch + (gx0 >> 3);
+    if (BZ_DBG_IN(dst, 1, o.bits, o.bits_bytes, kDbgOutput))
+        *dst = (uint8_t)byte;  // padding bits stay 0
     if (MODE == MODE_FP64 && nfb && o.fallbacks)
         atomicAdd(o.fallbacks, nfb);
 }
@@ -152,5 +157,8 @@ cudaError_t launch_small(int mode, const Image &g, const Window &win, const Thre
                           row0, row1);
     }
 }
+
+// Bounds-check status of this file's kernels (debug build; 1 otherwise).
+BZ_DEBUG_ACCESSOR(dbg_status_small)
 
 }  // namespace bz

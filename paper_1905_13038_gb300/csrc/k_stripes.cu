@@ -24,7 +24,9 @@ __device__ __forceinline__ uint32_t stripe_word(const Image &g, int64_t row, int
 {
     const uint8_t *rp = g.img + row * g.pitch;
     if (VEC4 && x + 4 <= g.W)
-        return __ldg(reinterpret_cast<const uint32_t *>(rp + x));
+        return BZ_DBG_IN(rp + x, 4, g.img, dbg_image_extent(g), kDbgImage)
+                   ? __ldg(reinterpret_cast<const uint32_t *>(rp + x))
+                   : 0u;
     uint32_t v = 0;
 #pragma unroll
     for (int b = 0; b < 4; b++)
@@ -59,7 +61,7 @@ __global__ void __launch_bounds__(kStripeThreads)
     auto store = [&](int64_t s) {
 #pragma unroll
         for (int b = 0; b < 4; b++)
-            if (x + b < g.W)
+            if (x + b < g.W && BZ_DBG_IN(out + s * g.W + x + b, 8, out, (size_t)S * g.W * 8, kDbgScratch))
                 out[s * g.W + x + b] = make_uint2(C[b], D[b]);
     };
     // window rows (y - o, y + u] of the first tile start y, eight loads at a time
@@ -194,7 +196,7 @@ __global__ void __launch_bounds__(kStripeThreads)
         stripe_rows<VEC4>(g, x, am, a1, C, D);
 #pragma unroll
     for (int b = 0; b < 4; b++)
-        if (x + b < g.W)
+        if (x + b < g.W && BZ_DBG_IN(QR + k * g.W + x + b, 16, QR, (size_t)K * g.W * 16, kDbgScratch))
             QR[k * g.W + x + b] = make_uint4(C[b], D[b], RC[b], RD[b]);
 }
 
@@ -216,7 +218,7 @@ __global__ void __launch_bounds__(kStripeThreads)
 #pragma unroll
         for (int j = 0; j < 16; j++) {
             v[j] = make_uint2(0u, 0u);
-            if (k + j < m) {
+            if (k + j < m && BZ_DBG_IN(QR + (s0 + k + j) * W + x, 16, QR, (size_t)(S + m + 1) * W * 16, kDbgScratch)) {
                 const uint4 q = __ldg(QR + (s0 + k + j) * W + x);
                 v[j] = make_uint2(q.x, q.y);
             }
@@ -232,10 +234,15 @@ __global__ void __launch_bounds__(kStripeThreads)
     for (int j = 0; j < G; j++) {
         const int64_t s = s0 + j;
         if (s < S) {
-            rr[j] = __ldg(QR + (s + m) * W + x);
+            const size_t qext = (size_t)(S + m + 1) * W * 16;
+            rr[j] = BZ_DBG_IN(QR + (s + m) * W + x, 16, QR, qext, kDbgScratch) ? __ldg(QR + (s + m) * W + x)
+                                                                              : make_uint4(0u, 0u, 0u, 0u);
             if (j > 0) {
-                vin[j] = __ldg(QR + (s + m - 1) * W + x);
-                vout[j] = __ldg(QR + (s - 1) * W + x);
+                vin[j] = BZ_DBG_IN(QR + (s + m - 1) * W + x, 16, QR, qext, kDbgScratch)
+                             ? __ldg(QR + (s + m - 1) * W + x)
+                             : make_uint4(0u, 0u, 0u, 0u);
+                vout[j] = BZ_DBG_IN(QR + (s - 1) * W + x, 16, QR, qext, kDbgScratch) ? __ldg(QR + (s - 1) * W + x)
+                                                                                  : make_uint4(0u, 0u, 0u, 0u);
             }
         }
     }
@@ -247,7 +254,8 @@ __global__ void __launch_bounds__(kStripeThreads)
                 c += vin[j].x - vout[j].x;
                 d += vin[j].y - vout[j].y;
             }
-            out[s * W + x] = make_uint2(c + rr[j].z, d + rr[j].w);
+            if (BZ_DBG_IN(out + s * W + x, 8, out, (size_t)S * W * 8, kDbgScratch))
+                out[s * W + x] = make_uint2(c + rr[j].z, d + rr[j].w);
         }
     }
 }
@@ -363,5 +371,8 @@ uint2 *launch_stripes(const Image &g, const Window &win, int64_t row0, int64_t t
     }
     return stripes;
 }
+
+// Bounds-check status of this file's kernels (debug build; 1 otherwise).
+BZ_DEBUG_ACCESSOR(dbg_status_stripes)
 
 }  // namespace bz

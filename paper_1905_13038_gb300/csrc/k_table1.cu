@@ -300,4 +300,7 @@ ThreshExt make_thresh_ext(int method, const double *prm, const GStats *gs, unsig
     return T;
 }
 
+// Bounds-check status of this file's kernels (debug build; 1 otherwise).
+BZ_DEBUG_ACCESSOR(dbg_status_table1)
+
 }  // namespace bz

@@ -210,4 +210,7 @@ cudaError_t launch_window(int mode, const Image &g, const Window &win, const Thr
     return launch_window_rows(mode, g, win, T, o, 0, g.H, stream);
 }
 
+// Bounds-check status of this file's kernels (debug build; 1 otherwise).
+BZ_DEBUG_ACCESSOR(dbg_status_window)
+
 }  // namespace bz
