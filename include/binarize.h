@@ -224,6 +224,29 @@ bz_status binarize_inplace(int32_t method, uint8_t *image, int64_t H, int64_t W,
  * admission under a memory budget. */
 int64_t bz_inplace_scratch_bytes(int64_t H, int64_t W, int32_t h, int64_t band_rows);
 
+/* The same result with the axes exchanged (Sec. 3.3: the roles of H and W
+ * swap, so the scratch follows H instead of W): the image is processed in
+ * bands of band_cols columns (0 picks the smallest allowed: 256 for
+ * w <= 450, else 512; otherwise a multiple of 256 at least that), each over
+ * all H rows.  Band k's packed bits go to a library scratch of one band
+ * (H * band_cols / 8 bytes, or H * ceil(W/8) if W is smaller;
+ * stream-ordered cudaMallocAsync) and are copied into bytes
+ * [c0/8, ceil(c1/8)) of every row right after the band: columns left of
+ * c1/8 are read by no later band because 7 c1 / 8 >= l - 1.  Arguments,
+ * layout and errors as binarize_inplace (BZ_EINVAL for a band_cols that is
+ * not allowed).  Each band is a narrow launch, so this is slower than
+ * binarize_inplace; it takes less scratch when H * band_cols / 8 is below
+ * 2 * max(o, 256) * ceil(W/8), which with the default bands means H < 2 W
+ * (w <= 450) or H < W (wider windows) for images taller than 256 rows. */
+bz_status binarize_inplace_cols(int32_t method, uint8_t *image, int64_t H,
+                                int64_t W, int64_t pitch, int32_t h, int32_t w,
+                                double k, double R, int64_t band_cols,
+                                bz_precision precision, void *stream);
+
+/* Scratch bytes binarize_inplace_cols takes (-1 if invalid). */
+int64_t bz_inplace_cols_scratch_bytes(int64_t H, int64_t W, int32_t w,
+                                      int64_t band_cols);
+
 /* ---------------------------------------------------------------------- */
 /* Local minimum and maximum (Sec. 3.4: Bernsen's midrange and the local  */
 /* contrast, kept recursively).  The window is Algorithm 1's, clipped to  */
@@ -406,8 +429,18 @@ bz_status binarize_batch_noalloc(const bz_job *jobs_host, int32_t n,
 /* ---------------------------------------------------------------------- */
 typedef struct bz_server bz_server;
 
-/* hbm_budget_bytes: upper bound on the summed image+output bytes of the
- * requests in flight on the device; max_slots: requests in flight at most. */
+/* hbm_budget_bytes: upper bound on the summed device bytes of the requests
+ * in flight (image + output for a job with a separate output; image + the
+ * in-place scratch for an in-place job, below); max_slots: requests in
+ * flight at most.
+ * In-place requests: a Sauvola or Niblack job with out == image and
+ * out_pitch == in_pitch is binarized over its image as binarize_inplace does
+ * (binarize_batch rejects such a job with BZ_EOVERLAP).  It is admitted with
+ * row bands (binarize_inplace, scratch bz_inplace_scratch_bytes(H, W, h, 0))
+ * when image + that scratch fits the budget left, else with column bands
+ * (binarize_inplace_cols, scratch bz_inplace_cols_scratch_bytes(H, W, w, 0))
+ * when those fit; otherwise it waits at the head of the queue.  Submission
+ * returns BZ_EBUDGET when image + the smaller scratch exceeds the budget. */
 bz_status bz_server_create(int64_t hbm_budget_bytes, int32_t max_slots,
                            bz_server **out);
 /* Queues a job; its buffers must stay valid until bz_server_wait returns

@@ -27,7 +27,7 @@ __all__ = [
     "WOLF", "FENG", "RAIS", "NICK", "PHANSALKAR", "binarize_wolf", "binarize_feng", "binarize_rais",
     "binarize_nick", "binarize_phansalkar", "global_stats", "binarize_precision_report_ext",
     "window_minmax", "binarize_bernsen", "haar_feature", "HAAR_FEATURES", "binarize_inplace",
-    "inplace_scratch_bytes", "binarize_host", "binarize_host_multi",
+    "inplace_scratch_bytes", "binarize_inplace_cols", "inplace_cols_scratch_bytes", "binarize_host", "binarize_host_multi",
     "autotune_window", "autotune_quantile", "autotune_batch", "tune_key", "tune_get", "tune_set",
     "tune_load", "tune_save", "tune_clear", "tune_window_plan", "bound_report", "use_library",
     "debug_status",
@@ -120,6 +120,8 @@ def _load():
         "binarize_host": ([i32, P, i64, i64, i64, i32, i32, f64, f64, P, i64, st, P], st),
         "binarize_host_multi": ([i32, P, i64, i64, i64, i32, P, P, f64, f64, P, i64, st, P], st),
         "bz_inplace_scratch_bytes": ([i64, i64, i32, i64], i64),
+        "binarize_inplace_cols": ([i32, P, i64, i64, i64, i32, i32, f64, f64, i64, st, P], st),
+        "bz_inplace_cols_scratch_bytes": ([i64, i64, i32, i64], i64),
         "binarize_precision_report_ext": ([i32, P, i64, i64, i64, i32, i32, P, P, P, P], st),
         "binarize_batch": ([ctypes.POINTER(_JobC), i32, st, P], st),
         "binarize_batch_noalloc": ([ctypes.POINTER(_JobC), i32, st, P], st),
@@ -396,6 +398,17 @@ def binarize_inplace(method: int, image, h: int, w: int, k: float = 0.5, R: floa
     return image
 
 
+def binarize_inplace_cols(method: int, image, h: int, w: int, k: float = 0.5, R: float = 128.0,
+                          band_cols: int = 0, precision="fp64", W: int | None = None, stream=None):
+    """binarize_inplace with the axes exchanged: column bands over all rows,
+    scratch proportional to H.  Returns the image tensor."""
+    ptr, H, W, pitch = _image(image, W)
+    _check("binarize_inplace_cols", _load().binarize_inplace_cols(method, ptr, H, W, pitch, h, w, k, R,
+                                                                  band_cols, _PREC[precision],
+                                                                  _stream(stream)))
+    return image
+
+
 def binarize_host(method: int, image, h: int, w: int, k: float = 0.5, R: float = 128.0, out=None,
                   precision="fp64", W: int | None = None, stream=None, sync: bool = True):
     """Sauvola / Niblack from host memory: `image` is a 2-D uint8 CPU tensor
@@ -454,6 +467,10 @@ def inplace_scratch_bytes(H: int, W: int, h: int, band_rows: int = 0) -> int:
     return int(_load().bz_inplace_scratch_bytes(H, W, h, band_rows))
 
 
+def inplace_cols_scratch_bytes(H: int, W: int, w: int, band_cols: int = 0) -> int:
+    return int(_load().bz_inplace_cols_scratch_bytes(H, W, w, band_cols))
+
+
 def last_fp64_fallbacks(stream=None) -> int:
     return int(_load().bz_last_fp64_fallbacks(_stream(stream)))
 
@@ -465,13 +482,19 @@ def kernels_per_call(H: int, W: int, h: int, w: int, precision="fp64") -> int:
 
 
 class Job:
-    """One image of a batch or a served request (tensors stay owned by the caller)."""
+    """One image of a batch or a served request (tensors stay owned by the caller).
+    inplace=True (served Sauvola / Niblack requests only): the packed result
+    replaces the first ceil(W/8) bytes of each image row (out is the image)."""
 
     def __init__(self, image, method: int, h: int, w: int, k: float = 0.5, R: float = 128.0,
-                 q_num: int = 1, q_den: int = 2, offset: int = 8, out=None, W: int | None = None):
+                 q_num: int = 1, q_den: int = 2, offset: int = 8, out=None, W: int | None = None,
+                 inplace: bool = False):
         ptr, H, W, pitch = _image(image, W)
         self.image = image
-        self.out, self.out_pitch = _out(out, H, W, image.device)
+        if inplace:
+            self.out, self.out_pitch = image, pitch
+        else:
+            self.out, self.out_pitch = _out(out, H, W, image.device)
         self.c = _JobC(ptr, self.out.data_ptr(), H, W, pitch, self.out_pitch, h, w, method, k, R,
                        q_num, q_den, offset)
 

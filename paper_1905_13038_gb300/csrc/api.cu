@@ -63,7 +63,7 @@ unsigned long long *fallback_counter(int device)
     return ptrs[device];
 }
 
-static bool finite_params(int method, double k, double R)
+bool finite_params(int method, double k, double R)
 {
     if (!isfinite(k) || fabs(k) > 1e6)
         return false;
@@ -514,6 +514,27 @@ bz_status haar_feature(const uint8_t *image, int64_t H, int64_t W, int64_t in_pi
                : BZ_ECUDA;
 }
 
+// Column bands (Sec. 3.3's exchanged axes applied to the in-place mode):
+// band k covers the output columns [c0, c1) of every row, c0 = k B.  Its
+// packed bits are written to a scratch of H rows x B/8 bytes and then copied
+// to bytes [c0/8, ceil(c1/8)) of each image row at once: later bands read
+// only columns >= c1 - l + 1 (their windows start there), and with
+// 7 c1 / 8 >= l - 1 every overwritten column c < c1 / 8 lies left of that.
+// The first band ends at c1 = B, so B = 256 serves l <= 225 and B = 512
+// every window up to 511; later bands end further right.  One scratch slot
+// suffices: the copy of band k is ordered after band k on the stream and
+// before band k + 1.
+static int64_t inplace_band_cols(int32_t w, int64_t band_cols)
+{
+    const int64_t l = (w + 1) / 2;
+    const int64_t bmin = (l - 1) * 8 <= 7 * 256 ? 256 : 512;
+    if (band_cols == 0)
+        return bmin;
+    if (band_cols < bmin || band_cols % 256 != 0)
+        return -1;
+    return band_cols;
+}
+
 bz_status binarize_inplace(int32_t method, uint8_t *image, int64_t H, int64_t W, int64_t pitch,
                            int32_t h, int32_t w, double k, double R, int64_t band_rows,
                            bz_precision precision, void *stream)
@@ -582,6 +603,61 @@ bz_status binarize_inplace(int32_t method, uint8_t *image, int64_t H, int64_t W,
                           scratch + (int64_t)(slot ^ 1) * band * cw, (size_t)cw, (size_t)cw,
                           (size_t)prev_rows, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
         st = BZ_ECUDA;
+    if (cudaFreeAsync(scratch, s) != cudaSuccess)
+        st = BZ_ECUDA;
+    return st;
+}
+
+bz_status binarize_inplace_cols(int32_t method, uint8_t *image, int64_t H, int64_t W, int64_t pitch,
+                                int32_t h, int32_t w, double k, double R, int64_t band_cols,
+                                bz_precision precision, void *stream)
+{
+    bz_status st = check_image(image, H, W, pitch, h, w);
+    if (st != BZ_OK)
+        return st;
+    if ((method != 0 && method != 1) || !finite_params(method, k, R))
+        return BZ_EINVAL;
+    int mode;
+    switch (precision) {
+    case BZ_FP64: mode = MODE_FP64; break;
+    case BZ_FP32: mode = MODE_FP32; break;
+    case BZ_FP64_DIRECT: mode = MODE_FP64_DIRECT; break;
+    default: return BZ_EINVAL;
+    }
+    const int64_t B = inplace_band_cols(w, band_cols);
+    if (B < 0)
+        return BZ_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const Window win = make_window(h, w);
+    const Image g{image, H, W, pitch};
+    const Thresh T = make_thresh(method, k, method == 0 ? R : 128.0);
+    unsigned long long *fb = nullptr;
+    if (mode == MODE_FP64) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess)
+            return BZ_ECUDA;
+        fb = fallback_counter(dev);
+        if (fb && cudaMemsetAsync(fb, 0, sizeof(unsigned long long), s) != cudaSuccess)
+            return BZ_ECUDA;
+    }
+    const int64_t slot_bytes = (B < W ? B : W + 7) / 8;  // bytes of a band's output row
+    uint8_t *scratch = nullptr;
+    if (cudaMallocAsync((void **)&scratch, (size_t)(H * slot_bytes), s) != cudaSuccess)
+        return BZ_ENOMEM;
+    for (int64_t c0 = 0; c0 < W && st == BZ_OK; c0 += B) {
+        const int64_t c1 = c0 + B < W ? c0 + B : W;
+        Outputs o{};
+        o.bits = scratch;
+        o.out_pitch = slot_bytes;
+        o.out_byte0 = c0 / 8;
+        o.bits_bytes = (size_t)(H * slot_bytes);
+        o.fallbacks = fb;
+        const int64_t nbytes = (c1 + 7) / 8 - c0 / 8;
+        if (launch_window_cols(mode, g, win, T, o, c0, c1, s) != cudaSuccess ||
+            cudaMemcpy2DAsync(image + c0 / 8, (size_t)pitch, scratch, (size_t)slot_bytes, (size_t)nbytes,
+                              (size_t)H, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+            st = BZ_ECUDA;
+    }
     if (cudaFreeAsync(scratch, s) != cudaSuccess)
         st = BZ_ECUDA;
     return st;
@@ -762,6 +838,16 @@ bz_status binarize_host_multi(int32_t method, const uint8_t *image_host, int64_t
 {
     return host_run(method, image_host, H, W, in_pitch, n, h, w, k, R, out_host, out_pitch, precision,
                     stream);
+}
+
+int64_t bz_inplace_cols_scratch_bytes(int64_t H, int64_t W, int32_t w, int64_t band_cols)
+{
+    if (H < 1 || W < 1 || w < 1 || w > 511)
+        return -1;
+    const int64_t B = inplace_band_cols(w, band_cols);
+    if (B < 0)
+        return -1;
+    return H * ((B < W ? B : W + 7) / 8);
 }
 
 int64_t bz_inplace_scratch_bytes(int64_t H, int64_t W, int32_t h, int64_t band_rows)

@@ -82,12 +82,17 @@ int plan_tile_schedule(int64_t H, int64_t W, int sms, bool pipe, bool stripes, i
 // Launches of the window path; mode is a bz::Mode.
 cudaError_t launch_window(int mode, const Image &g, const Window &win, const Thresh &T,
                           const Outputs &o, cudaStream_t stream);
-// The same over the output rows [row0, row1) only (windows still see the
-// whole image).
 // Kernels one launch_window_rows call enqueues (stripe pre-pass included).
 int window_kernel_count(int mode, const Image &g, const Window &win, int64_t row0, int64_t row1);
+// The same over the output rows [row0, row1) only (windows still see the
+// whole image).
 cudaError_t launch_window_rows(int mode, const Image &g, const Window &win, const Thresh &T,
                                const Outputs &o, int64_t row0, int64_t row1, cudaStream_t stream);
+// Binarize modes over the output columns [col0, col1) of every row only
+// (col0 a multiple of 256; windows still see the whole image); column j goes
+// to output byte j / 8 - o.out_byte0.
+cudaError_t launch_window_cols(int mode, const Image &g, const Window &win, const Thresh &T,
+                               const Outputs &o, int64_t col0, int64_t col1, cudaStream_t stream);
 
 // The other Table 1 methods (k_table1.cu).  prm = {k, R, alpha1, k1, k2,
 // gamma, p, q}.
@@ -202,5 +207,7 @@ bz_status check_image(const uint8_t *image, int64_t H, int64_t W, int64_t in_pit
 bz_status check_out(const uint8_t *image, int64_t H, int64_t W, int64_t in_pitch,
                     const uint8_t *out, int64_t out_pitch);
 bool ranges_overlap(const void *a, size_t na, const void *b, size_t nb);
+// Sauvola (method 0) / Niblack (1) parameters the library accepts.
+bool finite_params(int method, double k, double R);
 
 }  // namespace bz

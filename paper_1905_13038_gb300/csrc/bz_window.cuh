@@ -78,6 +78,7 @@ struct Outputs {
     uint8_t *bits;        // packed output (binarize modes)
     int64_t out_pitch;
     int64_t out_row0;     // image row i is output row i - out_row0
+    int64_t out_byte0;    // image column j goes to output byte j / 8 - out_byte0
     size_t bits_bytes;    // extent of `bits` (bounds checks of the debug build)
     int64_t sums_n;       // elements of S1, S2 and n (debug build)
     uint32_t *S1;         // MODE_SUMS (each may be null)
@@ -829,7 +830,7 @@ __device__ __forceinline__ void window_rows(const Image &g, const Window &win, c
         if (MODE != MODE_REPORT && j0 < W) {
             if (!INTERIOR && j0 + 8 > W)
                 byte &= (1u << (W - j0)) - 1u;  // padding bits are 0
-            uint8_t *dst = o.bits + (i - o.out_row0) * o.out_pitch + (j0 >> 3);
+            uint8_t *dst = o.bits + (i - o.out_row0) * o.out_pitch + ((j0 >> 3) - o.out_byte0);
             if (BZ_DBG_IN(dst, 1, o.bits, o.bits_bytes, kDbgOutput))
                 *dst = (uint8_t)byte;
         }
@@ -1251,7 +1252,7 @@ __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &w
             nfb += cnt;
             __syncwarp();  // the list is rewritten by the next row
         }
-        uint8_t *dst = o.bits + (i - o.out_row0) * o.out_pitch + (j0 >> 3);
+        uint8_t *dst = o.bits + (i - o.out_row0) * o.out_pitch + ((j0 >> 3) - o.out_byte0);
         if ((!EDGE || vmask) && BZ_DBG_IN(dst, 1, o.bits, o.bits_bytes, kDbgOutput))
             *dst = (uint8_t)(EDGE ? (byte & vmask) : byte);
     };
@@ -1299,6 +1300,7 @@ __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &w
 // schedule has n_edge = 0 and every column in the tile_h grid.
 struct TileSched {
     int64_t tiles_x, tile_h, edge_h, n_edge, tiles_total, row0, row1;
+    int64_t tx0;   // first tile column (column-band launches; else 0)
     int prefetch;  // tiles start with an L2 prefetch of their input
 };
 
@@ -1322,6 +1324,7 @@ __device__ __forceinline__ void sched_tile(const TileSched &S, int64_t W, const 
         if (stripes)
             st = stripes + ty * W;
     }
+    tx += S.tx0;
     if (y1 > S.row1)
         y1 = S.row1;
 }

@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(kSmThreads)
         }
         byte |= bit << m;
     }
-    uint8_t *dst = o.bits + (gy - o.out_row0) * o.out_pitch + (gx0 >> 3);
+    uint8_t *dst = o.bits + (gy - o.out_row0) * o.out_pitch + ((gx0 >> 3) - o.out_byte0);
     if (BZ_DBG_IN(dst, 1, o.bits, o.bits_bytes, kDbgOutput))
         *dst = (uint8_t)byte;  // padding bits stay 0
     if (MODE == MODE_FP64 && nfb && o.fallbacks)

@@ -82,17 +82,38 @@ Thresh make_thresh(int method, double k, double R)
     return T;
 }
 
+// Column band (ntx > 0): only the tile columns [tx0, tx0 + ntx) of rows
+// [row0, row1), on a uniform one-wave schedule of their own and without the
+// stripe pre-pass (it would cover every column).
+struct ColBand {
+    int64_t tx0 = 0, ntx = 0;
+};
+
 template <int MODE, bool VEC, typename S2T, bool WARMB>
 static cudaError_t launch_t(const Image &g, const Window &win, const Thresh &T, const Outputs &o,
-                            int64_t row0, int64_t row1, cudaStream_t stream)
+                            int64_t row0, int64_t row1, const ColBand &cb, cudaStream_t stream)
 {
     constexpr bool kCanPipe = VEC && (MODE == MODE_FP64 || MODE == MODE_FP32) && sizeof(S2T) == 4;
     const int aw = kCanPipe ? pipe_words(MODE, VEC, sizeof(S2T) == 4, g, win) : 0;
     const bool pipe = aw > 0;
-    const int64_t tile_h0 = window_tile_rows(row1 - row0, g.W, win.h, win.w);
-    const int64_t tiles_y0 = (row1 - row0 + tile_h0 - 1) / tile_h0;
-    uint2 *stripes = launch_stripes(g, win, row0, tile_h0, tiles_y0, stream);
-    const TileSched S = make_sched(g, win, row0, row1, pipe, stripes != nullptr);
+    uint2 *stripes = nullptr;
+    TileSched S;
+    if (cb.ntx > 0) {
+        S.tiles_x = cb.ntx;
+        S.tile_h = one_wave_tile_rows(row1 - row0, cb.ntx * kTileCols);
+        S.edge_h = S.tile_h;
+        S.n_edge = 0;
+        S.row0 = row0;
+        S.row1 = row1;
+        S.tx0 = cb.tx0;
+        S.tiles_total = cb.ntx * ((row1 - row0 + S.tile_h - 1) / S.tile_h);
+        S.prefetch = 1;
+    } else {
+        const int64_t tile_h0 = window_tile_rows(row1 - row0, g.W, win.h, win.w);
+        const int64_t tiles_y0 = (row1 - row0 + tile_h0 - 1) / tile_h0;
+        stripes = launch_stripes(g, win, row0, tile_h0, tiles_y0, stream);
+        S = make_sched(g, win, row0, row1, pipe, stripes != nullptr);
+    }
     int64_t blocks = (S.tiles_total + kWarpsPerBlock - 1) / kWarpsPerBlock;
     if (blocks > 2147483647LL)
         blocks = 2147483647LL;
@@ -114,9 +135,9 @@ static cudaError_t launch_t(const Image &g, const Window &win, const Thresh &T, 
 
 template <int MODE>
 static cudaError_t launch_m(const Image &g, const Window &win, const Thresh &T, const Outputs &o,
-                            int64_t row0, int64_t row1, cudaStream_t stream)
+                            int64_t row0, int64_t row1, cudaStream_t stream, const ColBand &cb = ColBand())
 {
-    if (small_path_applies(MODE, g, win, row0, row1))
+    if (cb.ntx == 0 && small_path_applies(MODE, g, win, row0, row1))
         return launch_small(MODE, g, win, T, o, row0, row1, stream);
     const bool vec = ((uintptr_t)g.img % 8 == 0) && (g.pitch % 8 == 0);
     const bool wide = (int64_t)win.h * win.w > 66051;  // S2 may reach 2^32
@@ -128,20 +149,21 @@ static cudaError_t launch_m(const Image &g, const Window &win, const Thresh &T, 
     }();
     const bool warmb = (MODE == MODE_FP64 || MODE == MODE_FP32) &&
                        (env_warmb >= 0 ? env_warmb != 0
-                                       : window_tile_rows(row1 - row0, g.W, win.h, win.w) <= 4);
+                                       : (cb.ntx > 0 ? one_wave_tile_rows(row1 - row0, cb.ntx * kTileCols)
+                                                     : window_tile_rows(row1 - row0, g.W, win.h, win.w)) <= 4);
     constexpr bool kB = (MODE == MODE_FP64 || MODE == MODE_FP32);
     if (warmb) {
         if (vec)
-            return wide ? launch_t<MODE, true, unsigned long long, kB>(g, win, T, o, row0, row1, stream)
-                        : launch_t<MODE, true, uint32_t, kB>(g, win, T, o, row0, row1, stream);
-        return wide ? launch_t<MODE, false, unsigned long long, kB>(g, win, T, o, row0, row1, stream)
-                    : launch_t<MODE, false, uint32_t, kB>(g, win, T, o, row0, row1, stream);
+            return wide ? launch_t<MODE, true, unsigned long long, kB>(g, win, T, o, row0, row1, cb, stream)
+                        : launch_t<MODE, true, uint32_t, kB>(g, win, T, o, row0, row1, cb, stream);
+        return wide ? launch_t<MODE, false, unsigned long long, kB>(g, win, T, o, row0, row1, cb, stream)
+                    : launch_t<MODE, false, uint32_t, kB>(g, win, T, o, row0, row1, cb, stream);
     }
     if (vec)
-        return wide ? launch_t<MODE, true, unsigned long long, false>(g, win, T, o, row0, row1, stream)
-                    : launch_t<MODE, true, uint32_t, false>(g, win, T, o, row0, row1, stream);
-    return wide ? launch_t<MODE, false, unsigned long long, false>(g, win, T, o, row0, row1, stream)
-                : launch_t<MODE, false, uint32_t, false>(g, win, T, o, row0, row1, stream);
+        return wide ? launch_t<MODE, true, unsigned long long, false>(g, win, T, o, row0, row1, cb, stream)
+                    : launch_t<MODE, true, uint32_t, false>(g, win, T, o, row0, row1, cb, stream);
+    return wide ? launch_t<MODE, false, unsigned long long, false>(g, win, T, o, row0, row1, cb, stream)
+                : launch_t<MODE, false, uint32_t, false>(g, win, T, o, row0, row1, cb, stream);
 }
 
 // Binarize launches on the window kernel read their tile height, edge-tile
@@ -189,6 +211,22 @@ cudaError_t launch_window_rows(int mode, const Image &g, const Window &win, cons
     }
     TuneScope scope(have ? &c : nullptr);
     return run();
+}
+
+cudaError_t launch_window_cols(int mode, const Image &g, const Window &win, const Thresh &T,
+                               const Outputs &o, int64_t col0, int64_t col1, cudaStream_t stream)
+{
+    if (col0 < 0 || col0 % kTileCols != 0 || col1 <= col0 || col1 > g.W)
+        return cudaErrorInvalidValue;
+    ColBand cb;
+    cb.tx0 = col0 / kTileCols;
+    cb.ntx = (col1 - col0 + kTileCols - 1) / kTileCols;
+    switch (mode) {
+    case MODE_FP64: return launch_m<MODE_FP64>(g, win, T, o, 0, g.H, stream, cb);
+    case MODE_FP32: return launch_m<MODE_FP32>(g, win, T, o, 0, g.H, stream, cb);
+    case MODE_FP64_DIRECT: return launch_m<MODE_FP64_DIRECT>(g, win, T, o, 0, g.H, stream, cb);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 int window_kernel_count(int mode, const Image &g, const Window &win, int64_t row0, int64_t row1)

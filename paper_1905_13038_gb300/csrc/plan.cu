@@ -114,6 +114,7 @@ static TileSched plan_sched(int64_t row0, int64_t row1, int64_t W, int64_t tile_
     S.n_edge = 0;
     S.row0 = row0;
     S.row1 = row1;
+    S.tx0 = 0;
     S.prefetch = 0;
     const int64_t uniform = S.tiles_x * ((rows + tile_h - 1) / tile_h);
     S.tiles_total = uniform;

@@ -15,6 +15,13 @@
 // sets a flag and signals), and completion is confirmed with the lane's CUDA
 // event; bz_server_wait blocks on a condition variable.
 //
+// In-place requests (out == image, out_pitch == in_pitch; Sauvola and
+// Niblack) hold the image plus the scratch of binarize_inplace: row bands
+// when image + row scratch fits the budget at admission, else column bands
+// (binarize_inplace_cols, the exchanged axes of Sec. 3.3) when their smaller
+// scratch fits; a request that fits neither waits at the head of the queue.
+// They run on the lane's stream after the lane's batch.
+//
 // Host-side fault injection for tests (environment variable BZ_FAULT):
 //   "launch"     every batch launch reports BZ_ECUDA without touching the GPU
 //   "slow:<ms>"  completions are reported <ms> milliseconds late
@@ -34,13 +41,17 @@ namespace bz {
 
 enum ReqState { RS_QUEUED, RS_RUNNING, RS_DONE };
 
+enum Orient { OR_NONE, OR_ROWS, OR_COLS };  // in-place orientation (OR_NONE: separate output)
+
 struct Request {
     bz_job job;
     bz_precision prec;
-    int64_t bytes;
+    int64_t bytes;       // bytes held on the device while running
     ReqState state;
     bz_status result;
     bool cancelled;
+    bool inplace;
+    int64_t bytes_rows, bytes_cols;  // in-place: image + scratch of each orientation (-1: not offered)
 };
 
 struct ExecLane {
@@ -52,7 +63,9 @@ struct ExecLane {
     bool failed = false;
     bool signalled = false;  // the stream's callback ran
     std::vector<uint64_t> tickets;
-    std::vector<bz_job> jobs;
+    std::vector<bz_job> jobs;      // separate-output jobs: one batch
+    std::vector<bz_job> ip_jobs;   // in-place jobs, run one by one after it
+    std::vector<int> ip_orient;
     bz_precision prec = BZ_FP64;
     std::chrono::steady_clock::time_point ready_at;
     bz_server *srv = nullptr;
@@ -84,6 +97,19 @@ namespace bz {
 static int64_t job_bytes(const bz_job &j)
 {
     return j.H * j.in_pitch + j.H * j.out_pitch;
+}
+
+static bool is_inplace(const bz_job &j)
+{
+    return j.out == j.image && j.out_pitch == j.in_pitch;
+}
+
+static bz_status run_inplace(const bz_job &j, int orient, bz_precision prec, cudaStream_t s)
+{
+    const int32_t m = j.method == BZ_SAUVOLA ? 0 : 1;
+    if (orient == OR_ROWS)
+        return binarize_inplace(m, j.out, j.H, j.W, j.in_pitch, j.h, j.w, j.k, j.R, 0, prec, s);
+    return binarize_inplace_cols(m, j.out, j.H, j.W, j.in_pitch, j.h, j.w, j.k, j.R, 0, prec, s);
 }
 
 // Completes the lanes whose batch finished; called with srv->mu held.
@@ -120,6 +146,8 @@ static void reap(bz_server *srv)
         }
         L->tickets.clear();
         L->jobs.clear();
+        L->ip_jobs.clear();
+        L->ip_orient.clear();
         L->busy = false;
         L->launched = false;
         L->failed = false;
@@ -147,18 +175,36 @@ static std::vector<ExecLane *> pick(bz_server *srv)
                 ++it;
                 continue;
             }
-            if (srv->inflight >= srv->max_slots || srv->inflight_bytes + r.bytes > srv->budget)
-                break;  // head-of-line: keep FIFO order under the budget
+            if (srv->inflight >= srv->max_slots)
+                break;
+            const int64_t room = srv->budget - srv->inflight_bytes;
+            int orient = OR_NONE;
+            if (r.inplace) {
+                if (r.bytes_rows >= 0 && r.bytes_rows <= room)
+                    orient = OR_ROWS;  // faster: whole-width launches
+                else if (r.bytes_cols >= 0 && r.bytes_cols <= room)
+                    orient = OR_COLS;  // less scratch
+                else
+                    break;  // head-of-line: keep FIFO order under the budget
+                r.bytes = orient == OR_ROWS ? r.bytes_rows : r.bytes_cols;
+            } else if (r.bytes > room) {
+                break;
+            }
             prec = r.prec;
             have_prec = true;
             r.state = RS_RUNNING;
             srv->inflight_bytes += r.bytes;
             srv->inflight += 1;
-            L->jobs.push_back(r.job);
+            if (r.inplace) {
+                L->ip_jobs.push_back(r.job);
+                L->ip_orient.push_back(orient);
+            } else {
+                L->jobs.push_back(r.job);
+            }
             L->tickets.push_back(*it);
             it = srv->queue.erase(it);
         }
-        if (L->jobs.empty())
+        if (L->tickets.empty())
             break;
         L->prec = prec;
         L->busy = true;
@@ -195,10 +241,13 @@ static void scheduler(bz_server *srv)
             lk.unlock();
             for (ExecLane *L : ready) {
                 bool ok = !srv->fault_launch;
-                if (ok)
+                if (ok && !L->jobs.empty())
                     ok = run_batch(L->slot, L->jobs.data(), (int32_t)L->jobs.size(), L->prec, L->stream) ==
-                             BZ_OK &&
-                         cudaEventRecord(L->ev, L->stream) == cudaSuccess &&
+                         BZ_OK;
+                for (size_t q = 0; ok && q < L->ip_jobs.size(); q++)
+                    ok = run_inplace(L->ip_jobs[q], L->ip_orient[q], L->prec, L->stream) == BZ_OK;
+                if (ok)
+                    ok = cudaEventRecord(L->ev, L->stream) == cudaSuccess &&
                          cudaLaunchHostFunc(L->stream, lane_done, L) == cudaSuccess;
                 lk.lock();
                 if (ok)
@@ -274,17 +323,39 @@ bz_status bz_server_submit(bz_server *srv, const bz_job *job, bz_precision preci
         return BZ_EINVAL;
     if (precision != BZ_FP64 && precision != BZ_FP32 && precision != BZ_FP64_DIRECT)
         return BZ_EINVAL;
-    const bz_status st = validate_job(*job);
-    if (st != BZ_OK)
-        return st;
-    const int64_t bytes = job_bytes(*job);
-    if (bytes > srv->budget)
-        return BZ_EBUDGET;
+    Request r{*job, precision, 0, RS_QUEUED, BZ_OK, false, is_inplace(*job), -1, -1};
+    if (r.inplace) {
+        const bz_job &j = *job;
+        bz_status st = check_image(j.image, j.H, j.W, j.in_pitch, j.h, j.w);
+        if (st != BZ_OK)
+            return st;
+        if ((j.method != BZ_SAUVOLA && j.method != BZ_NIBLACK) ||
+            !finite_params(j.method == BZ_SAUVOLA ? 0 : 1, j.k, j.R))
+            return BZ_EINVAL;
+        const int64_t img = j.H * j.in_pitch;
+        const int64_t sr = bz_inplace_scratch_bytes(j.H, j.W, j.h, 0);
+        const int64_t sc = bz_inplace_cols_scratch_bytes(j.H, j.W, j.w, 0);
+        r.bytes_rows = sr < 0 ? -1 : img + sr;
+        r.bytes_cols = sc < 0 ? -1 : img + sc;
+        const int64_t least = r.bytes_cols >= 0 && r.bytes_cols < r.bytes_rows ? r.bytes_cols : r.bytes_rows;
+        if (least < 0)
+            return BZ_EINVAL;
+        if (least > srv->budget)
+            return BZ_EBUDGET;
+        r.bytes = least;
+    } else {
+        const bz_status st = validate_job(*job);
+        if (st != BZ_OK)
+            return st;
+        r.bytes = job_bytes(*job);
+        if (r.bytes > srv->budget)
+            return BZ_EBUDGET;
+    }
     std::lock_guard<std::mutex> lk(srv->mu);
     if (srv->stop)
         return BZ_EINVAL;
     const uint64_t t = srv->next_ticket++;
-    srv->reqs[t] = Request{*job, precision, bytes, RS_QUEUED, BZ_OK, false};
+    srv->reqs[t] = r;
     srv->queue.push_back(t);
     *ticket = t;
     srv->cv_work.notify_one();

@@ -30,6 +30,7 @@ def test_header_declares_expected_entry_points():
               "binarize_rais", "binarize_nick", "binarize_phansalkar", "global_stats",
               "binarize_precision_report_ext", "binarize_batch_noalloc", "window_minmax",
               "binarize_bernsen", "haar_feature", "binarize_inplace", "bz_inplace_scratch_bytes",
+              "binarize_inplace_cols", "bz_inplace_cols_scratch_bytes",
               "binarize_host", "bz_kernels_per_call", "binarize_host_multi", "bz_tile_schedule"]:
         assert n in names, n
 
