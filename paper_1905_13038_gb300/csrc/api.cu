@@ -42,25 +42,59 @@ bz_status check_out(const uint8_t *image, int64_t H, int64_t W, int64_t in_pitch
     return BZ_OK;
 }
 
-// One 8-byte FP64-fallback counter per device, allocated on first use.
-unsigned long long *fallback_counter(int device)
+// Three 8-byte FP64-fallback counters per device (allocated zeroed on first
+// use): slots 0 and 1 for single-image calls in turn, slot 2 for batches.
+struct FbState {
+    unsigned long long *c = nullptr;
+    int tog = 0, last = 0;
+};
+static std::mutex g_fb_mu;
+static FbState g_fb[64];
+
+static unsigned long long *fb_counters(int device)
 {
-    static std::mutex mu;
-    static unsigned long long *ptrs[64] = {nullptr};
     if (device < 0 || device >= 64)
         return nullptr;
-    std::lock_guard<std::mutex> lk(mu);
-    if (!ptrs[device]) {
+    if (!g_fb[device].c) {
         void *p = nullptr;
-        if (cudaMalloc(&p, sizeof(unsigned long long)) != cudaSuccess)
+        if (cudaMalloc(&p, 3 * sizeof(unsigned long long)) != cudaSuccess)
             return nullptr;
-        if (cudaMemset(p, 0, sizeof(unsigned long long)) != cudaSuccess) {
+        if (cudaMemset(p, 0, 3 * sizeof(unsigned long long)) != cudaSuccess) {
             cudaFree(p);
             return nullptr;
         }
-        ptrs[device] = (unsigned long long *)p;
+        g_fb[device].c = (unsigned long long *)p;
     }
-    return ptrs[device];
+    return g_fb[device].c;
+}
+
+FbSlot fallback_slot(int device)
+{
+    std::lock_guard<std::mutex> lk(g_fb_mu);
+    FbSlot f;
+    unsigned long long *c = fb_counters(device);
+    if (!c)
+        return f;
+    FbState &st = g_fb[device];
+    st.tog ^= 1;
+    st.last = st.tog;
+    f.use = c + st.tog;
+    f.clear = c + (st.tog ^ 1);
+    return f;
+}
+
+unsigned long long *fallback_counter(int device)
+{
+    std::lock_guard<std::mutex> lk(g_fb_mu);
+    unsigned long long *c = fb_counters(device);
+    return c ? c + 2 : nullptr;
+}
+
+void fallback_mark_batch(int device)
+{
+    std::lock_guard<std::mutex> lk(g_fb_mu);
+    if (device >= 0 && device < 64)
+        g_fb[device].last = 2;
 }
 
 bool finite_params(int method, double k, double R)
@@ -104,11 +138,9 @@ static bz_status run_threshold(int method, const uint8_t *image, int64_t H, int6
         int dev = 0;
         if (cudaGetDevice(&dev) != cudaSuccess)
             return BZ_ECUDA;
-        o.fallbacks = fallback_counter(dev);
-        if (o.fallbacks &&
-            cudaMemsetAsync(o.fallbacks, 0, sizeof(unsigned long long), (cudaStream_t)stream) !=
-                cudaSuccess)
-            return BZ_ECUDA;
+        const FbSlot fb = fallback_slot(dev);
+        o.fallbacks = fb.use;
+        o.fallbacks_clear = fb.clear;
     }
     return launch_window(mode, g, win, T, o, (cudaStream_t)stream) == cudaSuccess ? BZ_OK
                                                                                   : BZ_ECUDA;
@@ -191,11 +223,9 @@ static bz_status run_ext_binarize(int method, const uint8_t *image, int64_t H, i
         int dev = 0;
         if (cudaGetDevice(&dev) != cudaSuccess)
             return BZ_ECUDA;
-        o.fallbacks = fallback_counter(dev);
-        if (o.fallbacks &&
-            cudaMemsetAsync(o.fallbacks, 0, sizeof(unsigned long long), (cudaStream_t)stream) !=
-                cudaSuccess)
-            return BZ_ECUDA;
+        const FbSlot fb = fallback_slot(dev);
+        o.fallbacks = fb.use;
+        o.fallbacks_clear = fb.clear;
     }
     return run_ext(method, image, H, W, in_pitch, h, w, prm, mode, o, stream);
 }
@@ -559,14 +589,14 @@ bz_status binarize_inplace(int32_t method, uint8_t *image, int64_t H, int64_t W,
     const int64_t cw = (W + 7) / 8;
     Image g{image, H, W, pitch};
     Thresh T = make_thresh(method, k, method == 0 ? R : 128.0);
-    unsigned long long *fb = nullptr;
+    unsigned long long *fb = nullptr, *fbc = nullptr;
     if (mode == MODE_FP64) {
         int dev = 0;
         if (cudaGetDevice(&dev) != cudaSuccess)
             return BZ_ECUDA;
-        fb = fallback_counter(dev);
-        if (fb && cudaMemsetAsync(fb, 0, sizeof(unsigned long long), s) != cudaSuccess)
-            return BZ_ECUDA;
+        const FbSlot f = fallback_slot(dev);
+        fb = f.use;
+        fbc = f.clear;
     }
     const int64_t band = B < H ? B : H;
     uint8_t *scratch = nullptr;
@@ -587,6 +617,7 @@ bz_status binarize_inplace(int32_t method, uint8_t *image, int64_t H, int64_t W,
         o.out_row0 = r0;
         o.bits_bytes = (size_t)band * cw;
         o.fallbacks = fb;
+        o.fallbacks_clear = fbc;
         if (launch_window_rows(mode, g, win, T, o, r0, r1, s) != cudaSuccess)
             st = BZ_ECUDA;
         else if (prev_row0 >= 0 &&
@@ -631,14 +662,14 @@ bz_status binarize_inplace_cols(int32_t method, uint8_t *image, int64_t H, int64
     const Window win = make_window(h, w);
     const Image g{image, H, W, pitch};
     const Thresh T = make_thresh(method, k, method == 0 ? R : 128.0);
-    unsigned long long *fb = nullptr;
+    unsigned long long *fb = nullptr, *fbc = nullptr;
     if (mode == MODE_FP64) {
         int dev = 0;
         if (cudaGetDevice(&dev) != cudaSuccess)
             return BZ_ECUDA;
-        fb = fallback_counter(dev);
-        if (fb && cudaMemsetAsync(fb, 0, sizeof(unsigned long long), s) != cudaSuccess)
-            return BZ_ECUDA;
+        const FbSlot f = fallback_slot(dev);
+        fb = f.use;
+        fbc = f.clear;
     }
     const int64_t slot_bytes = (B < W ? B : W + 7) / 8;  // bytes of a band's output row
     uint8_t *scratch = nullptr;
@@ -652,6 +683,7 @@ bz_status binarize_inplace_cols(int32_t method, uint8_t *image, int64_t H, int64
         o.out_byte0 = c0 / 8;
         o.bits_bytes = (size_t)(H * slot_bytes);
         o.fallbacks = fb;
+        o.fallbacks_clear = fbc;
         const int64_t nbytes = (c1 + 7) / 8 - c0 / 8;
         if (launch_window_cols(mode, g, win, T, o, c0, c1, s) != cudaSuccess ||
             cudaMemcpy2DAsync(image + c0 / 8, (size_t)pitch, scratch, (size_t)slot_bytes, (size_t)nbytes,
@@ -773,7 +805,8 @@ static bz_status host_run(int32_t method, const uint8_t *image_host, int64_t H, 
     // no wider than needed) keeps the copy a single contiguous transfer
     const int64_t dpitch = (in_pitch % 16 == 0 && in_pitch - W < 16) ? in_pitch : (W + 15) & ~(int64_t)15;
     const size_t plane = (size_t)(H * cw);
-    unsigned long long *fb = mode == MODE_FP64 ? fallback_counter(dev) : nullptr;
+    const FbSlot fbs = mode == MODE_FP64 ? fallback_slot(dev) : FbSlot();
+    unsigned long long *fb = fbs.use;
     std::lock_guard<std::mutex> lk(hs->mu);
     HostSlot &sl = hs->slot[hs->next];
     hs->next ^= 1;
@@ -789,14 +822,14 @@ static bz_status host_run(int32_t method, const uint8_t *image_host, int64_t H, 
     ok = ok && cudaEventRecord(sl.up, hs->up) == cudaSuccess;
     // compute once the upload is done and the slot's previous outputs are home
     ok = ok && cudaStreamWaitEvent(hs->comp, sl.up, 0) == cudaSuccess &&
-         cudaStreamWaitEvent(hs->comp, sl.down, 0) == cudaSuccess &&
-         (!fb || cudaMemsetAsync(fb, 0, sizeof(unsigned long long), hs->comp) == cudaSuccess);
+         cudaStreamWaitEvent(hs->comp, sl.down, 0) == cudaSuccess;
     for (int q = 0; ok && q < n; q++) {
         Outputs o{};
         o.bits = sl.out + plane * (size_t)q;
         o.out_pitch = cw;
         o.bits_bytes = plane;
         o.fallbacks = fb;
+        o.fallbacks_clear = fbs.clear;
         ok = launch_window(mode, Image{sl.img, H, W, dpitch}, make_window(hv[q], wv[q]), T, o, hs->comp) ==
              cudaSuccess;
     }
@@ -1007,9 +1040,14 @@ int64_t bz_last_fp64_fallbacks(void *stream)
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess)
         return -1;
-    unsigned long long *p = fallback_counter(dev);
+    unsigned long long *p = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_fb_mu);
+        if (dev >= 0 && dev < 64 && g_fb[dev].c)
+            p = g_fb[dev].c + g_fb[dev].last;
+    }
     if (!p)
-        return -1;
+        return 0;  // no BZ_FP64 call on this device yet
     unsigned long long v = 0;
     if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess)
         return -1;

@@ -456,6 +456,8 @@ bz_status run_batch(BatchSlot &s, const bz_job *jobs, int32_t n, bz_precision pr
     auto launch = [&]() -> bz_status {
         if (cudaGraphLaunch(s.exec[gi], stream) != cudaSuccess)
             return BZ_ECUDA;
+        if (mode == 0)
+            fallback_mark_batch(s.device);
         if (cudaEventRecord(s.done, stream) != cudaSuccess)
             return BZ_ECUDA;
         return BZ_OK;

@@ -198,8 +198,16 @@ int dbg_status_haar(unsigned *status, unsigned long long *addr, bool reset);
 int dbg_status_batch(unsigned *status, unsigned long long *addr, bool reset);
 int dbg_status_table1(unsigned *status, unsigned long long *addr, bool reset);
 
-// Library-owned per-device scratch: FP64-fallback counter.
+// Library-owned per-device FP64-fallback counters: two that single-image
+// calls alternate between (fallback_slot: this call's counter and the one
+// its launches zero), and one for batches (fallback_counter, reset inside the
+// batch graph).  bz_last_fp64_fallbacks reads the latest call's.
+struct FbSlot {
+    unsigned long long *use = nullptr, *clear = nullptr;
+};
+FbSlot fallback_slot(int device);
 unsigned long long *fallback_counter(int device);
+void fallback_mark_batch(int device);
 
 // Validation helpers (return BZ_OK or an error status).
 bz_status check_image(const uint8_t *image, int64_t H, int64_t W, int64_t in_pitch, int32_t h,

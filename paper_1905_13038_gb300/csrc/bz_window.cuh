@@ -62,6 +62,7 @@ struct Thresh {
     float aalpha, abeta, agamma;
     float eps;      // relative part of the certified bound
     float delta64;  // absolute bound on |t64 - t_exact|
+    float bnd_c;    // interior pipelined form: bound on |d32 - (t64 - I)| over all pixels
     double k, R;    // canonical FP64 parameters
     int method;     // a bz::Method other than METHOD_QUANTILE
 };
@@ -85,10 +86,22 @@ struct Outputs {
     uint64_t *S2;
     uint32_t *n;
     unsigned long long *fallbacks;  // optional FP64-fallback counter
+    unsigned long long *fallbacks_clear;  // the other call slot's counter, zeroed by the launch (after its wait)
     unsigned long long *flips;      // MODE_REPORT (each may be null)
     unsigned long long *maxdt_bits; // MODE_REPORT (double bits, >= 0)
     unsigned long long *maxratio_bits;  // MODE_REPORT: max |t32 - t64| / certified bound (double bits)
+    int32_t report_path;  // MODE_REPORT: the path a BZ_FP32 launch takes (kReport*), whose form the flips follow
 };
+
+__device__ __forceinline__ void fallbacks_clear(const Outputs &o)
+{
+    if (o.fallbacks_clear && blockIdx.x == 0 && threadIdx.x == 0)
+        *o.fallbacks_clear = 0ull;
+}
+
+// Paths of an FP32 binarize launch; MODE_REPORT counts flips with the FP32
+// form of the path the same image and window take in BZ_FP32.
+constexpr int32_t kReportGeneric = 0, kReportPipe = 1, kReportSmall = 2;
 
 template <typename T>
 __device__ __forceinline__ T warp_incl_scan(T v, int lane)
@@ -113,6 +126,13 @@ __device__ __forceinline__ void pdl_begin()
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     asm volatile("griddepcontrol.wait;" ::: "memory");
 }
+
+// Single-image calls alternate between two FP64-fallback counters: a call
+// counts into one and its launches zero the other for the next call, after
+// their griddepcontrol.wait (the next call's kernels add only after their
+// own wait, i.e. after this launch has finished), so that no memset sits
+// between two launches and the next kernel can start early.
+__device__ __forceinline__ void fallbacks_clear(const struct Outputs &o);
 
 // ------------------------------------------------------------ threshold --
 // Canonical FP64 threshold: IEEE binary64, round to nearest, no contraction,
@@ -782,8 +802,30 @@ __device__ __forceinline__ void window_rows(const Image &g, const Window &win, c
                         const double t64 = canonical_t(T.method, S1, S2, n, T.k, T.R);
                         const uint32_t I = (uint32_t)byte_at(P, m);
                         const uint32_t b64 = ((double)I <= t64) ? 0u : 1u;
-                        nflip += (b64 != bit);
-                        const double dt = fabs((double)t - t64);
+                        // the FP32 value of the path this pixel takes in
+                        // BZ_FP32 (t here is the generic form's)
+                        double t32 = (double)t;
+                        if (o.report_path == kReportSmall) {
+                            const float inv1 = __frcp_rn((float)n);
+                            const float mu1 = __uint2float_rn(S1) * inv1;
+                            const float s1 = sqrt_approx((v_float<S2T>(n, S2, S1) * inv1) * inv1);
+                            t32 = (double)fmaf(fmaf(T.beta, mu1, T.gamma), s1, T.alpha * mu1);
+                        } else if (o.report_path == kReportPipe && INTERIOR) {
+                            const float an = T.alpha * inv_n, gn = T.gamma * inv_n, bn2 = (T.beta * inv_n) * inv_n;
+                            const float S1f = __uint2float_rn(S1);
+                            const float sq = sqrt_approx(__ull2float_rn((uint64_t)n * S2 - (uint64_t)S1 * (uint64_t)S1));
+                            const float If = pixel_f(P, m);
+                            const float dP = simple ? fmaf(S1f, fmaf(bn2, sq, an), -If)
+                                                    : fmaf(fmaf(bn2, S1f, gn), sq, fmaf(S1f, an, -If));
+                            t32 = (double)dP + (double)I;
+                        } else if (o.report_path == kReportPipe || (INTERIOR && simple)) {
+                            const float sB = sqrt_approx(v_float<S2T>(n, S2, S1) * (inv_n * inv_n));
+                            t32 = simple ? (double)(mu * fmaf(T.beta, sB, T.alpha))
+                                         : (double)fmaf(fmaf(T.beta, mu, T.gamma), sB, T.alpha * mu);
+                        }
+                        const uint32_t b32 = t32 < (double)I ? 1u : 0u;
+                        nflip += (b64 != b32);
+                        const double dt = fabs(t32 - t64);
                         maxdt = dt > maxdt ? dt : maxdt;
                         // the certified bound of every evaluation form the FP64
                         // mode uses: general t with var = (V / n) / n (this
@@ -800,7 +842,17 @@ __device__ __forceinline__ void window_rows(const Image &g, const Window &win, c
                             const float tS = mu * fmaf(T.beta, sB, T.alpha);
                             rS = fabs((double)tS - t64) / (double)fmaf(T.eps, tS, T.delta64);
                         }
-                        maxratio = fmax(maxratio, fmax(rA, fmax(rB, rS)));
+                        // the interior pipelined form: d = t - I from row
+                        // constants, against the launch constant T.bnd_c
+                        const float an = T.alpha * inv_n, gn = T.gamma * inv_n, bn2 = (T.beta * inv_n) * inv_n;
+                        const float S1f = __uint2float_rn(S1);
+                        const float sqN = sqrt_approx(
+                            __ull2float_rn((uint64_t)n * S2 - (uint64_t)S1 * (uint64_t)S1));
+                        const float If = pixel_f(P, m);
+                        const float dN = simple ? fmaf(S1f, fmaf(bn2, sqN, an), -If)
+                                                : fmaf(fmaf(bn2, S1f, gn), sqN, fmaf(S1f, an, -If));
+                        const double rN = fabs((double)dN - (t64 - (double)I)) / (double)T.bnd_c;
+                        maxratio = fmax(maxratio, fmax(fmax(rA, rN), fmax(rB, rS)));
                     }
                 }
             }
@@ -1144,6 +1196,18 @@ __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &w
             }
         };
         auto count = [&](int m, uint32_t &n_m, float &inv_m) { count_of(lane, m, n_m, inv_m); };
+        // interior tiles: t / n per unit of S1 from row constants, so that a
+        // pixel costs d = t - I = S1 (alpha/n + beta/n^2 sqrt(V)) - I (Sauvola
+        // with alpha, beta >= 0), else alpha S1/n + (beta S1/n^2 + gamma/n)
+        // sqrt(V) - I; certified when |d| > T.bnd_c
+        const float an = T.alpha * inv_nw, gn = T.gamma * inv_nw, bn2 = (T.beta * inv_nw) * inv_nw;
+        auto eval_n = [&](bool SIMPLE, int m, uint32_t S1, uint32_t S2) -> float {
+            const float S1f = __uint2float_rn(S1);
+            const uint64_t V = (uint64_t)nw * S2 - (uint64_t)S1 * S1;
+            const float sq = sqrt_approx(__ull2float_rn(V));
+            const float If = pixel_f(P, m);
+            return SIMPLE ? fmaf(S1f, fmaf(bn2, sq, an), -If) : fmaf(fmaf(bn2, S1f, gn), sq, fmaf(S1f, an, -If));
+        };
         // FP32 threshold of pixel m: returns its bit and sets `slack` =
         // |d| - E, certified when > 0 (columns past the row count as
         // certified).  SIMPLE: Sauvola with alpha, beta >= 0 (mag = t).
@@ -1173,7 +1237,25 @@ __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &w
         // hot path: the bits and the row's smallest slack only
         uint32_t byte = 0;
         float minslack = 1.0f;
-        if (simple) {
+        if (!EDGE && !EXTM) {
+            float mind = 3.0e38f;
+            if (simple) {
+#pragma unroll
+                for (int m = kColsPerLane - 1; m >= 0; m--) {
+                    const float d = eval_n(true, m, S1v[m], S2v[m]);
+                    byte = (byte << 1) | (__float_as_uint(d) >> 31);
+                    mind = fminf(mind, fabsf(d));
+                }
+            } else {
+#pragma unroll
+                for (int m = kColsPerLane - 1; m >= 0; m--) {
+                    const float d = eval_n(false, m, S1v[m], S2v[m]);
+                    byte = (byte << 1) | (__float_as_uint(d) >> 31);
+                    mind = fminf(mind, fabsf(d));
+                }
+            }
+            minslack = mind - T.bnd_c;
+        } else if (simple) {
 #pragma unroll
             for (int m = 0; m < kColsPerLane; m++) {
                 float sk;
@@ -1204,7 +1286,14 @@ __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &w
                     const uint32_t S1 = vs[((m >> 2) * 32 + lane) * 4 + (m & 3)];
                     const uint32_t S2 = vs[((2 + (m >> 2)) * 32 + lane) * 4 + (m & 3)];
                     float sk;
-                    const uint32_t b = eval(simple, m, S1, S2, sk);
+                    uint32_t b;
+                    if (!EDGE && !EXTM) {
+                        const float d = eval_n(simple, m, S1, S2);
+                        b = __float_as_uint(d) >> 31;
+                        sk = fabsf(d) - T.bnd_c;
+                    } else {
+                        b = eval(simple, m, S1, S2, sk);
+                    }
                     if (sk > 0.0f)
                         byte |= b << m;
                     else

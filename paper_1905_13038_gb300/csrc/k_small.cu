@@ -24,6 +24,7 @@ __global__ void __launch_bounds__(kSmThreads)
     __shared__ uint8_t R[kSmRows][kSmCols];
     __shared__ uint32_t P1[kSmTH][kSmCols], P2[kSmTH][kSmCols];
     pdl_begin();
+    fallbacks_clear(o);
     const int tid = threadIdx.x;
     const int64_t x0 = (int64_t)(blockIdx.x % tiles_x) * kSmTW;
     const int64_t y0 = row0 + (int64_t)(blockIdx.x / tiles_x) * kSmTH;

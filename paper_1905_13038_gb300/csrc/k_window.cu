@@ -35,6 +35,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock, kBlocksPerSM)
         tile_prefetch_l2(g, win, tx * kTileCols, y0, y1, lane);
     }
     asm volatile("griddepcontrol.wait;" ::: "memory");
+    fallbacks_clear(o);
     for (int64_t t = wid; t < S.tiles_total; t += stride) {
         int64_t tx, y0, y1;
         const uint2 *st;
@@ -79,6 +80,13 @@ Thresh make_thresh(int method, double k, double R)
     T.agamma = fabsf(T.gamma);
     T.eps = kEpsF32;
     T.delta64 = (float)(mag * 1.01) + 1e-30f;
+    // Interior pipelined form (row constants alpha/n, gamma/n, beta/n^2 from
+    // 1/n with 3 roundings; V and S1 rounded once; sqrt.approx within
+    // 2^-22; three fused operations): |d32 - (t - I)| <= 17 u (M + 255),
+    // u = 2^-24, M = |alpha| 255 + (|beta| 255 + |gamma|) 127.5 the largest
+    // magnitude of the terms of t.  32 u (M + 256) leaves a margin.
+    const double M = fabs(alpha) * 255.0 + (fabs(beta) * 255.0 + fabs(gamma)) * 127.5;
+    T.bnd_c = (float)(32.0 / 16777216.0 * (M + 256.0)) + T.delta64;
     return T;
 }
 
@@ -141,6 +149,16 @@ static cudaError_t launch_m(const Image &g, const Window &win, const Thresh &T, 
         return launch_small(MODE, g, win, T, o, row0, row1, stream);
     const bool vec = ((uintptr_t)g.img % 8 == 0) && (g.pitch % 8 == 0);
     const bool wide = (int64_t)win.h * win.w > 66051;  // S2 may reach 2^32
+    if (MODE == MODE_REPORT) {  // the FP32 form the report follows
+        Outputs o2 = o;
+        o2.report_path = small_path_applies(MODE_FP32, g, win, row0, row1) ? kReportSmall
+                         : (vec && !wide && pipe_words(MODE_FP32, true, true, g, win) > 0) ? kReportPipe
+                                                                                       : kReportGeneric;
+        return vec ? (wide ? launch_t<MODE, true, unsigned long long, false>(g, win, T, o2, row0, row1, cb, stream)
+                           : launch_t<MODE, true, uint32_t, false>(g, win, T, o2, row0, row1, cb, stream))
+                   : (wide ? launch_t<MODE, false, unsigned long long, false>(g, win, T, o2, row0, row1, cb, stream)
+                           : launch_t<MODE, false, uint32_t, false>(g, win, T, o2, row0, row1, cb, stream));
+    }
     // short tiles (a small image): the launch is latency-bound, so the
     // warm-up issues its loads in batches (binarize modes only)
     static const int env_warmb = [] {  // BZ_WARMB=0/1 forces it (tuning)
