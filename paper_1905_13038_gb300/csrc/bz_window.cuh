@@ -1201,10 +1201,13 @@ __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &w
         // with alpha, beta >= 0), else alpha S1/n + (beta S1/n^2 + gamma/n)
         // sqrt(V) - I; certified when |d| > T.bnd_c
         const float an = T.alpha * inv_nw, gn = T.gamma * inv_nw, bn2 = (T.beta * inv_nw) * inv_nw;
-        auto eval_n = [&](bool SIMPLE, int m, uint32_t S1, uint32_t S2) -> float {
+        // V = n S2 - S1^2 < n^2 255^2 / 4: below 2^32 when n <= 513, so
+        // that wrapping 32-bit products give it exactly (V32)
+        auto eval_n = [&](bool SIMPLE, bool V32, int m, uint32_t S1, uint32_t S2) -> float {
             const float S1f = __uint2float_rn(S1);
-            const uint64_t V = (uint64_t)nw * S2 - (uint64_t)S1 * S1;
-            const float sq = sqrt_approx(__ull2float_rn(V));
+            const float Vf = V32 ? __uint2float_rn(nw * S2 - S1 * S1)
+                                 : __ull2float_rn((uint64_t)nw * S2 - (uint64_t)S1 * S1);
+            const float sq = sqrt_approx(Vf);
             const float If = pixel_f(P, m);
             return SIMPLE ? fmaf(S1f, fmaf(bn2, sq, an), -If) : fmaf(fmaf(bn2, S1f, gn), sq, fmaf(S1f, an, -If));
         };
@@ -1238,23 +1241,28 @@ __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &w
         uint32_t byte = 0;
         float minslack = 1.0f;
         if (!EDGE && !EXTM) {
-            float mind = 3.0e38f;
+            bool unc = false;  // some |d| <= T.bnd_c
+            auto row8 = [&](bool SIMPLE, bool V32) {
+#pragma unroll
+                for (int m = kColsPerLane - 1; m >= 0; m--) {
+                    const float d = eval_n(SIMPLE, V32, m, S1v[m], S2v[m]);
+                    byte = (byte << 1) | (__float_as_uint(d) >> 31);
+                    unc |= fabsf(d) <= T.bnd_c;
+                }
+            };
+            const bool v32 = nw <= 513u;
             if (simple) {
-#pragma unroll
-                for (int m = kColsPerLane - 1; m >= 0; m--) {
-                    const float d = eval_n(true, m, S1v[m], S2v[m]);
-                    byte = (byte << 1) | (__float_as_uint(d) >> 31);
-                    mind = fminf(mind, fabsf(d));
-                }
+                if (v32)
+                    row8(true, true);
+                else
+                    row8(true, false);
             } else {
-#pragma unroll
-                for (int m = kColsPerLane - 1; m >= 0; m--) {
-                    const float d = eval_n(false, m, S1v[m], S2v[m]);
-                    byte = (byte << 1) | (__float_as_uint(d) >> 31);
-                    mind = fminf(mind, fabsf(d));
-                }
+                if (v32)
+                    row8(false, true);
+                else
+                    row8(false, false);
             }
-            minslack = mind - T.bnd_c;
+            minslack = unc ? -1.0f : 1.0f;
         } else if (simple) {
 #pragma unroll
             for (int m = 0; m < kColsPerLane; m++) {
@@ -1288,7 +1296,7 @@ __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &w
                     float sk;
                     uint32_t b;
                     if (!EDGE && !EXTM) {
-                        const float d = eval_n(simple, m, S1, S2);
+                        const float d = eval_n(simple, false, m, S1, S2);
                         b = __float_as_uint(d) >> 31;
                         sk = fabsf(d) - T.bnd_c;
                     } else {
