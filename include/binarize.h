@@ -37,6 +37,10 @@
  * out has H rows of out_pitch >= ceil(W/8) bytes.  Only the first ceil(W/8)
  * bytes of each output row are written.  Image and output
  * must not overlap (Sec. 3.2 assumptions): overlap -> BZ_EOVERLAP.
+ * The library's own stream-ordered scratch (stripe sums of tall windows,
+ * global statistics, in-place bands) comes from a memory pool per device
+ * that keeps up to 256 MB between calls ("the library's pool"), or, on a
+ * capturing stream, from the graph's own allocations.
  *
  * Errors.  Argument errors are reported synchronously and nothing is
  * launched.  Launch failures return BZ_ECUDA.  Work is asynchronous with
@@ -210,7 +214,7 @@ bz_status binarize_host_multi(int32_t method, const uint8_t *image_host,
  * (same bit layout as binarize_sauvola); the bytes after them keep their
  * gray levels.  The image is processed in bands of band_rows rows (0 picks
  * max(o, 256)); band k goes to a library scratch of two bands
- * (2 * band_rows * ceil(W/8) bytes, stream-ordered cudaMallocAsync) and is
+ * (2 * band_rows * ceil(W/8) bytes, stream-ordered, from the library's pool) and is
  * copied into place after band k+1 has read its rows, which needs
  * band_rows >= o = floor((h+1)/2) (else BZ_EINVAL).  Results equal
  * binarize_sauvola / binarize_niblack with a separate output.  Smaller
@@ -230,7 +234,7 @@ int64_t bz_inplace_scratch_bytes(int64_t H, int64_t W, int32_t h, int64_t band_r
  * w <= 450, else 512; otherwise a multiple of 256 at least that), each over
  * all H rows.  Band k's packed bits go to a library scratch of one band
  * (H * band_cols / 8 bytes, or H * ceil(W/8) if W is smaller;
- * stream-ordered cudaMallocAsync) and are copied into bytes
+ * stream-ordered, from the library's pool) and are copied into bytes
  * [c0/8, ceil(c1/8)) of every row right after the band: columns left of
  * c1/8 are read by no later band because 7 c1 / 8 >= l - 1.  Arguments,
  * layout and errors as binarize_inplace (BZ_EINVAL for a band_cols that is
@@ -300,7 +304,7 @@ bz_status haar_feature(const uint8_t *image, int64_t H, int64_t W,
 /* window statistics).  L, M and S are the global minimum, mean and        */
 /* population standard deviation of the image (Table 1 notations), found   */
 /* by one reduction pass on `stream` before the window pass.  The library  */
-/* takes 24 bytes of stream-ordered scratch (cudaMallocAsync) per call and */
+/* takes 24 bytes of stream-ordered scratch (library pool) per call and   */
 /* frees it on the stream: allocation failure -> BZ_ENOMEM.                */
 /*                                                                        */
 /* Canonical FP64 thresholds (every operation binary64 round-to-nearest,   */

@@ -183,7 +183,7 @@ static bz_status run_ext(int method, const uint8_t *image, int64_t H, int64_t W,
     cudaStream_t s = (cudaStream_t)stream;
     Image g{image, H, W, in_pitch};
     GStats *gs = nullptr;
-    if (cudaMallocAsync((void **)&gs, sizeof(GStats), s) != cudaSuccess)
+    if (scratch_alloc((void **)&gs, sizeof(GStats), s) != cudaSuccess)
         return BZ_ENOMEM;
     bz_status st = BZ_OK;
     const unsigned long long N = (unsigned long long)H * (unsigned long long)W;
@@ -191,7 +191,7 @@ static bz_status run_ext(int method, const uint8_t *image, int64_t H, int64_t W,
     if (launch_global_stats(g, gs, s) != cudaSuccess ||
         launch_window_ext(mode, g, make_window(h, w), T, o, s) != cudaSuccess)
         st = BZ_ECUDA;
-    if (cudaFreeAsync(gs, s) != cudaSuccess)
+    if (scratch_free(gs, s) != cudaSuccess)
         st = BZ_ECUDA;
     return st;
 }
@@ -408,7 +408,7 @@ bz_status global_stats(const uint8_t *image, int64_t H, int64_t W, int64_t in_pi
         return BZ_EOVERLAP;
     cudaStream_t s = (cudaStream_t)stream;
     GStats *gs = nullptr;
-    if (cudaMallocAsync((void **)&gs, sizeof(GStats), s) != cudaSuccess)
+    if (scratch_alloc((void **)&gs, sizeof(GStats), s) != cudaSuccess)
         return BZ_ENOMEM;
     Image g{image, H, W, in_pitch};
     bz_status st = BZ_OK;
@@ -416,7 +416,7 @@ bz_status global_stats(const uint8_t *image, int64_t H, int64_t W, int64_t in_pi
         launch_global_finalize(gs, (unsigned long long)H * (unsigned long long)W, stats_dev,
                                sums_dev, s) != cudaSuccess)
         st = BZ_ECUDA;
-    if (cudaFreeAsync(gs, s) != cudaSuccess)
+    if (scratch_free(gs, s) != cudaSuccess)
         st = BZ_ECUDA;
     return st;
 }
@@ -600,7 +600,7 @@ bz_status binarize_inplace(int32_t method, uint8_t *image, int64_t H, int64_t W,
     }
     const int64_t band = B < H ? B : H;
     uint8_t *scratch = nullptr;
-    if (cudaMallocAsync((void **)&scratch, (size_t)(2 * band * cw), s) != cudaSuccess)
+    if (scratch_alloc((void **)&scratch, (size_t)(2 * band * cw), s) != cudaSuccess)
         return BZ_ENOMEM;
     // Band k is binarized into scratch slot k % 2 while the image still holds
     // every gray level its windows need; band k-1 is copied into place only
@@ -634,7 +634,7 @@ bz_status binarize_inplace(int32_t method, uint8_t *image, int64_t H, int64_t W,
                           scratch + (int64_t)(slot ^ 1) * band * cw, (size_t)cw, (size_t)cw,
                           (size_t)prev_rows, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
         st = BZ_ECUDA;
-    if (cudaFreeAsync(scratch, s) != cudaSuccess)
+    if (scratch_free(scratch, s) != cudaSuccess)
         st = BZ_ECUDA;
     return st;
 }
@@ -673,7 +673,7 @@ bz_status binarize_inplace_cols(int32_t method, uint8_t *image, int64_t H, int64
     }
     const int64_t slot_bytes = (B < W ? B : W + 7) / 8;  // bytes of a band's output row
     uint8_t *scratch = nullptr;
-    if (cudaMallocAsync((void **)&scratch, (size_t)(H * slot_bytes), s) != cudaSuccess)
+    if (scratch_alloc((void **)&scratch, (size_t)(H * slot_bytes), s) != cudaSuccess)
         return BZ_ENOMEM;
     for (int64_t c0 = 0; c0 < W && st == BZ_OK; c0 += B) {
         const int64_t c1 = c0 + B < W ? c0 + B : W;
@@ -690,7 +690,7 @@ bz_status binarize_inplace_cols(int32_t method, uint8_t *image, int64_t H, int64
                               (size_t)H, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
             st = BZ_ECUDA;
     }
-    if (cudaFreeAsync(scratch, s) != cudaSuccess)
+    if (scratch_free(scratch, s) != cudaSuccess)
         st = BZ_ECUDA;
     return st;
 }

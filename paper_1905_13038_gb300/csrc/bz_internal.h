@@ -173,14 +173,14 @@ std::string batch_tune_key(int mode);
 // current TuneScope; the fastest configuration goes to `best`.
 bool tune_window(int mode, const Image &g, const Window &win, int64_t row0, int64_t row1, bool pipe,
                  const std::function<cudaError_t()> &launch, cudaStream_t stream, TuneCfg &best);
-bool tune_quantile(const Image &g, const std::function<cudaError_t()> &launch, cudaStream_t stream,
-                   TuneCfg &best);
+bool tune_quantile(const Image &g, const Window &win, const std::function<cudaError_t()> &launch,
+                   cudaStream_t stream, TuneCfg &best);
 
 // Planner pieces the tuner reads (plan.cu, k_stripes.cu, k_quantile.cu).
 int64_t one_wave_tile_rows(int64_t rows, int64_t W);
 double default_edge_fraction(bool pipe);
 bool stripes_allowed(int h);
-int64_t quantile_band_rows(int64_t H, int64_t W);
+int64_t quantile_band_rows(int64_t H, int64_t W, int h);
 // Window-kernel plan of an H x W image on a GPU with `sms` SMs under the
 // current TuneScope / environment: tile_h, edge_h, n_edge, tiles_total,
 // stripes (0/1), resident warps into out[0..5].
@@ -197,6 +197,14 @@ int dbg_status_minmax(unsigned *status, unsigned long long *addr, bool reset);
 int dbg_status_haar(unsigned *status, unsigned long long *addr, bool reset);
 int dbg_status_batch(unsigned *status, unsigned long long *addr, bool reset);
 int dbg_status_table1(unsigned *status, unsigned long long *addr, bool reset);
+
+// Stream-ordered scratch (stripe sums, global statistics, in-place bands)
+// from a library-owned memory pool per device that keeps up to 256 MB
+// between calls: the device's default pool returns its memory at every
+// synchronisation, so a call after a synchronisation would map it again.
+// Under stream capture the allocation is the graph's own (cudaMallocAsync).
+cudaError_t scratch_alloc(void **p, size_t bytes, cudaStream_t s);
+cudaError_t scratch_free(void *p, cudaStream_t s);
 
 // Library-owned per-device FP64-fallback counters: two that single-image
 // calls alternate between (fallback_slot: this call's counter and the one

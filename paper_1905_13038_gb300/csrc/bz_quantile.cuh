@@ -31,7 +31,9 @@
 // Updates are shared-memory atomics without a return value.  The own
 // histograms hold 16-bit counts, two lanes per 32-bit word (a lane's counts
 // stay below 7 h <= 3577, so neither half borrows from or carries into the
-// other).  Image columns outside [0, W) are staged as the value 256, a bin
+// other), or for windows of at most 36 rows 8-bit counts, four lanes per
+// word (7 h <= 252), which shrinks a warp's arrays from 27.5 to 19.2 KB and
+// lets 11 instead of 8 warps share an SM.  Image columns outside [0, W) are staged as the value 256, a bin
 // that is counted but never queried, so no update needs a mask.  Each row's
 // bytes are loaded one row step ahead into registers, so the global-memory
 // latency overlaps the previous row's work.
@@ -48,8 +50,11 @@ constexpr int kQSentinel = 543;    // a slot that always holds the value 256
 constexpr int kQBins = 260;        // gray values 0..255, 256 = outside the image, read-ahead pad
 constexpr int kQQuarters = 68;     // totals per 4 gray values: 0..63, 64 = outside the image
 
-struct QWarpSmem {
-    uint32_t own[kQBins][16];          // own-part counts: lane L in word L >> 1, half L & 1
+// OWNW = 16: 16-bit own counts (lane L in word L >> 1, half L & 1);
+// OWNW = 8: 8-bit own counts (lane L in word L >> 2, byte L & 3).
+template <int OWNW>
+struct QWarpSmemT {
+    uint32_t own[kQBins][OWNW];        // own-part counts
     uint32_t core[kQBins];             // core-part histogram
     uint32_t grp[4][kQBins];           // group-part histogram of each 8-lane group
     uint32_t coreQ[4][kQQuarters];     // core totals per 4 gray values, partial per updating group
@@ -59,6 +64,14 @@ struct QWarpSmem {
     uint16_t rin[kQSpanCap];           // staged entering row
     uint16_t rout[kQSpanCap];          // staged leaving row
 };
+typedef QWarpSmemT<16> QWarpSmem;
+typedef QWarpSmemT<8> QWarpSmem8;
+
+// 8-bit own counts hold a lane's own part (at most 7 columns x h rows)
+__host__ __device__ constexpr bool quantile_own8(int h)
+{
+    return 7 * h <= 255;
+}
 
 // Pixels of a shared part below gray value Q: the prefix up to Q's 4-value
 // step plus at most 3 bins.
@@ -82,13 +95,16 @@ __host__ __device__ constexpr int quantile_prefetch(int w)
 
 // One warp (lane = threadIdx.x & 31) computes output columns [x0, x0 + 32)
 // x rows [y0, y1).  out (packed bits) and Qout (dense quantile plane, W per
-// row) may each be null.  NPF = quantile_prefetch(w); CORE = (w >= 32).
-template <int NPF, bool CORE>
+// row) may each be null.  NPF = quantile_prefetch(w); CORE = (w >= 32);
+// OWN8 = quantile_own8(h).
+template <int NPF, bool CORE, bool OWN8 = false>
 __device__ __forceinline__ void quantile_warp_tile(const Image &g, const Window &win, int32_t q_num,
                                                    int32_t q_den, int32_t offset, uint8_t *out,
                                                    int64_t out_pitch, uint8_t *Qout, int64_t x0,
-                                                   int64_t y0, int64_t y1, QWarpSmem &S, int lane)
+                                                   int64_t y0, int64_t y1, QWarpSmemT<OWN8 ? 8 : 16> &S,
+                                                   int lane)
 {
+    constexpr int kOW = OWN8 ? 8 : 16;  // words per own-count row
     const int w = win.w, h = win.h;
     const int G = lane >> 3, pos = lane & 7;
     const int64_t span0 = x0 - win.l + 1;  // image column of staged slot 0
@@ -102,7 +118,7 @@ __device__ __forceinline__ void quantile_warp_tile(const Image &g, const Window 
     {
         const uint4 z = make_uint4(0u, 0u, 0u, 0u);
         uint4 *p = reinterpret_cast<uint4 *>(&S);
-        constexpr int n16 = (int)(offsetof(QWarpSmem, rin) / 16);
+        constexpr int n16 = (int)(offsetof(QWarpSmemT<kOW>, rin) / 16);
         for (int k = lane; k < n16; k += 32)
             p[k] = z;
         if (lane == 0) {
@@ -133,10 +149,11 @@ __device__ __forceinline__ void quantile_warp_tile(const Image &g, const Window 
     const int ncore = CORE ? w - 31 : 0;
     const int core_rounds = (ncore + 31) >> 5;
     const bool has_grp = ngrp > 0;
-    const uint32_t dplus = (lane & 1) ? 0x10000u : 1u;  // own-count step of this lane
+    // own-count step of this lane, its field of an own word, its column
+    const uint32_t dplus = OWN8 ? 1u << (8 * (lane & 3)) : ((lane & 1) ? 0x10000u : 1u);
     const uint32_t dminus = 0u - dplus;
-    const uint32_t osel = (lane & 1) ? 0x4432u : 0x4410u;  // this lane's half of an own word
-    uint32_t *const ownl = &S.own[0][lane >> 1];           // this lane's own-count column
+    const uint32_t osel = OWN8 ? 0x4440u | (unsigned)(lane & 3) : ((lane & 1) ? 0x4432u : 0x4410u);
+    uint32_t *const ownl = &S.own[0][OWN8 ? lane >> 2 : lane >> 1];
 
     // prefetched slots lane + 32 t, t < NPF: stored if inside the span,
     // loaded if also inside the image (else the value 256)
@@ -223,7 +240,7 @@ __device__ __forceinline__ void quantile_warp_tile(const Image &g, const Window 
 #pragma unroll
             for (int e = 0; e < 7; e++) {
                 const int a = S.rin[ok[e]];
-                atomicAdd(&ownl[a * 16], dplus);
+                atomicAdd(&ownl[a * kOW], dplus);
                 nb += (uint32_t)(a - Q) >> 31;  // a < Q
             }
             bown += nb;
@@ -249,7 +266,7 @@ __device__ __forceinline__ void quantile_warp_tile(const Image &g, const Window 
 #pragma unroll
             for (int e = 0; e < 7; e++) {
                 const int b = S.rout[ok[e]];
-                atomicAdd(&ownl[b * 16], dminus);
+                atomicAdd(&ownl[b * kOW], dminus);
                 nb += (uint32_t)(b - Q) >> 31;  // b < Q
             }
             bown -= nb;
@@ -328,7 +345,7 @@ __device__ __forceinline__ void quantile_warp_tile(const Image &g, const Window 
             for (int k = 0; k < 4; k++) {
                 int v = v0 + k;
                 v = v < 0 ? 0 : v;
-                o[k] = __byte_perm(ownl[v * 16], 0u, osel);
+                o[k] = __byte_perm(ownl[v * kOW], 0u, osel);
                 c[k] = o[k];
                 if (has_grp)
                     c[k] += S.grp[G][v];

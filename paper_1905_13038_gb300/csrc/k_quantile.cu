@@ -6,39 +6,39 @@
 
 namespace bz {
 
-template <int NPF, bool CORE>
+template <int NPF, bool CORE, bool OWN8>
 __global__ void __launch_bounds__(32)
     k_quantile(Image g, Window win, int32_t q_num, int32_t q_den, int32_t offset, uint8_t *out,
                int64_t out_pitch, uint8_t *Qout, int64_t tiles_x, int64_t tile_h)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    QWarpSmem &S = *reinterpret_cast<QWarpSmem *>(smem);
+    QWarpSmemT<OWN8 ? 8 : 16> &S = *reinterpret_cast<QWarpSmemT<OWN8 ? 8 : 16> *>(smem);
     const int64_t tx = blockIdx.x % tiles_x, ty = blockIdx.x / tiles_x;
     const int64_t x0 = tx * kQCols, y0 = ty * tile_h;
     const int64_t y1 = y0 + tile_h < g.H ? y0 + tile_h : g.H;
-    quantile_warp_tile<NPF, CORE>(g, win, q_num, q_den, offset, out, out_pitch, Qout, x0, y0, y1, S,
-                       threadIdx.x & 31);
+    quantile_warp_tile<NPF, CORE, OWN8>(g, win, q_num, q_den, offset, out, out_pitch, Qout, x0, y0, y1, S,
+                                         threadIdx.x & 31);
 }
 
-template <int NPF, bool CORE>
+template <int NPF, bool CORE, bool OWN8>
 static cudaError_t launch_q(const Image &g, const Window &win, int32_t q_num, int32_t q_den,
                             int32_t offset, uint8_t *out, int64_t out_pitch, uint8_t *Q,
                             cudaStream_t stream)
 {
-    const auto kernel = k_quantile<NPF, CORE>;
-    const size_t smem = sizeof(QWarpSmem);
+    const auto kernel = k_quantile<NPF, CORE, OWN8>;
+    const size_t smem = sizeof(QWarpSmemT<OWN8 ? 8 : 16>);
     cudaError_t e =
         cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess)
         return e;
-    // eight warps' arrays per SM need the whole shared-memory carve-out
+    // eight (eleven) warps' arrays per SM need the whole shared-memory carve-out
     e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess)
         return e;
     const int64_t tiles_x = (g.W + kQCols - 1) / kQCols;
     const TuneCfg *t = tune_override();
-    int64_t tile_h = (t && t->tile_h > 0) ? t->tile_h : quantile_band_rows(g.H, g.W);
+    int64_t tile_h = (t && t->tile_h > 0) ? t->tile_h : quantile_band_rows(g.H, g.W, win.h);
     tile_h = tile_h < g.H ? tile_h : g.H;
     const int64_t tiles_y = (g.H + tile_h - 1) / tile_h;
     kernel<<<(unsigned)(tiles_x * tiles_y), 32, smem, stream>>>(g, win, q_num, q_den, offset, out,
@@ -49,18 +49,19 @@ static cudaError_t launch_q(const Image &g, const Window &win, int32_t q_num, in
 // One wave: as many row bands as the resident warps allow for the column
 // strips (the histograms cap residency at a few warps per SM, so a second,
 // partial wave would leave most SMs idle).
-int64_t quantile_band_rows(int64_t H, int64_t W)
+int64_t quantile_band_rows(int64_t H, int64_t W, int h)
 {
-    static int per_sm = [] {
+    auto occupancy = [](const void *kernel, size_t smem) {
         int v = 1;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_quantile<2, false>, 32, sizeof(QWarpSmem)) !=
-                cudaSuccess ||
-            v < 1) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, kernel, 32, smem) != cudaSuccess || v < 1) {
             cudaGetLastError();
             v = 1;
         }
         return v;
-    }();
+    };
+    static int per_sm16 = occupancy((const void *)k_quantile<2, false, false>, sizeof(QWarpSmem));
+    static int per_sm8 = occupancy((const void *)k_quantile<2, false, true>, sizeof(QWarpSmem8));
+    const int per_sm = quantile_own8(h) ? per_sm8 : per_sm16;
     int dev = 0, sms = 152;
     if (cudaGetDevice(&dev) == cudaSuccess)
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -76,13 +77,21 @@ cudaError_t launch_quantile(const Image &g, const Window &win, int32_t q_num, in
                             int32_t offset, uint8_t *out, int64_t out_pitch, uint8_t *Q,
                             cudaStream_t stream)
 {
+    const bool own8 = quantile_own8(win.h);
     auto run = [&]() -> cudaError_t {
         switch (quantile_prefetch(win.w)) {
         case 2:
-            return win.w >= 32 ? launch_q<2, true>(g, win, q_num, q_den, offset, out, out_pitch, Q, stream)
-                               : launch_q<2, false>(g, win, q_num, q_den, offset, out, out_pitch, Q, stream);
-        case 4: return launch_q<4, true>(g, win, q_num, q_den, offset, out, out_pitch, Q, stream);
-        default: return launch_q<6, true>(g, win, q_num, q_den, offset, out, out_pitch, Q, stream);
+            if (win.w >= 32)
+                return own8 ? launch_q<2, true, true>(g, win, q_num, q_den, offset, out, out_pitch, Q, stream)
+                            : launch_q<2, true, false>(g, win, q_num, q_den, offset, out, out_pitch, Q, stream);
+            return own8 ? launch_q<2, false, true>(g, win, q_num, q_den, offset, out, out_pitch, Q, stream)
+                        : launch_q<2, false, false>(g, win, q_num, q_den, offset, out, out_pitch, Q, stream);
+        case 4:
+            return own8 ? launch_q<4, true, true>(g, win, q_num, q_den, offset, out, out_pitch, Q, stream)
+                        : launch_q<4, true, false>(g, win, q_num, q_den, offset, out, out_pitch, Q, stream);
+        default:
+            return own8 ? launch_q<6, true, true>(g, win, q_num, q_den, offset, out, out_pitch, Q, stream)
+                        : launch_q<6, true, false>(g, win, q_num, q_den, offset, out, out_pitch, Q, stream);
         }
     };
     if (tune_env() == 0 && !tune_forced())
@@ -92,7 +101,7 @@ cudaError_t launch_quantile(const Image &g, const Window &win, int32_t q_num, in
     bool have = tune_get(key, c);
     if (tune_now(have)) {
         TuneCfg b;
-        if (tune_quantile(g, run, stream, b)) {
+        if (tune_quantile(g, win, run, stream, b)) {
             c = b;
             have = true;
             tune_put(key, c, true);

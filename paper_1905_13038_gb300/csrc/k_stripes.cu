@@ -330,7 +330,7 @@ uint2 *launch_stripes(const Image &g, const Window &win, int64_t row0, int64_t t
     const int64_t K = tiles_y + m + 1;  // chunks s .. s+m for every tile start
     const size_t qbytes = mode ? (size_t)K * (size_t)g.W * sizeof(uint4) : 0;
     uint2 *stripes = nullptr;
-    if (cudaMallocAsync((void **)&stripes, sbytes + qbytes, stream) != cudaSuccess) {
+    if (scratch_alloc((void **)&stripes, sbytes + qbytes, stream) != cudaSuccess) {
         cudaGetLastError();  // no scratch: the tiles warm up themselves
         return nullptr;
     }
@@ -349,7 +349,7 @@ uint2 *launch_stripes(const Image &g, const Window &win, int64_t row0, int64_t t
             e = launch_pdl(k_stripe_slide<sg>, (unsigned)b2, kStripeThreads, stream, g.W, tiles_y, m,
                            (const uint4 *)QR, stripes);
         if (e != cudaSuccess) {
-            cudaFreeAsync(stripes, stream);
+            scratch_free(stripes, stream);
             return nullptr;
         }
     } else {
@@ -361,12 +361,12 @@ uint2 *launch_stripes(const Image &g, const Window &win, int64_t row0, int64_t t
                  : launch_pdl(k_stripes<false>, (unsigned)sblocks, kStripeThreads, stream, g, win.o, win.u,
                               row0, tile_h, tiles_y, words, group, stripes);
         if (e != cudaSuccess) {
-            cudaFreeAsync(stripes, stream);
+            scratch_free(stripes, stream);
             return nullptr;
         }
     }
     if (cudaGetLastError() != cudaSuccess) {
-        cudaFreeAsync(stripes, stream);
+        scratch_free(stripes, stream);
         return nullptr;
     }
     return stripes;

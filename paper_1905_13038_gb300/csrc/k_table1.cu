@@ -230,7 +230,7 @@ static cudaError_t launch_ext_pipe(const Image &g, const Window &win, const Thre
         break;
     }
     cudaError_t e = cudaGetLastError();
-    if (stripes && cudaFreeAsync(stripes, stream) != cudaSuccess && e == cudaSuccess)
+    if (stripes && scratch_free(stripes, stream) != cudaSuccess && e == cudaSuccess)
         e = cudaGetLastError();
     return e;
 }
@@ -249,7 +249,7 @@ static cudaError_t launch_ext_t(const Image &g, const Window &win, const ThreshE
     k_window_ext<MODE, VEC, S2T><<<(unsigned)blocks, 32 * kWarpsPerBlockExt, 0, stream>>>(
         g, win, T, o, S, stripes);
     cudaError_t e = cudaGetLastError();
-    if (stripes && cudaFreeAsync(stripes, stream) != cudaSuccess && e == cudaSuccess)
+    if (stripes && scratch_free(stripes, stream) != cudaSuccess && e == cudaSuccess)
         e = cudaGetLastError();
     return e;
 }

@@ -136,7 +136,7 @@ static cudaError_t launch_t(const Image &g, const Window &win, const Thresh &T, 
     else
         e = launch_pdl(k_window<MODE, VEC, S2T, WARMB, 0>, (unsigned)blocks, 32 * kWarpsPerBlock, stream, g, win,
                        T, o, S, cst);
-    if (stripes && cudaFreeAsync(stripes, stream) != cudaSuccess && e == cudaSuccess)
+    if (stripes && scratch_free(stripes, stream) != cudaSuccess && e == cudaSuccess)
         e = cudaGetLastError();
     return e;
 }

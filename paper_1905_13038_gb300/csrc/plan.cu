@@ -1,8 +1,11 @@
 // Host-side planning of the window kernel's launches: the one-wave tile
-// height, the balanced tile schedule (shorter edge tiles), and the tuning
-// switches read from the environment.  Pure host code; the kernels that
-// consume the schedule live in k_window.cu and k_table1.cu.
+// height, the balanced tile schedule (shorter edge tiles), the tuning
+// switches read from the environment, and the library's stream-ordered
+// scratch pool.  Pure host code; the kernels that consume the schedule live
+// in k_window.cu and k_table1.cu.
 #include <stdlib.h>
+
+#include <mutex>
 
 #include "bz_internal.h"
 
@@ -152,6 +155,49 @@ TileSched make_sched(const Image &g, const Window &win, int64_t row0, int64_t ro
     }();
     S.prefetch = (pf && !stripes) ? 1 : 0;
     return S;
+}
+
+cudaError_t scratch_alloc(void **p, size_t bytes, cudaStream_t s)
+{
+    static std::mutex mu;
+    static cudaMemPool_t pools[64] = {nullptr};
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cap);
+    if (e != cudaSuccess)
+        return e;
+    int dev = 0;
+    e = cudaGetDevice(&dev);
+    if (e != cudaSuccess)
+        return e;
+    if (cap != cudaStreamCaptureStatusNone || dev < 0 || dev >= 64)
+        return cudaMallocAsync(p, bytes, s);
+    cudaMemPool_t pool = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (!pools[dev]) {
+            cudaMemPoolProps props = {};
+            props.allocType = cudaMemAllocationTypePinned;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = dev;
+            cudaMemPool_t np = nullptr;
+            if (cudaMemPoolCreate(&np, &props) == cudaSuccess) {
+                uint64_t keep = 256ull << 20;
+                cudaMemPoolSetAttribute(np, cudaMemPoolAttrReleaseThreshold, &keep);
+                pools[dev] = np;
+            } else {
+                cudaGetLastError();
+            }
+        }
+        pool = pools[dev];
+    }
+    if (!pool)
+        return cudaMallocAsync(p, bytes, s);
+    return cudaMallocFromPoolAsync(p, bytes, pool, s);
+}
+
+cudaError_t scratch_free(void *p, cudaStream_t s)
+{
+    return cudaFreeAsync(p, s);
 }
 
 int plan_window_launch(int64_t H, int64_t W, const Window &win, int sms, bool pipe, int64_t out[6])

@@ -481,10 +481,10 @@ bool tune_window(int mode, const Image &g, const Window &win, int64_t row0, int6
     return best_ms > 0.0;
 }
 
-bool tune_quantile(const Image &g, const std::function<cudaError_t()> &launch, cudaStream_t stream,
-                   TuneCfg &best)
+bool tune_quantile(const Image &g, const Window &win, const std::function<cudaError_t()> &launch,
+                   cudaStream_t stream, TuneCfg &best)
 {
-    const int64_t th0 = quantile_band_rows(g.H, g.W);
+    const int64_t th0 = quantile_band_rows(g.H, g.W, win.h);
     std::vector<int64_t> ths;
     push_unique(ths, th0, 1, g.H);
     push_unique(ths, (th0 * 3 + 3) / 4, 1, g.H);

@@ -22,6 +22,9 @@ CASES = [
     (300, 300, 257, 257, 1, 2),  # h*w > 65535: 32-bit histogram counters
     (50, 70, 5, 5, 0, 1),
     (50, 70, 5, 5, 1, 1),
+    (160, 230, 36, 36, 1, 2),    # the tallest window with 8-bit own counts (7 h = 252)
+    (160, 230, 36, 130, 1, 10),  # ... with a core part and a wide read-ahead
+    (160, 230, 37, 37, 1, 2),    # the shortest window with 16-bit own counts
 ]
 
 
@@ -66,3 +69,21 @@ def test_quantile_page_full(h, w, qn, qd):
     out = bz.binarize_quantile(t, h, w, qn, qd, 8)
     _, ref = oracle.binarize_quantile(img, h, w, qn, qd, 8, threads=nt)
     check_packed(out, ref, W)
+
+
+@pytest.mark.parametrize("h,w", [(36, 36), (36, 9), (37, 37)])
+def test_own_counts_at_their_limit(h, w):
+    """A flat page puts every pixel of a lane's own part (7 columns x h rows,
+    252 at h = 36) in one gray level, the most an 8-bit own count ever
+    holds; a page that is flat except for one bright column moves Q across
+    the full count."""
+    import paper_1905_13038_gb300 as bz
+    H, W = 120, 150
+    flat = np.full((H, W), 77, dtype=np.uint8)
+    ramp = flat.copy()
+    ramp[:, 70] = 250
+    for img in (flat, ramp):
+        t, _ = to_device(img)
+        for qn, qd in ((1, 2), (1, 100), (99, 100)):
+            Q = bz.window_quantile(t, h, w, qn, qd).cpu().numpy()
+            np.testing.assert_array_equal(Q, oracle.window_quantile(img, h, w, qn, qd))
