@@ -185,15 +185,42 @@ __global__ void __launch_bounds__(kStripeThreads)
     am = am < a0 ? a0 : (am > a1 ? a1 : am);
     uint32_t C[4] = {0u, 0u, 0u, 0u}, D[4] = {0u, 0u, 0u, 0u};
     uint32_t RC[4] = {0u, 0u, 0u, 0u}, RD[4] = {0u, 0u, 0u, 0u};
-    if (a0 < am)
-        stripe_rows<VEC4>(g, x, a0, am, C, D);
+    if (a1 - a0 <= kChunkBatch) {
+        // the whole chunk in one batch of loads (one memory round trip),
+        // its first rows summed apart (the branch is uniform: a warp's
+        // threads share the chunk)
+        uint32_t wd[kChunkBatch];
 #pragma unroll
-    for (int b = 0; b < 4; b++) {
-        RC[b] = C[b];
-        RD[b] = D[b];
+        for (int j = 0; j < kChunkBatch; j++)
+            wd[j] = a0 + j < a1 ? stripe_word<VEC4>(g, a0 + j, x) : 0u;
+        const int nm = (int)(am - a0);
+        PackedSums PR, PQ;
+#pragma unroll
+        for (int j = 0; j < kChunkBatch; j++) {
+            if (j < nm)
+                PR.add(wd[j]);
+            else
+                PQ.add(wd[j]);
+        }
+        PR.flush(RC);
+        PQ.flush(C);
+#pragma unroll
+        for (int b = 0; b < 4; b++) {
+            RD[b] = PR.d[b];
+            C[b] += RC[b];
+            D[b] = RD[b] + PQ.d[b];
+        }
+    } else {
+        if (a0 < am)
+            stripe_rows<VEC4>(g, x, a0, am, C, D);
+#pragma unroll
+        for (int b = 0; b < 4; b++) {
+            RC[b] = C[b];
+            RD[b] = D[b];
+        }
+        if (am < a1)
+            stripe_rows<VEC4>(g, x, am, a1, C, D);
     }
-    if (am < a1)
-        stripe_rows<VEC4>(g, x, am, a1, C, D);
 #pragma unroll
     for (int b = 0; b < 4; b++)
         if (x + b < g.W && BZ_DBG_IN(QR + k * g.W + x + b, 16, QR, (size_t)K * g.W * 16, kDbgScratch))
@@ -271,11 +298,12 @@ static int stripe_group()
     return env > 0 ? env : 2;
 }
 
-// Stripes pay off once the window spans about five tile heights: each tile's
-// own warm-up reads h rows for tile_h output rows.  Measured on GB300 (4096 x
-// 3072 page, 21-row tiles): 63 x 63 64 us per call without stripes (the edge
-// columns then also get the balanced schedule) against 88 us with them;
-// 255 x 255 143 us without against 78 us with.
+// Stripes pay off once the window spans about three tile heights: each
+// tile's own warm-up reads h rows for tile_h output rows.  Measured on GB300
+// (4096 x 3072 page, BZ_FP64, 21-row tiles, events over 64 calls): 63 x 63
+// 58.7 us without stripes, 54.7 with the chunked pre-pass (68.2 with the
+// group form); 255 x 255 127.6 without, 56.8 with; 31 x 127 (1.5 tile
+// heights) 47.0 without, 54.7 with.
 // BZ_STRIPES=0/1 forces it (tuning), then a tuned configuration (only for
 // windows of 48 rows or more, the range the pre-pass is tested on).
 bool stripes_allowed(int h)
@@ -294,12 +322,13 @@ static bool use_stripes(int h, int64_t tile_h)
     const TuneCfg *t = tune_override();
     if (t && t->stripes >= 0)
         return t->stripes != 0 && stripes_allowed(h);
-    return h >= 48 && h >= 5 * tile_h;
+    return h >= 48 && h >= 3 * tile_h;
 }
 
-// Chunked form when the window spans at least four tile heights (measured on
-// GB300: 255 x 255 86 vs 105 us; at 63 x 63, three tile heights, the
-// per-group slide is 2 us faster).  BZ_STRIPE_MODE=0/1 forces one (tuning).
+// Chunked form when the window spans at least two tile heights (its
+// chunk sums take one round trip of loads per chunk; measured above: 63 x 63
+// 54.7 us against 68.2 with the group form).  BZ_STRIPE_MODE=0/1 forces one
+// (tuning).
 static int stripe_mode(const Window &win, int64_t tile_h)
 {
     static const int env_mode = [] {
@@ -307,7 +336,7 @@ static int stripe_mode(const Window &win, int64_t tile_h)
         return e ? atoi(e) : -1;
     }();
     const int m = (int)(win.h / tile_h);
-    return env_mode >= 0 ? env_mode : (m >= 4 ? 1 : 0);
+    return env_mode >= 0 ? env_mode : (m >= 2 ? 1 : 0);
 }
 
 int stripe_kernel_count(const Window &win, int64_t tile_h, int64_t tiles_y)
