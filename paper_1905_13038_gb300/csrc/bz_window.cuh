@@ -30,7 +30,7 @@ namespace bz {
 
 constexpr int kColsPerLane = 8;
 constexpr int kTileCols = 32 * kColsPerLane;  // 256
-constexpr int kWarmRows = 8;                   // warm-up rows per batch (WARMB)
+constexpr int kWarmRows = 8;                   // warm-up rows per batch (WARMB), a multiple of 4
 
 enum Mode : int { MODE_FP64 = 0, MODE_FP32 = 1, MODE_FP64_DIRECT = 2, MODE_SUMS = 3, MODE_REPORT = 4 };
 
@@ -311,6 +311,44 @@ __device__ __forceinline__ void slide8(uint2 A, uint2 B, uint2 C, uint2 D, int32
                         dp2a_hi_uu(__byte_perm(BC, 0u, 0x4342u), BC, 0u);
             E1[m] = dp4a_us(BC, 0x0000FFFFu, dp4a_us(AD, 0x00000101u, E1[m]));
             E1[m + 1] = dp4a_us(BC, 0xFFFF0000u, dp4a_us(AD, 0x01010000u, E1[m + 1]));
+        }
+    }
+}
+
+// Four warm-up rows at once: the bytes of each column in rows r .. r+3 are
+// gathered into one word (a 4 x 4 byte transpose, eight byte permutes per
+// four columns and stream), so that E1 += sum (a - b) and E2 += sum (a^2 - b^2)
+// take four DP4A per column instead of four extractions and updates per row.
+__device__ __forceinline__ void warm8x4(const uint2 (&A)[4], const uint2 (&B)[4], int32_t *E1, uint32_t *E2)
+{
+#pragma unroll
+    for (int q = 0; q < 2; q++) {
+        uint32_t ca[4], cb[4];
+        {
+            const uint32_t a0 = q ? A[0].y : A[0].x, a1 = q ? A[1].y : A[1].x;
+            const uint32_t a2 = q ? A[2].y : A[2].x, a3 = q ? A[3].y : A[3].x;
+            const uint32_t lo01 = __byte_perm(a0, a1, 0x5140u), hi01 = __byte_perm(a0, a1, 0x7362u);
+            const uint32_t lo23 = __byte_perm(a2, a3, 0x5140u), hi23 = __byte_perm(a2, a3, 0x7362u);
+            ca[0] = __byte_perm(lo01, lo23, 0x5410u);
+            ca[1] = __byte_perm(lo01, lo23, 0x7632u);
+            ca[2] = __byte_perm(hi01, hi23, 0x5410u);
+            ca[3] = __byte_perm(hi01, hi23, 0x7632u);
+        }
+        {
+            const uint32_t b0 = q ? B[0].y : B[0].x, b1 = q ? B[1].y : B[1].x;
+            const uint32_t b2 = q ? B[2].y : B[2].x, b3 = q ? B[3].y : B[3].x;
+            const uint32_t lo01 = __byte_perm(b0, b1, 0x5140u), hi01 = __byte_perm(b0, b1, 0x7362u);
+            const uint32_t lo23 = __byte_perm(b2, b3, 0x5140u), hi23 = __byte_perm(b2, b3, 0x7362u);
+            cb[0] = __byte_perm(lo01, lo23, 0x5410u);
+            cb[1] = __byte_perm(lo01, lo23, 0x7632u);
+            cb[2] = __byte_perm(hi01, hi23, 0x5410u);
+            cb[3] = __byte_perm(hi01, hi23, 0x7632u);
+        }
+#pragma unroll
+        for (int c = 0; c < 4; c++) {
+            const int m = 4 * q + c;
+            E1[m] = dp4a_us(cb[c], 0xFFFFFFFFu, dp4a_us(ca[c], 0x01010101u, E1[m]));
+            E2[m] = __dp4a(ca[c], ca[c], E2[m]) - __dp4a(cb[c], cb[c], 0u);
         }
     }
 }
@@ -1062,13 +1100,38 @@ __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &w
                     }
                 }
 #pragma unroll
+                for (int q = 0; q < kWarmRows; q += 4) {  // rows past a_hi are zero
+                    const uint2 A4[4] = {Ar[q], Ar[q + 1], Ar[q + 2], Ar[q + 3]};
+                    const uint2 B4[4] = {Br[q], Br[q + 1], Br[q + 2], Br[q + 3]};
+                    warm8x4(A4, B4, E1, E2);
+                }
+#pragma unroll
                 for (int q = 0; q < kWarmRows; q++) {
-                    warm8(Ar[q], Br[q], E1, E2);
                     a1p += w1r[q];
                     a2p += w2r[q];
                 }
             }
             a_hi = a_lo - 1;
+        }
+        // four rows at a time (their loads issued together), then the rest
+        // one row at a time with one row of look-ahead
+        for (; a_lo + 3 <= a_hi; a_lo += 4) {
+            uint2 Ar[4], Br[4];
+            uint32_t w1r[4], w2r[4];
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const uint8_t *rp = g.img + (a_lo + q) * g.pitch;
+                Ar[q] = ldA(rp);
+                Br[q] = ldB(rp);
+                w1r[q] = w2r[q] = 0u;
+                anchor_row(rp, w1r[q], w2r[q]);
+            }
+            warm8x4(Ar, Br, E1, E2);
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                a1p += w1r[q];
+                a2p += w2r[q];
+            }
         }
         uint2 A = Z, B = Z;
         uint32_t w1 = 0, w2 = 0;
