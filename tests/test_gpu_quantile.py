@@ -87,3 +87,23 @@ def test_own_counts_at_their_limit(h, w):
         for qn, qd in ((1, 2), (1, 100), (99, 100)):
             Q = bz.window_quantile(t, h, w, qn, qd).cpu().numpy()
             np.testing.assert_array_equal(Q, oracle.window_quantile(img, h, w, qn, qd))
+
+
+@pytest.mark.parametrize("h,w,qn,qd", [(31, 31, 1, 20), (31, 31, 19, 20), (45, 77, 1, 8), (101, 101, 7, 8),
+                                        (15, 15, 0, 1), (15, 15, 1, 1)])
+def test_long_walks_across_empty_gray_levels(h, w, qn, qd):
+    """Far-from-median ranks on a page of two levels (30 and 220) in blocks
+    with sparse noise: from one row to the next Q crosses the empty gray
+    values between the levels, the longest moves its walk makes."""
+    import paper_1905_13038_gb300 as bz
+    rng = np.random.default_rng(h * 1000 + qn)
+    H, W = 260, 330
+    yy, xx = np.mgrid[0:H, 0:W]
+    img = np.where(((yy // 37) + (xx // 53)) % 2 == 0, 30, 220).astype(np.uint8)
+    noise = rng.random((H, W)) < 0.03
+    img[noise] = rng.integers(0, 256, int(noise.sum())).astype(np.uint8)
+    t, _ = to_device(img)
+    Q = bz.window_quantile(t, h, w, qn, qd).cpu().numpy()
+    np.testing.assert_array_equal(Q, oracle.window_quantile(img, h, w, qn, qd))
+    out = bz.binarize_quantile(t, h, w, qn, qd, 8)
+    check_packed(out, oracle.binarize_quantile(img, h, w, qn, qd, 8)[1], W)
