@@ -5,7 +5,7 @@ One step = the page binarized with Sauvola (k = 0.5, R = 128, BZ_FP64: output
 identical to the canonical FP64 threshold) at each of the four windows
 h x w = 15x15, 63x63, 255x255 and 31x127, i.e. four binarization calls (the
 window kernel, preceded by the stripe pre-pass for windows spanning about
-three tile heights or more).  Inputs are resident in HBM: 32 rotating input/output buffer pairs
+five tile heights or more).  Inputs are resident in HBM: 32 rotating input/output buffer pairs
 (about 450 MB, more than three times the 129 MB L2) so that no launch finds
 its image in L2.  The timed region is a CUDA graph of K steps, timed with CUDA
 events on its stream, bracketed by a barrier and a synchronize, maximum over
@@ -805,7 +805,7 @@ def main():
     calls = args.steps * len(WINDOWS)
     launch_ms = ms / calls  # per binarization call (the unit of the roofline)
     # kernels per call as the library plans them (the window kernel, plus
-    # the stripe pre-pass for windows spanning about three tile heights or more)
+    # the stripe pre-pass for windows spanning about five tile heights or more)
     launches = args.steps * sum(bz.kernels_per_call(H, W, h, w, prec) for (h, w) in WINDOWS)
     hbm, peak_kind = peaks()
     achieved_gbs = BYTES_PER_PIXEL * H * W / (launch_ms * 1e-3) / 1e9

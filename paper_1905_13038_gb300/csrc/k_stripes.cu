@@ -193,22 +193,49 @@ __global__ void __launch_bounds__(kStripeThreads)
 #pragma unroll
         for (int j = 0; j < kChunkBatch; j++)
             wd[j] = a0 + j < a1 ? stripe_word<VEC4>(g, a0 + j, x) : 0u;
+        // four rows at a time: the bytes of each column in the four rows
+        // gathered into one word (a 4 x 4 byte transpose), so that its sum
+        // and its sum of squares are one DP4A each; groups before the split
+        // at nm go to R, groups after it to the rest, the group across it is
+        // split by a byte mask (rows past the chunk are zero words)
         const int nm = (int)(am - a0);
-        PackedSums PR, PQ;
+        uint32_t QC[4] = {0u, 0u, 0u, 0u}, QD[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
-        for (int j = 0; j < kChunkBatch; j++) {
-            if (j < nm)
-                PR.add(wd[j]);
-            else
-                PQ.add(wd[j]);
+        for (int gq = 0; gq < kChunkBatch / 4; gq++) {
+            const uint32_t w0 = wd[4 * gq], w1 = wd[4 * gq + 1], w2 = wd[4 * gq + 2], w3 = wd[4 * gq + 3];
+            const uint32_t lo01 = __byte_perm(w0, w1, 0x5140u), hi01 = __byte_perm(w0, w1, 0x7362u);
+            const uint32_t lo23 = __byte_perm(w2, w3, 0x5140u), hi23 = __byte_perm(w2, w3, 0x7362u);
+            const uint32_t col[4] = {__byte_perm(lo01, lo23, 0x5410u), __byte_perm(lo01, lo23, 0x7632u),
+                                     __byte_perm(hi01, hi23, 0x5410u), __byte_perm(hi01, hi23, 0x7632u)};
+            const int k = nm - 4 * gq;  // rows of this group that belong to R (uniform)
+            if (k >= 4) {
+#pragma unroll
+                for (int b = 0; b < 4; b++) {
+                    RC[b] = __dp4a(col[b], 0x01010101u, RC[b]);
+                    RD[b] = __dp4a(col[b], col[b], RD[b]);
+                }
+            } else if (k <= 0) {
+#pragma unroll
+                for (int b = 0; b < 4; b++) {
+                    QC[b] = __dp4a(col[b], 0x01010101u, QC[b]);
+                    QD[b] = __dp4a(col[b], col[b], QD[b]);
+                }
+            } else {
+                const uint32_t mr = 0xFFFFFFFFu >> (8 * (4 - k));
+#pragma unroll
+                for (int b = 0; b < 4; b++) {
+                    const uint32_t cr = col[b] & mr, cq = col[b] & ~mr;
+                    RC[b] = __dp4a(cr, 0x01010101u, RC[b]);
+                    RD[b] = __dp4a(cr, cr, RD[b]);
+                    QC[b] = __dp4a(cq, 0x01010101u, QC[b]);
+                    QD[b] = __dp4a(cq, cq, QD[b]);
+                }
+            }
         }
-        PR.flush(RC);
-        PQ.flush(C);
 #pragma unroll
         for (int b = 0; b < 4; b++) {
-            RD[b] = PR.d[b];
-            C[b] += RC[b];
-            D[b] = RD[b] + PQ.d[b];
+            C[b] = RC[b] + QC[b];
+            D[b] = RD[b] + QD[b];
         }
     } else {
         if (a0 < am)
@@ -298,12 +325,12 @@ static int stripe_group()
     return env > 0 ? env : 2;
 }
 
-// Stripes pay off once the window spans about three tile heights: each
-// tile's own warm-up reads h rows for tile_h output rows.  Measured on GB300
-// (4096 x 3072 page, BZ_FP64, 21-row tiles, events over 64 calls): 63 x 63
-// 58.7 us without stripes, 54.7 with the chunked pre-pass (68.2 with the
-// group form); 255 x 255 127.6 without, 56.8 with; 31 x 127 (1.5 tile
-// heights) 47.0 without, 54.7 with.
+// Stripes pay off once the window spans about five tile heights: each
+// tile's own warm-up reads h rows for tile_h output rows (four rows per
+// step).  Measured on GB300 (4096 x 3072 page, BZ_FP64, 21-row tiles, events
+// over 64 calls): 63 x 63 48.5 us without stripes, 53.1 with the chunked
+// pre-pass; 255 x 255 90.5 without, 54.8 with; 31 x 127 (1.5 tile heights)
+// 42.1 without.
 // BZ_STRIPES=0/1 forces it (tuning), then a tuned configuration (only for
 // windows of 48 rows or more, the range the pre-pass is tested on).
 bool stripes_allowed(int h)
@@ -322,11 +349,11 @@ static bool use_stripes(int h, int64_t tile_h)
     const TuneCfg *t = tune_override();
     if (t && t->stripes >= 0)
         return t->stripes != 0 && stripes_allowed(h);
-    return h >= 48 && h >= 3 * tile_h;
+    return h >= 48 && h >= 5 * tile_h;
 }
 
 // Chunked form when the window spans at least two tile heights (its
-// chunk sums take one round trip of loads per chunk; measured above: 63 x 63
+// chunk sums take one round trip of loads per chunk; 63 x 63 with stripes:
 // 54.7 us against 68.2 with the group form).  BZ_STRIPE_MODE=0/1 forces one
 // (tuning).
 static int stripe_mode(const Window &win, int64_t tile_h)

@@ -70,9 +70,9 @@ def test_plan_falls_back_to_the_heuristic_without_an_entry():
     assert L.bz_tile_schedule(3072, 4096, 152, 1, 0, out) == 0
     assert plan["tile_h"] == out[1] and plan["edge_h"] == out[2] and plan["n_edge"] == out[3]
     assert plan["tiles"] == out[4] <= plan["resident"] == 152 * 16
-    # a tall window spanning three tile heights or more takes the stripe pre-pass
+    # a tall window spanning five tile heights or more takes the stripe pre-pass
     assert bz.tune_window_plan(GPU, "fp64", 3072, 4096, 255, 255, 152)[1]["stripes"] == 1
-    assert bz.tune_window_plan(GPU, "fp64", 3072, 4096, 63, 63, 152)[1]["stripes"] == 1
+    assert bz.tune_window_plan(GPU, "fp64", 3072, 4096, 63, 63, 152)[1]["stripes"] == 0
     assert bz.tune_window_plan(GPU, "fp64", 3072, 4096, 31, 127, 152)[1]["stripes"] == 0
 
 
