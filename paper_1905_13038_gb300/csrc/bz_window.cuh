@@ -641,16 +641,38 @@ __device__ __forceinline__ void window_rows(const Image &g, const Window &win, c
                     }
                 }
 #pragma unroll
+                for (int q = 0; q < kWarmRows; q += 4) {  // rows past a_hi are zero
+                    const uint2 A4[4] = {Ar[q], Ar[q + 1], Ar[q + 2], Ar[q + 3]};
+                    const uint2 B4[4] = {Br[q], Br[q + 1], Br[q + 2], Br[q + 3]};
+                    warm8x4(A4, B4, E1, E2);
+                }
+#pragma unroll
                 for (int q = 0; q < kWarmRows; q++) {
-                    warm8(Ar[q], Br[q], E1, E2);
                     a1p += w1r[q];
                     a2p += w2r[q];
                 }
             }
-            a_hi = a_lo - 1;  // done: skip the one-row loop below
+            a_hi = a_lo - 1;  // done: skip the loops below
         }
-        // one row of look-ahead: the loads of row a+1 are in flight while row
-        // a is accumulated
+        // four rows at a time (their loads issued together)
+        for (; a_lo + 3 <= a_hi; a_lo += 4) {
+            uint2 Ar[4], Br[4];
+            uint32_t w1r[4], w2r[4];
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                load_row(a_lo + q, Ar[q], Br[q]);
+                w1r[q] = w2r[q] = 0u;
+                anchor_row(a_lo + q, w1r[q], w2r[q]);
+            }
+            warm8x4(Ar, Br, E1, E2);
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                a1p += w1r[q];
+                a2p += w2r[q];
+            }
+        }
+        // the rest with one row of look-ahead: the loads of row a+1 are in
+        // flight while row a is accumulated
         uint2 A = Z, B = Z;
         uint32_t w1 = 0, w2 = 0;
         if (a_lo <= a_hi) {
