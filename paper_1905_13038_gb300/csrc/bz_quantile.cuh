@@ -30,10 +30,11 @@
 //
 // Updates are shared-memory atomics without a return value.  The own
 // histograms hold 16-bit counts, two lanes per 32-bit word (a lane's counts
-// stay below 7 h <= 3577, so neither half borrows from or carries into the
-// other), or for windows of at most 36 rows 8-bit counts, four lanes per
-// word (7 h <= 252), which shrinks a warp's arrays from 27.5 to 19.2 KB and
-// lets 11 instead of 8 warps share an SM.  Image columns outside [0, W) are staged as the value 256, a bin
+// stay below 7 h <= 3577, so no field borrows from or carries into the
+// next), 10-bit counts, three lanes per word, for windows of at most 146 rows
+// (7 h <= 1022), or 8-bit counts, four lanes per word, for windows of at most
+// 36 rows (7 h <= 252): a warp's arrays take 27.5, 22.3 or 19.2 KB, so 8, 10
+// or 11 warps share an SM.  Image columns outside [0, W) are staged as the value 256, a bin
 // that is counted but never queried, so no update needs a mask.  Each row's
 // bytes are loaded one row step ahead into registers, so the global-memory
 // latency overlaps the previous row's work.
@@ -65,12 +66,18 @@ struct QWarpSmemT {
     uint16_t rout[kQSpanCap];          // staged leaving row
 };
 typedef QWarpSmemT<16> QWarpSmem;
-typedef QWarpSmemT<8> QWarpSmem8;
 
-// 8-bit own counts hold a lane's own part (at most 7 columns x h rows)
-__host__ __device__ constexpr bool quantile_own8(int h)
+// Bits of an own count: a lane's own part holds at most 7 columns x h rows,
+// so 8 bits (four lanes per word) serve h <= 36, 10 bits (three lanes per
+// word) h <= 146, 16 bits (two lanes per word) every window.
+__host__ __device__ constexpr int quantile_own_bits(int h)
 {
-    return 7 * h <= 255;
+    return 7 * h <= 255 ? 8 : (7 * h <= 1023 ? 10 : 16);
+}
+// Own-count words per gray value: 8, 11 or 16.
+__host__ __device__ constexpr int quantile_own_words(int bits)
+{
+    return bits == 8 ? 8 : (bits == 10 ? 11 : 16);
 }
 
 // Pixels of a shared part below gray value Q: the prefix up to Q's 4-value
@@ -96,15 +103,16 @@ __host__ __device__ constexpr int quantile_prefetch(int w)
 // One warp (lane = threadIdx.x & 31) computes output columns [x0, x0 + 32)
 // x rows [y0, y1).  out (packed bits) and Qout (dense quantile plane, W per
 // row) may each be null.  NPF = quantile_prefetch(w); CORE = (w >= 32);
-// OWN8 = quantile_own8(h).
-template <int NPF, bool CORE, bool OWN8 = false>
+// OB = quantile_own_bits(h) or more.
+template <int NPF, bool CORE, int OB = 16>
 __device__ __forceinline__ void quantile_warp_tile(const Image &g, const Window &win, int32_t q_num,
                                                    int32_t q_den, int32_t offset, uint8_t *out,
                                                    int64_t out_pitch, uint8_t *Qout, int64_t x0,
-                                                   int64_t y0, int64_t y1, QWarpSmemT<OWN8 ? 8 : 16> &S,
-                                                   int lane)
+                                                   int64_t y0, int64_t y1,
+                                                   QWarpSmemT<quantile_own_words(OB)> &S, int lane)
 {
-    constexpr int kOW = OWN8 ? 8 : 16;  // words per own-count row
+    constexpr int kOW = quantile_own_words(OB);  // words per own-count row
+    constexpr int kLPW = OB == 8 ? 4 : (OB == 10 ? 3 : 2);  // lanes per own word
     const int w = win.w, h = win.h;
     const int G = lane >> 3, pos = lane & 7;
     const int64_t span0 = x0 - win.l + 1;  // image column of staged slot 0
@@ -150,10 +158,14 @@ __device__ __forceinline__ void quantile_warp_tile(const Image &g, const Window 
     const int core_rounds = (ncore + 31) >> 5;
     const bool has_grp = ngrp > 0;
     // own-count step of this lane, its field of an own word, its column
-    const uint32_t dplus = OWN8 ? 1u << (8 * (lane & 3)) : ((lane & 1) ? 0x10000u : 1u);
+    const int ofield = lane % kLPW;
+    const uint32_t dplus = 1u << (OB * ofield);
     const uint32_t dminus = 0u - dplus;
-    const uint32_t osel = OWN8 ? 0x4440u | (unsigned)(lane & 3) : ((lane & 1) ? 0x4432u : 0x4410u);
-    uint32_t *const ownl = &S.own[0][OWN8 ? lane >> 2 : lane >> 1];
+    const uint32_t osel = OB == 8 ? 0x4440u | (unsigned)ofield : (ofield ? 0x4432u : 0x4410u);
+    uint32_t *const ownl = &S.own[0][lane / kLPW];
+    auto own_count = [&](uint32_t wd) -> uint32_t {
+        return OB == 10 ? (wd >> (10 * ofield)) & 0x3FFu : __byte_perm(wd, 0u, osel);
+    };
 
     // prefetched slots lane + 32 t, t < NPF: stored if inside the span,
     // loaded if also inside the image (else the value 256)
@@ -345,7 +357,7 @@ __device__ __forceinline__ void quantile_warp_tile(const Image &g, const Window 
             for (int k = 0; k < 4; k++) {
                 int v = v0 + k;
                 v = v < 0 ? 0 : v;
-                o[k] = __byte_perm(ownl[v * kOW], 0u, osel);
+                o[k] = own_count(ownl[v * kOW]);
                 c[k] = o[k];
                 if (has_grp)
                     c[k] += S.grp[G][v];

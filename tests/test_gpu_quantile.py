@@ -24,7 +24,9 @@ CASES = [
     (50, 70, 5, 5, 1, 1),
     (160, 230, 36, 36, 1, 2),    # the tallest window with 8-bit own counts (7 h = 252)
     (160, 230, 36, 130, 1, 10),  # ... with a core part and a wide read-ahead
-    (160, 230, 37, 37, 1, 2),    # the shortest window with 16-bit own counts
+    (160, 230, 37, 37, 1, 2),    # the shortest window with 10-bit own counts
+    (200, 230, 146, 40, 1, 2),   # the tallest window with 10-bit own counts (7 h = 1022)
+    (200, 230, 147, 147, 1, 10),  # the shortest window with 16-bit own counts
 ]
 
 
@@ -71,14 +73,14 @@ def test_quantile_page_full(h, w, qn, qd):
     check_packed(out, ref, W)
 
 
-@pytest.mark.parametrize("h,w", [(36, 36), (36, 9), (37, 37)])
+@pytest.mark.parametrize("h,w", [(36, 36), (36, 9), (37, 37), (146, 20), (147, 147)])
 def test_own_counts_at_their_limit(h, w):
-    """A flat page puts every pixel of a lane's own part (7 columns x h rows,
-    252 at h = 36) in one gray level, the most an 8-bit own count ever
-    holds; a page that is flat except for one bright column moves Q across
-    the full count."""
+    """A flat page puts every pixel of a lane's own part (7 columns x h rows:
+    252 at h = 36, 1022 at h = 146) in one gray level, the most an 8-bit
+    (10-bit) own count ever holds; a page that is flat except for one bright
+    column moves Q across the full count."""
     import paper_1905_13038_gb300 as bz
-    H, W = 120, 150
+    H, W = 200, 150
     flat = np.full((H, W), 77, dtype=np.uint8)
     ramp = flat.copy()
     ramp[:, 70] = 250
