@@ -163,7 +163,11 @@ int32_t bz_tile_schedule(int64_t H, int64_t W, int32_t sms, int32_t pipe,
 
 /* Number of pixels the most recent BZ_FP64 call on this device could not
  * decide in FP32 and evaluated in FP64, read back synchronously after the
- * stream finishes.  Diagnostic only; returns -1 when unknown. */
+ * stream finishes (0 before any BZ_FP64 call).  Single-image calls count into
+ * two per-device counters in turn, each zeroed by the call after it, so the
+ * count is that of the latest call only while calls on the device are
+ * ordered (one stream); batches count into a third.  Diagnostic only;
+ * returns -1 when unknown. */
 int64_t bz_last_fp64_fallbacks(void *stream);
 
 /* Sauvola (method 0) or Niblack (method 1) from HOST memory: the image is
