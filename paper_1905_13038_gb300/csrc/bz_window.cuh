@@ -994,6 +994,173 @@ __device__ __forceinline__ uint2 shift8(uint2 v, int sh)
     return make_uint2((uint32_t)x, (uint32_t)(x >> 32));
 }
 
+// Column sums over four rows of one word (columns c .. c+3): the bytes of each
+// column are gathered into one word (4 x 4 byte transpose), then one DP4A adds
+// the column's sum and one its sum of squares.
+__device__ __forceinline__ void col4_sums(uint32_t r0, uint32_t r1, uint32_t r2, uint32_t r3, uint32_t *C,
+                                          uint32_t *D)
+{
+    const uint32_t lo01 = __byte_perm(r0, r1, 0x5140u), hi01 = __byte_perm(r0, r1, 0x7362u);
+    const uint32_t lo23 = __byte_perm(r2, r3, 0x5140u), hi23 = __byte_perm(r2, r3, 0x7362u);
+    const uint32_t c[4] = {__byte_perm(lo01, lo23, 0x5410u), __byte_perm(lo01, lo23, 0x7632u),
+                           __byte_perm(hi01, hi23, 0x5410u), __byte_perm(hi01, hi23, 0x7632u)};
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        C[k] = __dp4a(c[k], 0x01010101u, C[k]);
+        D[k] = __dp4a(c[k], c[k], D[k]);
+    }
+}
+
+// Warm-up of the pipelined path (row y0, window rows a_lo .. a_hi) as column
+// sums (Sec. 3.1 stripe identity): every lane sums its own 8 columns (one
+// aligned 8-byte load per row) and AW words of the halo, the columns
+// [x0 - 64 AW, x0) and [x0 + 256, x0 + 256 + r) that the window edges of the
+// tile reach (l, r <= 64 AW).  The sums C, D then go through the warp's shared
+// memory once, E_j = C_{j+r} - C_{j-l} (likewise for the squares), and the
+// anchor is the sum of C and D over the columns [x0 - l, x0 + r).  The same
+// integers as sliding both window-edge streams down the rows (E-form), with
+// one load stream instead of two plus the anchor's.  EDGE: columns outside
+// [0, W) count as 0 (words left of column 0 or starting at W or later are not
+// read; the sums of columns >= W, read from the row's padding, are cleared).
+// `sm`: the warp's shared memory, 4608 bytes used (column k of
+// [x0 - 64 AW, x0 + 256 + 64 AW) at word k + k / 8, so that lanes 8 columns
+// apart read distinct banks); free again when this returns.
+template <int AW, bool EDGE>
+__device__ __forceinline__ void warm_cols(const Image &g, const Window &win, int64_t x0, int lane,
+                                          int64_t a_lo, int64_t a_hi, uint32_t *sm, int32_t *E1,
+                                          uint32_t *E2, uint32_t &a1p, uint32_t &a2p)
+{
+    constexpr int HALO = 64 * AW;
+    constexpr int NPH = (kTileCols + 2 * HALO) * 9 / 8;  // words per array
+    [[maybe_unused]] const size_t ext = dbg_image_extent(g);
+    const int l = win.l, r = win.r;
+    const int64_t j0 = x0 + kColsPerLane * lane;
+    // halo word q of this lane: AW = 1, lanes 0-15 left and 16-31 right; AW =
+    // 2, word 0 left and word 1 right.  `hk`: its first column, relative to
+    // x0 - HALO.  Right words past the window's reach are not read.
+    int hk[AW];
+    bool hv[AW];
+#pragma unroll
+    for (int q = 0; q < AW; q++) {
+        const bool left = AW == 1 ? lane < 16 : q == 0;
+        const int k = AW == 1 ? 4 * (lane & 15) : 4 * lane;
+        hk[q] = left ? k : HALO + kTileCols + k;
+        hv[q] = left || k < r;
+        if (EDGE) {
+            const int64_t c = x0 - HALO + hk[q];
+            hv[q] = hv[q] && c >= 0 && c < g.W;
+        }
+    }
+    const bool ov = !EDGE || j0 < g.W;
+    uint32_t Co[kColsPerLane], Do[kColsPerLane], Ch[AW][4], Dh[AW][4];
+#pragma unroll
+    for (int m = 0; m < kColsPerLane; m++)
+        Co[m] = Do[m] = 0u;
+#pragma unroll
+    for (int q = 0; q < AW; q++)
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+            Ch[q][k] = Dh[q][k] = 0u;
+
+    const uint8_t *po = g.img + j0;
+    const uint8_t *ph[AW];
+#pragma unroll
+    for (int q = 0; q < AW; q++)
+        ph[q] = g.img + (x0 - HALO + hk[q]);
+    // four rows per round; rows past a_hi read as zero (the last round only)
+    auto group = [&](int64_t a, bool partial) {
+        uint2 O[4];
+        uint32_t Hw[AW][4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            O[q] = make_uint2(0u, 0u);
+#pragma unroll
+            for (int w = 0; w < AW; w++)
+                Hw[w][q] = 0u;
+            if (!partial || a + q <= a_hi) {  // warp-uniform
+                const int64_t ro = (a + q) * g.pitch;
+                if (ov && BZ_DBG_IN(po + ro, 8, g.img, ext, kDbgImage))
+                    O[q] = __ldg(reinterpret_cast<const uint2 *>(po + ro));
+#pragma unroll
+                for (int w = 0; w < AW; w++)
+                    if (hv[w] && BZ_DBG_IN(ph[w] + ro, 4, g.img, ext, kDbgImage))
+                        Hw[w][q] = __ldg(reinterpret_cast<const uint32_t *>(ph[w] + ro));
+            }
+        }
+        col4_sums(O[0].x, O[1].x, O[2].x, O[3].x, Co, Do);
+        col4_sums(O[0].y, O[1].y, O[2].y, O[3].y, Co + 4, Do + 4);
+#pragma unroll
+        for (int w = 0; w < AW; w++)
+            col4_sums(Hw[w][0], Hw[w][1], Hw[w][2], Hw[w][3], Ch[w], Dh[w]);
+    };
+    int64_t a = a_lo;
+    for (; a + 3 <= a_hi; a += 4)
+        group(a, false);
+    if (a <= a_hi)
+        group(a, true);
+    if (EDGE) {  // columns >= W were read from the row padding
+#pragma unroll
+        for (int m = 0; m < kColsPerLane; m++)
+            if (j0 + m >= g.W)
+                Co[m] = Do[m] = 0u;
+#pragma unroll
+        for (int q = 0; q < AW; q++)
+#pragma unroll
+            for (int k = 0; k < 4; k++)
+                if (x0 - HALO + hk[q] + k >= g.W)
+                    Ch[q][k] = Dh[q][k] = 0u;
+    }
+
+    // the anchor: own columns below x0 + r, left-halo columns from x0 - l
+    const int own_n = r - kColsPerLane * lane;  // own columns inside the anchor
+#pragma unroll
+    for (int m = 0; m < kColsPerLane; m++)
+        if (m < own_n) {
+            a1p += Co[m];
+            a2p += Do[m];
+        }
+#pragma unroll
+    for (int q = 0; q < AW; q++)
+        if (hk[q] < HALO)
+#pragma unroll
+            for (int k = 0; k < 4; k++)
+                if (hk[q] + k >= HALO - l) {
+                    a1p += Ch[q][k];
+                    a2p += Dh[q][k];
+                }
+
+    uint32_t *sC = sm, *sD = sm + NPH;
+    __syncwarp();  // the previous tile's last row may still read the slots
+    {
+        const int p0 = HALO + HALO / 8 + 9 * lane;  // own column 0 (HALO + 8 lane)
+#pragma unroll
+        for (int m = 0; m < kColsPerLane; m++) {
+            sC[p0 + m] = Co[m];
+            sD[p0 + m] = Do[m];
+        }
+#pragma unroll
+        for (int q = 0; q < AW; q++) {
+            // hk a multiple of 4: its 4 columns share one pad word; words not
+            // read are zero columns
+            const int p = hk[q] + (hk[q] >> 3);
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                sC[p + k] = Ch[q][k];
+                sD[p + k] = Dh[q][k];
+            }
+        }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int m = 0; m < kColsPerLane; m++) {
+        const int iA = HALO + kColsPerLane * lane + m + r, iB = HALO + kColsPerLane * lane + m - l;
+        const int pA = iA + (iA >> 3), pB = iB + (iB >> 3);
+        E1[m] = (int32_t)(sC[pA] - sC[pB]);
+        E2[m] = sD[pA] - sD[pB];
+    }
+    __syncwarp();  // the slots are rewritten next
+}
+
 // Interior tiles, binarize modes, 32-bit S2: a one-row software pipeline.
 // Iteration i computes the window sums of row i (slide, lane prefix, warp
 // scan) and stores them to a warp-private shared-memory slot, then evaluates
@@ -1105,8 +1272,11 @@ __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &w
             a_lo = 0;
         if (a_hi > H - 1)
             a_hi = H - 1;
-        const uint2 Z = make_uint2(0u, 0u);
-        if (WARMB) {
+        if (!WARMB) {
+            warm_cols<AW, EDGE>(g, win, x0, lane, a_lo, a_hi, reinterpret_cast<uint32_t *>(slots), E1, E2, a1p,
+                                a2p);
+        } else {  // small pages: eight rows per batch of loads (latency-bound tiles of 1-4 rows)
+            const uint2 Z = make_uint2(0u, 0u);
             for (int64_t a = a_lo; a <= a_hi; a += kWarmRows) {
                 uint2 Ar[kWarmRows], Br[kWarmRows];
                 uint32_t w1r[kWarmRows], w2r[kWarmRows];
@@ -1133,52 +1303,6 @@ __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &w
                     a2p += w2r[q];
                 }
             }
-            a_hi = a_lo - 1;
-        }
-        // four rows at a time (their loads issued together), then the rest
-        // one row at a time with one row of look-ahead
-        for (; a_lo + 3 <= a_hi; a_lo += 4) {
-            uint2 Ar[4], Br[4];
-            uint32_t w1r[4], w2r[4];
-#pragma unroll
-            for (int q = 0; q < 4; q++) {
-                const uint8_t *rp = g.img + (a_lo + q) * g.pitch;
-                Ar[q] = ldA(rp);
-                Br[q] = ldB(rp);
-                w1r[q] = w2r[q] = 0u;
-                anchor_row(rp, w1r[q], w2r[q]);
-            }
-            warm8x4(Ar, Br, E1, E2);
-#pragma unroll
-            for (int q = 0; q < 4; q++) {
-                a1p += w1r[q];
-                a2p += w2r[q];
-            }
-        }
-        uint2 A = Z, B = Z;
-        uint32_t w1 = 0, w2 = 0;
-        if (a_lo <= a_hi) {
-            const uint8_t *rp = g.img + a_lo * g.pitch;
-            A = ldA(rp);
-            B = ldB(rp);
-            anchor_row(rp, w1, w2);
-        }
-        for (int64_t a = a_lo; a <= a_hi; a++) {
-            uint2 An = Z, Bn = Z;
-            uint32_t v1 = 0, v2 = 0;
-            if (a < a_hi) {
-                const uint8_t *rp = g.img + (a + 1) * g.pitch;
-                An = ldA(rp);
-                Bn = ldB(rp);
-                anchor_row(rp, v1, v2);
-            }
-            warm8(A, B, E1, E2);
-            a1p += w1;
-            a2p += w2;
-            A = An;
-            B = Bn;
-            w1 = v1;
-            w2 = v2;
         }
     }
     uint32_t A1 = __reduce_add_sync(0xFFFFFFFFu, a1p);
