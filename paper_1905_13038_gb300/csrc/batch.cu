@@ -30,7 +30,7 @@ __global__ void __launch_bounds__(32 * kBatchWarps, CLS < 2 ? kBlocksPerSM : 1)
     k_batch_window(BatchHeader *hdr, const WinJobDev *jobs_all, unsigned long long *fallbacks)
 {
     constexpr bool kPipe = CLS < 2 && (MODE == MODE_FP64 || MODE == MODE_FP32);
-    __shared__ uint4 slots[kBatchWarps][kPipe ? 416 : 1];  // 6.5 KB per warp (pipelined path)
+    __shared__ uint4 slots[kBatchWarps][kPipe ? kPipeSlots : 1];  // pipelined path
     const int lane = threadIdx.x & 31;
     const WinJobDev *jobs = jobs_all + hdr->cls_begin[CLS];
     const int64_t total = hdr->cls_tiles[CLS];

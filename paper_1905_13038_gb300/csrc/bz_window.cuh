@@ -31,6 +31,11 @@ namespace bz {
 constexpr int kColsPerLane = 8;
 constexpr int kTileCols = 32 * kColsPerLane;  // 256
 constexpr int kWarmRows = 8;                   // warm-up rows per batch (WARMB), a multiple of 4
+// Per-warp shared memory of the pipelined path, in 16-byte units: two 2 KB
+// row slots of window sums, the 2 KB edge column table, the 512-byte FP64
+// near-tie list, then the 1 KB table of per-row threshold constants.
+constexpr int kPipeSlotsRows = 416;
+constexpr int kPipeSlots = kPipeSlotsRows + 64;  // 7.5 KB
 
 enum Mode : int { MODE_FP64 = 0, MODE_FP32 = 1, MODE_FP64_DIRECT = 2, MODE_SUMS = 3, MODE_REPORT = 4 };
 
@@ -1173,8 +1178,9 @@ __device__ __forceinline__ void warm_cols(const Image &g, const Window &win, int
 // narrower than a tile): streams that leave the row are clamped and shifted
 // (edge_clamp), the anchor window is clipped to the row, and the per-column
 // counts and their reciprocals come from a per-warp table.
-// smem: 6656 bytes per warp (two 2 KB row slots, the 2 KB column table, and
-// 512 bytes for the FP64 near-tie list and its results).
+// smem: kPipeSlots x 16 = 7680 bytes per warp (two 2 KB row slots, the 2 KB
+// column table, 512 bytes for the FP64 near-tie list and its results, and the
+// 1 KB table of per-row constants; the warm-up uses the first 4.5 KB first).
 template <int MODE, bool WARMB = false, bool EDGE = false, int AW = 1, int EXTM = 0>
 __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &win, const Thresh &T,
                                                  const Outputs &o, int64_t x0, int64_t y0,
@@ -1216,9 +1222,6 @@ __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &w
         const uint2 v = ld8_w3(rp + pB, kB, selB, g.img, img_ext);
         return EDGE ? shift8(v, shift_of(1)) : v;
     };
-    const float inv_w = __frcp_rn((float)win.w);
-    const float inv_h = __frcp_rn((float)win.h);
-    const float inv_hw = inv_h * inv_w;
 
     // anchor words: the caller guarantees (aend - a4) <= 128 AW, AW words
     // per lane (lane + 32 q); lanes past the window read the first word and
@@ -1380,18 +1383,53 @@ __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &w
         vmask = left >= 8 ? 0xFFu : (left <= 0 ? 0u : (1u << (unsigned)left) - 1u);
     }
 
+    // The per-row constants of the threshold, 32 rows at a time (one row per
+    // lane) in the warp's shared memory, read back with two broadcast loads
+    // per row: the clipped row count, n = rows * w, 1/n from correctly rounded
+    // reciprocals (EDGE: 1/rows, the column factor comes from the table), the
+    // interior form's alpha/n, gamma/n and beta/n^2, and the output row's
+    // offset.  Computed in each row instead, they cost every lane ~40
+    // instructions per row (64-bit clipping, the reciprocal's fix-up).
+    struct RowC {
+        float inv_nw, an, gn, bn2;
+        uint32_t nrow, nw;
+        int64_t dst;
+    };
+    RowC *rtab = reinterpret_cast<RowC *>(slots + kPipeSlotsRows);
+    auto fill_rows = [&](int64_t i0) {
+        __syncwarp();  // the previous 32 rows' entries are read
+        const int64_t i = i0 + lane;
+        if (i < y1) {
+            const float inv_w = __frcp_rn((float)win.w);
+            const float inv_h = __frcp_rn((float)win.h);
+            const int64_t rows = (i + u < H - 1 ? i + u : H - 1) - (i - oo > -1 ? i - oo : -1);
+            RowC c;
+            c.nrow = (uint32_t)rows;
+            c.nw = c.nrow * (uint32_t)win.w;
+            c.inv_nw = c.nrow == (uint32_t)win.h ? (EDGE ? inv_h : inv_h * inv_w)
+                                                 : __frcp_rn((float)rows) * (EDGE ? 1.0f : inv_w);
+            c.an = T.alpha * c.inv_nw;
+            c.gn = T.gamma * c.inv_nw;
+            c.bn2 = (T.beta * c.inv_nw) * c.inv_nw;
+            c.dst = (i - o.out_row0) * o.out_pitch;
+            rtab[lane] = c;
+        }
+        __syncwarp();
+    };
+
     // threshold of row i from slot (i & 1) and its pixels P; stores the byte
     auto threshold_row = [&](int64_t i, uint2 P) {
+        if ((((int)(i - y0)) & 31) == 0)  // warp-uniform
+            fill_rows(i);
         const uint4 *sl = slots + (int)(i & 1) * 128;
         const uint4 s1a = sl[0 * 32 + lane], s1b = sl[1 * 32 + lane];
         const uint4 s2a = sl[2 * 32 + lane], s2b = sl[3 * 32 + lane];
         const uint32_t S1v[8] = {s1a.x, s1a.y, s1a.z, s1a.w, s1b.x, s1b.y, s1b.z, s1b.w};
         const uint32_t S2v[8] = {s2a.x, s2a.y, s2a.z, s2a.w, s2b.x, s2b.y, s2b.z, s2b.w};
-        const int64_t rows = (i + u < H - 1 ? i + u : H - 1) - (i - oo > -1 ? i - oo : -1);
-        const uint32_t nrow = (uint32_t)rows;
-        const uint32_t nw = nrow * (uint32_t)win.w;
-        const float inv_nw = nrow == (uint32_t)win.h ? (EDGE ? inv_h : inv_hw)
-                                                     : __frcp_rn((float)rows) * (EDGE ? 1.0f : inv_w);
+        const RowC rc = rtab[((int)(i - y0)) & 31];
+        const uint32_t nrow = rc.nrow;
+        const uint32_t nw = rc.nw;
+        const float inv_nw = rc.inv_nw;
         // count and 1/count of column m: the window width (interior tiles) or
         // the table entry (edge tiles)
         auto count_of = [&](int ln, int m, uint32_t &n_m, float &inv_m) {
@@ -1409,7 +1447,7 @@ __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &w
         // pixel costs d = t - I = S1 (alpha/n + beta/n^2 sqrt(V)) - I (Sauvola
         // with alpha, beta >= 0), else alpha S1/n + (beta S1/n^2 + gamma/n)
         // sqrt(V) - I; certified when |d| > T.bnd_c
-        const float an = T.alpha * inv_nw, gn = T.gamma * inv_nw, bn2 = (T.beta * inv_nw) * inv_nw;
+        const float an = rc.an, gn = rc.gn, bn2 = rc.bn2;
         // V = n S2 - S1^2 < n^2 255^2 / 4: below 2^32 when n <= 513, so
         // that wrapping 32-bit products give it exactly (V32)
         auto eval_n = [&](bool SIMPLE, bool V32, int m, uint32_t S1, uint32_t S2) -> float {
@@ -1558,7 +1596,7 @@ __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &w
             nfb += cnt;
             __syncwarp();  // the list is rewritten by the next row
         }
-        uint8_t *dst = o.bits + (i - o.out_row0) * o.out_pitch + ((j0 >> 3) - o.out_byte0);
+        uint8_t *dst = o.bits + rc.dst + ((j0 >> 3) - o.out_byte0);
         if ((!EDGE || vmask) && BZ_DBG_IN(dst, 1, o.bits, o.bits_bytes, kDbgOutput))
             *dst = (uint8_t)(EDGE ? (byte & vmask) : byte);
     };
@@ -1678,7 +1716,7 @@ __device__ __forceinline__ void tile_prefetch_l2(const Image &g, const Window &w
 // One warp computes the tile of columns [x0, x0+256) x rows [y0, y1).
 // prefetch: start with tile_prefetch_l2.
 // AW > 0: the launch takes the pipelined path with AW anchor words per lane
-// (pipe_words) and the caller provides 6.5 KB of shared memory per warp
+// (pipe_words) and the caller provides kPipeSlots x 16 bytes of shared memory per warp
 // (`slots`); interior and edge tiles then both take it.  AW = 0: window_rows.
 template <int MODE, bool VEC, typename S2T, int AW, bool WARMB = false>
 __device__ __forceinline__ void window_tile(const Image &g, const Window &win, const Thresh &T,

@@ -190,7 +190,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlockExt, 4)
     k_window_ext_pipe(Image g, Window win, ThreshExt T, Outputs o, TileSched S, const uint2 *stripes)
 {
     fallbacks_clear(o);  // plain launch: ordered after the previous kernel
-    __shared__ uint4 slots[kWarpsPerBlockExt][416];  // 6.5 KB per warp
+    __shared__ uint4 slots[kWarpsPerBlockExt][kPipeSlots];
     const int lane = threadIdx.x & 31;
     const int64_t wid = (int64_t)blockIdx.x * kWarpsPerBlockExt + (threadIdx.x >> 5);
     const int64_t stride = (int64_t)gridDim.x * kWarpsPerBlockExt;

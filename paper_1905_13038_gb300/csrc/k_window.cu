@@ -17,7 +17,7 @@ template <int MODE, bool VEC, typename S2T, bool WARMB, int AW>
 __global__ void __launch_bounds__(32 * kWarpsPerBlock, kBlocksPerSM)
     k_window(Image g, Window win, Thresh T, Outputs o, TileSched S, const uint2 *stripes)
 {
-    __shared__ uint4 slots[kWarpsPerBlock][AW ? 416 : 1];  // 6.5 KB per warp (pipelined path)
+    __shared__ uint4 slots[kWarpsPerBlock][AW ? kPipeSlots : 1];  // pipelined path
     const int lane = threadIdx.x & 31;
     const int64_t wid = (int64_t)blockIdx.x * kWarpsPerBlock + (threadIdx.x >> 5);
     const int64_t stride = (int64_t)gridDim.x * kWarpsPerBlock;

@@ -76,15 +76,18 @@ int64_t window_tile_rows(int64_t H, int64_t W, int h, int w)
 }
 
 // Edge-tile height as a fraction of the interior height: the measured time
-// per row of an edge tile is about 1.2x an interior row's on the pipelined
-// path and 1.3-2x on the generic path (GB300, 4096 x 3072 page).  Table 1
-// methods (generic path), Wolf / Rais / Phansalkar at 15², 31², 63²: 0.5
-// gave 778 us summed over the nine calls, 0.6 788, 0.7 795, uniform tiles
-// 940.  BZ_EDGE_FRAC overrides it (tuning; >= 1 disables the balanced
-// schedule).
+// per row of an edge tile is above an interior row's on the pipelined path
+// (clamped streams, per-column counts) and 1.3-2x on the generic path
+// (GB300, 4096 x 3072 page).  Pipelined path, Sauvola BZ_FP64 at 15², 63²,
+// 31 x 127 (events over 64 calls each, with the column-sum warm-up): 0.6 gave
+// 32.5 / 43.1 / 39.7 us, 0.7 33.3 / 42.6 / 38.4, 0.82 36.9 / 42.7 / 39.5,
+// uniform tiles 39.5 / 45.9 / 42.5.  Table 1 methods (generic path), Wolf /
+// Rais / Phansalkar at 15², 31², 63²: 0.5 gave 778 us summed over the nine
+// calls, 0.6 788, 0.7 795, uniform tiles 940.  BZ_EDGE_FRAC overrides it
+// (tuning; >= 1 disables the balanced schedule).
 double default_edge_fraction(bool pipe)
 {
-    return pipe ? 0.82 : 0.5;
+    return pipe ? 0.7 : 0.5;
 }
 
 static double edge_fraction(bool pipe)

@@ -458,12 +458,12 @@ bool tune_window(int mode, const Image &g, const Window &win, int64_t row0, int6
     push_unique(ths, (th0 * 5 + 3) / 4, 1, rows);
     push_unique(ths, (th0 * 3 + 1) / 2, 1, rows);
     push_unique(ths, 2 * th0, 1, rows);
-    const float edges[3] = {(float)default_edge_fraction(pipe), 0.65f, 1.0f};
+    const float edges[4] = {(float)default_edge_fraction(pipe), pipe ? 0.6f : 0.65f, 0.82f, 1.0f};
     const int nstripe = stripes_allowed(win.h) ? 2 : 1;
     double best_ms = -1.0;
     for (int st = 0; st < nstripe; st++) {
         for (int64_t th : ths) {
-            for (int e = 0; e < (st ? 1 : 3); e++) {  // stripe launches use uniform tiles
+            for (int e = 0; e < (st ? 1 : 4); e++) {  // stripe launches use uniform tiles
                 TuneCfg c;
                 c.tile_h = (int32_t)th;
                 c.edge = st ? 1.0f : edges[e];
