@@ -1166,6 +1166,151 @@ __device__ __forceinline__ void warm_cols(const Image &g, const Window &win, int
     __syncwarp();  // the slots are rewritten next
 }
 
+// Per-row constants of the pipelined path's threshold (a 32-row table in the
+// warp's shared memory): the clipped row count, n = rows * w, 1/n from
+// correctly rounded reciprocals (edge tiles: 1/rows, the column factor comes
+// from the column table), the interior form's alpha/n, gamma/n and beta/n^2,
+// and the output row's offset.
+struct RowC {
+    float inv_nw, an, gn, bn2;
+    uint32_t nrow, nw;
+    int64_t dst;
+};
+
+// FP32 d = t - I of the interior form: S1 (alpha/n + beta/n^2 sqrt(V)) - I
+// (SIMPLE: Sauvola with alpha, beta >= 0), else alpha S1/n + (beta S1/n^2 +
+// gamma/n) sqrt(V) - I, with S1 and V = n S2 - S1^2 each rounded once (V32:
+// V below 2^32, exact in wrapping 32-bit products); certified when |d| >
+// bnd_c.
+__device__ __forceinline__ float eval_interior(bool SIMPLE, bool V32, uint32_t S1, uint32_t S2, uint32_t nw,
+                                               float an, float gn, float bn2, float If)
+{
+    const float S1f = __uint2float_rn(S1);
+    const float Vf = V32 ? __uint2float_rn(nw * S2 - S1 * S1) : __ull2float_rn((uint64_t)nw * S2 - (uint64_t)S1 * S1);
+    const float sq = sqrt_approx(Vf);
+    return SIMPLE ? fmaf(S1f, fmaf(bn2, sq, an), -If) : fmaf(fmaf(bn2, S1f, gn), sq, fmaf(S1f, an, -If));
+}
+
+// FP32 threshold of one pixel from m = S1/n and var = V/n^2 with its
+// per-pixel certified bound: returns the bit and sets slack = |t - I| -
+// bound, certified when > 0.  SIMPLE: Sauvola with alpha, beta >= 0.
+template <int EXTM, typename S2T>
+__device__ __forceinline__ uint32_t eval_bounded(const Thresh &T, const ExtF &F, bool SIMPLE, uint32_t n_m,
+                                                 float inv_m, uint32_t S1, uint32_t S2, float If, float &slack)
+{
+    const float mu = __uint2float_rn(S1) * inv_m;
+    const float var = v_float<S2T>(n_m, (uint64_t)S2, S1) * (inv_m * inv_m);
+    float t, bnd;
+    if (EXTM) {
+        t = ext_t32<EXTM ? EXTM : METHOD_WOLF>(F, mu, var, inv_m, bnd);
+    } else if (SIMPLE) {
+        t = mu * fmaf(T.beta, sqrt_approx(var), T.alpha);
+        bnd = fmaf(T.eps, t, T.delta64);
+    } else {
+        const float s = sqrt_approx(var);
+        t = fmaf(fmaf(T.beta, mu, T.gamma), s, T.alpha * mu);
+        bnd = fmaf(T.eps, fmaf(fmaf(T.abeta, mu, T.agamma), s, T.aalpha * mu), T.delta64);
+    }
+    const float d = t - If;
+    slack = fabsf(d) - bnd;
+    return __float_as_uint(d) >> 31;
+}
+
+// The near-tie path of one row of the pipelined kernel (BZ_FP64), called by
+// the whole warp when some lane has an uncertified pixel.  Out of line, so
+// that its registers do not weigh on the row loop's allocation (inline, it
+// cost the loop ~4 % of its time with no near-tie taken).  The lanes with an
+// uncertified pixel re-read the row's sums from the slot `par` and
+// re-evaluate their 8 pixels in the same FP32 form as the row loop; the
+// uncertified ones are then decided in FP64, spread over the lanes of the
+// warp (up to 32 per round), since FP64 is slow on this part and such pixels
+// come in clusters (flat or saturated areas).  Returns the lane's byte in
+// bits 0-7 and its number of FP64 decisions above.
+template <bool EDGE, int EXTM, typename TT>
+static __device__ __noinline__ uint32_t near_tie_row(const TT T, const ExtF F, uint4 *slots, int par, int lane,
+                                                     uint2 P, uint32_t byte, bool need, const RowC rc,
+                                                     bool simple, uint32_t vmask)
+{
+    const uint4 *sl = slots + par * 128;
+    const uint2 *ctab = reinterpret_cast<const uint2 *>(slots + 256);
+    auto count_of = [&](int ln, int m, uint32_t &n_m, float &inv_m) {
+        if (EDGE) {
+            const uint2 e = ctab[m * 32 + ln];
+            n_m = rc.nrow * e.y;
+            inv_m = rc.inv_nw * __uint_as_float(e.x);
+        } else {
+            n_m = rc.nw;
+            inv_m = rc.inv_nw;
+        }
+    };
+    __syncwarp();  // the slot and the column table are read across lanes
+    const volatile uint32_t *vs = reinterpret_cast<const volatile uint32_t *>(sl);
+    uint32_t und = 0;
+    if (need) {
+        byte = 0;
+        for (int m = 0; m < kColsPerLane; m++) {
+            const uint32_t S1 = vs[((m >> 2) * 32 + lane) * 4 + (m & 3)];
+            const uint32_t S2 = vs[((2 + (m >> 2)) * 32 + lane) * 4 + (m & 3)];
+            float sk;
+            uint32_t b;
+            if (!EDGE && !EXTM) {
+                const float d = eval_interior(simple, false, S1, S2, rc.nw, rc.an, rc.gn, rc.bn2, pixel_f(P, m));
+                b = __float_as_uint(d) >> 31;
+                sk = fabsf(d) - T.bnd_c;
+            } else {
+                uint32_t n_m;
+                float inv_m;
+                count_of(lane, m, n_m, inv_m);
+                b = eval_bounded<EXTM, uint32_t>(T, F, simple, n_m, inv_m, S1, S2, pixel_f(P, m), sk);
+                if (EDGE && !(vmask >> m & 1u))
+                    sk = 1.0f;  // columns past the row count as certified
+            }
+            if (sk > 0.0f)
+                byte |= b << m;
+            else
+                und |= 1u << m;
+        }
+    }
+    // the warp's list of uncertified (lane, pixel) pairs and their bits
+    uint8_t *list = reinterpret_cast<uint8_t *>(slots + 384);
+    uint8_t *res = list + 256;
+    const uint32_t cnt = (uint32_t)__popc(und);
+    const uint32_t incl = warp_incl_scan<uint32_t>(cnt, lane);
+    const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    uint32_t at = incl - cnt;
+    for (uint32_t u2 = und; u2; u2 &= u2 - 1)
+        list[at++] = (uint8_t)(lane * 8 + (__ffs(u2) - 1));
+    __syncwarp();
+    Global G{};
+    if constexpr (EXTM != 0)
+        G = global_lms(*T.gs, T.N);
+    for (uint32_t r0 = 0; r0 < total; r0 += 32) {
+        const uint32_t e = r0 + lane < total ? list[r0 + lane] : (uint32_t)(lane * 8);
+        const int own = (int)(e >> 3), m = (int)(e & 7u);
+        const uint2 Pown = make_uint2(__shfl_sync(0xFFFFFFFFu, P.x, own), __shfl_sync(0xFFFFFFFFu, P.y, own));
+        if (r0 + lane < total) {
+            const uint32_t S1 = vs[((m >> 2) * 32 + own) * 4 + (m & 3)];
+            const uint32_t S2 = vs[((2 + (m >> 2)) * 32 + own) * 4 + (m & 3)];
+            uint32_t n_m;
+            float inv_m;
+            count_of(own, m, n_m, inv_m);
+            if constexpr (EXTM != 0) {
+                res[e] = (uint8_t)fp64_bit_ext(EXTM, (uint32_t)byte_at(Pown, m), S1, (uint64_t)S2, n_m, T.k, T.R,
+                                               T.X.alpha1, T.X.k1, T.X.k2, T.X.gamma, T.X.p, T.X.q, G.L, G.M, G.S);
+            } else {
+                res[e] = (uint8_t)fp64_bit(T.method, (uint32_t)byte_at(Pown, m), S1, (uint64_t)S2, n_m, T.k, T.R);
+            }
+        }
+    }
+    __syncwarp();
+    for (uint32_t u2 = und; u2; u2 &= u2 - 1) {
+        const int m = __ffs(u2) - 1;
+        byte |= (uint32_t)res[lane * 8 + m] << m;
+    }
+    __syncwarp();  // the list is rewritten by the next row
+    return byte | (cnt << 8);
+}
+
 // Interior tiles, binarize modes, 32-bit S2: a one-row software pipeline.
 // Iteration i computes the window sums of row i (slide, lane prefix, warp
 // scan) and stores them to a warp-private shared-memory slot, then evaluates
@@ -1390,11 +1535,6 @@ __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &w
     // interior form's alpha/n, gamma/n and beta/n^2, and the output row's
     // offset.  Computed in each row instead, they cost every lane ~40
     // instructions per row (64-bit clipping, the reciprocal's fix-up).
-    struct RowC {
-        float inv_nw, an, gn, bn2;
-        uint32_t nrow, nw;
-        int64_t dst;
-    };
     RowC *rtab = reinterpret_cast<RowC *>(slots + kPipeSlotsRows);
     auto fill_rows = [&](int64_t i0) {
         __syncwarp();  // the previous 32 rows' entries are read
@@ -1451,12 +1591,7 @@ __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &w
         // V = n S2 - S1^2 < n^2 255^2 / 4: below 2^32 when n <= 513, so
         // that wrapping 32-bit products give it exactly (V32)
         auto eval_n = [&](bool SIMPLE, bool V32, int m, uint32_t S1, uint32_t S2) -> float {
-            const float S1f = __uint2float_rn(S1);
-            const float Vf = V32 ? __uint2float_rn(nw * S2 - S1 * S1)
-                                 : __ull2float_rn((uint64_t)nw * S2 - (uint64_t)S1 * S1);
-            const float sq = sqrt_approx(Vf);
-            const float If = pixel_f(P, m);
-            return SIMPLE ? fmaf(S1f, fmaf(bn2, sq, an), -If) : fmaf(fmaf(bn2, S1f, gn), sq, fmaf(S1f, an, -If));
+            return eval_interior(SIMPLE, V32, S1, S2, nw, an, gn, bn2, pixel_f(P, m));
         };
         // FP32 threshold of pixel m: returns its bit and sets `slack` =
         // |d| - E, certified when > 0 (columns past the row count as
@@ -1465,36 +1600,22 @@ __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &w
             uint32_t n_m;
             float inv_m;
             count(m, n_m, inv_m);
-            const float mu = __uint2float_rn(S1) * inv_m;
-            const float var = v_float<S2T>(n_m, (uint64_t)S2, S1) * (inv_m * inv_m);
-            float t, bnd;
-            if (EXTM) {
-                t = ext_t32<EXTM ? EXTM : METHOD_WOLF>(F, mu, var, inv_m, bnd);
-            } else if (SIMPLE) {
-                t = mu * fmaf(T.beta, sqrt_approx(var), T.alpha);
-                bnd = fmaf(T.eps, t, T.delta64);
-            } else {
-                const float s = sqrt_approx(var);
-                t = fmaf(fmaf(T.beta, mu, T.gamma), s, T.alpha * mu);
-                bnd = fmaf(T.eps, fmaf(fmaf(T.abeta, mu, T.agamma), s, T.aalpha * mu), T.delta64);
-            }
-            const float d = t - pixel_f(P, m);
-            slack = fabsf(d) - bnd;
+            const uint32_t b = eval_bounded<EXTM, S2T>(T, F, SIMPLE, n_m, inv_m, S1, S2, pixel_f(P, m), slack);
             if (EDGE && !(vmask >> m & 1u))
                 slack = 1.0f;
-            return __float_as_uint(d) >> 31;
+            return b;
         };
         // hot path: the bits and the row's smallest slack only
         uint32_t byte = 0;
         float minslack = 1.0f;
         if (!EDGE && !EXTM) {
-            bool unc = false;  // some |d| <= T.bnd_c
+            float mind = 3.0e38f;  // the row's smallest |d| (one min per pixel)
             auto row8 = [&](bool SIMPLE, bool V32) {
 #pragma unroll
                 for (int m = kColsPerLane - 1; m >= 0; m--) {
                     const float d = eval_n(SIMPLE, V32, m, S1v[m], S2v[m]);
                     byte = (byte << 1) | (__float_as_uint(d) >> 31);
-                    unc |= fabsf(d) <= T.bnd_c;
+                    mind = fminf(mind, fabsf(d));
                 }
             };
             const bool v32 = nw <= 513u;
@@ -1509,7 +1630,7 @@ __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &w
                 else
                     row8(false, false);
             }
-            minslack = unc ? -1.0f : 1.0f;
+            minslack = mind <= T.bnd_c ? -1.0f : 1.0f;
         } else if (simple) {
 #pragma unroll
             for (int m = 0; m < kColsPerLane; m++) {
@@ -1526,75 +1647,15 @@ __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &w
             }
         }
         if (MODE == MODE_FP64 && __any_sync(0xFFFFFFFFu, !(minslack > 0.0f))) {
-            // rare path (the whole warp): the lanes with an uncertified pixel
-            // re-read the row's sums (volatile, so that the hot path keeps no
-            // copy alive) and re-evaluate their 8 pixels; the uncertified
-            // ones are then decided in FP64, spread over the lanes of the
-            // warp (up to 32 per round), since FP64 is slow and such pixels
-            // come in clusters (flat or saturated areas)
-            __syncwarp();  // the slot and the column table are read across lanes
-            const volatile uint32_t *vs = reinterpret_cast<const volatile uint32_t *>(sl);
-            uint32_t und = 0;
-            if (!(minslack > 0.0f)) {
-                byte = 0;
-                for (int m = 0; m < kColsPerLane; m++) {
-                    const uint32_t S1 = vs[((m >> 2) * 32 + lane) * 4 + (m & 3)];
-                    const uint32_t S2 = vs[((2 + (m >> 2)) * 32 + lane) * 4 + (m & 3)];
-                    float sk;
-                    uint32_t b;
-                    if (!EDGE && !EXTM) {
-                        const float d = eval_n(simple, false, m, S1, S2);
-                        b = __float_as_uint(d) >> 31;
-                        sk = fabsf(d) - T.bnd_c;
-                    } else {
-                        b = eval(simple, m, S1, S2, sk);
-                    }
-                    if (sk > 0.0f)
-                        byte |= b << m;
-                    else
-                        und |= 1u << m;
-                }
-            }
-            // the warp's list of uncertified (lane, pixel) pairs and their bits
-            uint8_t *list = reinterpret_cast<uint8_t *>(slots + 384);
-            uint8_t *res = list + 256;
-            const uint32_t cnt = (uint32_t)__popc(und);
-            const uint32_t incl = warp_incl_scan<uint32_t>(cnt, lane);
-            const uint32_t total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-            uint32_t at = incl - cnt;
-            for (uint32_t u2 = und; u2; u2 &= u2 - 1)
-                list[at++] = (uint8_t)(lane * 8 + (__ffs(u2) - 1));
-            __syncwarp();
-            Global G{};
-            if (EXTM)
-                G = global_lms(*TX.gs, TX.N);
-            for (uint32_t r0 = 0; r0 < total; r0 += 32) {
-                const uint32_t e = r0 + lane < total ? list[r0 + lane] : (uint32_t)(lane * 8);
-                const int own = (int)(e >> 3), m = (int)(e & 7u);
-                const uint2 Pown = make_uint2(__shfl_sync(0xFFFFFFFFu, P.x, own), __shfl_sync(0xFFFFFFFFu, P.y, own));
-                if (r0 + lane < total) {
-                    const uint32_t S1 = vs[((m >> 2) * 32 + own) * 4 + (m & 3)];
-                    const uint32_t S2 = vs[((2 + (m >> 2)) * 32 + own) * 4 + (m & 3)];
-                    uint32_t n_m;
-                    float inv_m;
-                    count_of(own, m, n_m, inv_m);
-                    if (EXTM) {
-                        res[e] = (uint8_t)fp64_bit_ext(EXTM, (uint32_t)byte_at(Pown, m), S1, (uint64_t)S2, n_m,
-                                                       T.k, T.R, TX.X.alpha1, TX.X.k1, TX.X.k2, TX.X.gamma,
-                                                       TX.X.p, TX.X.q, G.L, G.M, G.S);
-                    } else {
-                        res[e] = (uint8_t)fp64_bit(T.method, (uint32_t)byte_at(Pown, m), S1, (uint64_t)S2, n_m,
-                                                   T.k, T.R);
-                    }
-                }
-            }
-            __syncwarp();
-            for (uint32_t u2 = und; u2; u2 &= u2 - 1) {
-                const int m = __ffs(u2) - 1;
-                byte |= (uint32_t)res[lane * 8 + m] << m;
-            }
-            nfb += cnt;
-            __syncwarp();  // the list is rewritten by the next row
+            uint32_t rb;
+            if constexpr (EXTM != 0)
+                rb = near_tie_row<EDGE, EXTM, ThreshExt>(TX, F, slots, (int)(i & 1), lane, P, byte,
+                                                         !(minslack > 0.0f), rc, simple, vmask);
+            else
+                rb = near_tie_row<EDGE, 0, Thresh>(T, F, slots, (int)(i & 1), lane, P, byte, !(minslack > 0.0f),
+                                                   rc, simple, vmask);
+            byte = rb & 0xFFu;
+            nfb += rb >> 8;
         }
         uint8_t *dst = o.bits + rc.dst + ((j0 >> 3) - o.out_byte0);
         if ((!EDGE || vmask) && BZ_DBG_IN(dst, 1, o.bits, o.bits_bytes, kDbgOutput))
