@@ -850,8 +850,9 @@ def main():
     # completion of all steps.
     e2e_steps = max(2, min(args.steps, 25))
     host_out = [torch.empty((H, (W + 7) // 8), dtype=torch.uint8).pin_memory() for _ in WINDOWS]
-    bz.binarize_host_multi(0, pinned, WINDOWS, K_SAUVOLA, R_SAUVOLA, outs=host_out, precision=prec,
-                           stream=stream, sync=False)  # warm (library streams, buffers)
+    for _ in range(max(3, args.warmup)):  # warm-up calls (library streams, buffers, events), untimed
+        bz.binarize_host_multi(0, pinned, WINDOWS, K_SAUVOLA, R_SAUVOLA, outs=host_out, precision=prec,
+                               stream=stream, sync=False)
     stream.synchronize()
     barrier()
     t_e2e = time.perf_counter()

@@ -700,15 +700,19 @@ bz_status binarize_inplace_cols(int32_t method, uint8_t *image, int64_t H, int64
 // buffer and the events that mark its upload, compute and download done.
 // Call n uploads into slot n % 2 once that slot's previous compute has read
 // it, computes once the upload is done and the slot's previous output is
-// home, and downloads; the caller's stream waits only for the download, so
-// call n+1's upload runs during call n's compute and call n+1's compute
-// during call n's download.  Fixed buffers rather than stream-ordered
+// home, and downloads each window's output as soon as that window's launch
+// is done (one event per window, so a call's downloads run during its later
+// windows' compute and only the last one is left after it); the caller's
+// stream waits only for the downloads, so call n+1's upload runs during call
+// n's compute and call n+1's compute during call n's last download.  Fixed
+// buffers rather than stream-ordered
 // allocations: a pool allocation on one stream can be handed memory freed on
 // another and then wait for that stream's work.
 struct HostSlot {
     uint8_t *img = nullptr, *out = nullptr;
     size_t img_cap = 0, out_cap = 0;
     cudaEvent_t up = nullptr, comp = nullptr, down = nullptr;
+    cudaEvent_t win[64] = {};  // window q's launches done (created on first use)
 };
 
 struct HostState {
@@ -832,11 +836,19 @@ static bz_status host_run(int32_t method, const uint8_t *image_host, int64_t H, 
         o.fallbacks_clear = fbs.clear;
         ok = launch_window(mode, Image{sl.img, H, W, dpitch}, make_window(hv[q], wv[q]), T, o, hs->comp) ==
              cudaSuccess;
+        if (ok && q + 1 < n) {  // window q's output can go home while the next ones compute
+            if (!sl.win[q])
+                ok = cudaEventCreateWithFlags(&sl.win[q], cudaEventDisableTiming) == cudaSuccess;
+            ok = ok && cudaEventRecord(sl.win[q], hs->comp) == cudaSuccess;
+        }
     }
     ok = ok && cudaEventRecord(sl.comp, hs->comp) == cudaSuccess;
-    // download, and order the caller's stream after it
-    ok = ok && cudaStreamWaitEvent(hs->down, sl.comp, 0) == cudaSuccess;
+    // downloads, each after its window's launches, and order the caller's
+    // stream after them
     for (int q = 0; ok && q < n; q++) {
+        ok = cudaStreamWaitEvent(hs->down, q + 1 < n ? sl.win[q] : sl.comp, 0) == cudaSuccess;
+        if (!ok)
+            break;
         const uint8_t *src = sl.out + plane * (size_t)q;
         if (out_pitch == cw)
             ok = cudaMemcpyAsync(outs[q], src, plane, cudaMemcpyDeviceToHost, hs->down) == cudaSuccess;
