@@ -33,9 +33,12 @@ constexpr int kTileCols = 32 * kColsPerLane;  // 256
 constexpr int kWarmRows = 8;                   // warm-up rows per batch (WARMB), a multiple of 4
 // Per-warp shared memory of the pipelined path, in 16-byte units: two 2 KB
 // row slots of window sums, the 2 KB edge column table, the 512-byte FP64
-// near-tie list, then the 1 KB table of per-row threshold constants.
+// near-tie list, the 1 KB table of per-row threshold constants, then 3.75 KB
+// where the row loop parks its state while a near-tie row is decided.
 constexpr int kPipeSlotsRows = 416;
-constexpr int kPipeSlots = kPipeSlotsRows + 64;  // 7.5 KB
+constexpr int kPipeSlotsPark = kPipeSlotsRows + 64;
+constexpr int kPipeParkWords = 30;                                 // per lane
+constexpr int kPipeSlots = kPipeSlotsPark + kPipeParkWords * 8;  // 11.25 KB
 
 enum Mode : int { MODE_FP64 = 0, MODE_FP32 = 1, MODE_FP64_DIRECT = 2, MODE_SUMS = 3, MODE_REPORT = 4 };
 
@@ -1557,8 +1560,12 @@ __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &w
         __syncwarp();
     };
 
-    // threshold of row i from slot (i & 1) and its pixels P; stores the byte
-    auto threshold_row = [&](int64_t i, uint2 P) {
+    // FP32 threshold of row i from slot (i & 1) and its pixels P.  Stores the
+    // byte and returns false when every pixel of the warp's row is certified
+    // (always outside MODE_FP64); else returns true with the FP32 byte and
+    // the lane's smallest slack in byte_out / slack_out, stored by
+    // threshold_rare after the near-tie path.
+    auto threshold_fast = [&](int64_t i, uint2 P, uint32_t &byte_out, float &slack_out) -> bool {
         if ((((int)(i - y0)) & 31) == 0)  // warp-uniform
             fill_rows(i);
         const uint4 *sl = slots + (int)(i & 1) * 128;
@@ -1647,16 +1654,27 @@ __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &w
             }
         }
         if (MODE == MODE_FP64 && __any_sync(0xFFFFFFFFu, !(minslack > 0.0f))) {
-            uint32_t rb;
-            if constexpr (EXTM != 0)
-                rb = near_tie_row<EDGE, EXTM, ThreshExt>(TX, F, slots, (int)(i & 1), lane, P, byte,
-                                                         !(minslack > 0.0f), rc, simple, vmask);
-            else
-                rb = near_tie_row<EDGE, 0, Thresh>(T, F, slots, (int)(i & 1), lane, P, byte, !(minslack > 0.0f),
-                                                   rc, simple, vmask);
-            byte = rb & 0xFFu;
-            nfb += rb >> 8;
+            byte_out = byte;
+            slack_out = minslack;
+            return true;
         }
+        uint8_t *dst = o.bits + rc.dst + ((j0 >> 3) - o.out_byte0);
+        if ((!EDGE || vmask) && BZ_DBG_IN(dst, 1, o.bits, o.bits_bytes, kDbgOutput))
+            *dst = (uint8_t)(EDGE ? (byte & vmask) : byte);
+        return false;
+    };
+    // the near-tie path of row i (the whole warp), then the byte's store
+    auto threshold_rare = [&](int64_t i, uint2 P, uint32_t byte, float minslack) {
+        const RowC rc = rtab[((int)(i - y0)) & 31];
+        uint32_t rb;
+        if constexpr (EXTM != 0)
+            rb = near_tie_row<EDGE, EXTM, ThreshExt>(TX, F, slots, (int)(i & 1), lane, P, byte, !(minslack > 0.0f),
+                                                     rc, simple, vmask);
+        else
+            rb = near_tie_row<EDGE, 0, Thresh>(T, F, slots, (int)(i & 1), lane, P, byte, !(minslack > 0.0f), rc,
+                                               simple, vmask);
+        byte = rb & 0xFFu;
+        nfb += rb >> 8;
         uint8_t *dst = o.bits + rc.dst + ((j0 >> 3) - o.out_byte0);
         if ((!EDGE || vmask) && BZ_DBG_IN(dst, 1, o.bits, o.bits_bytes, kDbgOutput))
             *dst = (uint8_t)(EDGE ? (byte & vmask) : byte);
@@ -1672,22 +1690,86 @@ __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &w
         return __ldg(reinterpret_cast<const uint2 *>(g.img + i * g.pitch + j0));
     };
 
+    // The loop state parks in the warp's shared memory while a near-tie row
+    // is decided (word w of the lane at w * 32 + lane), so that the near-tie
+    // path finds the registers free and the row loop's allocation does not
+    // have to keep its state alive across that path (which, kept live across
+    // it, cost the loop ~3 % of its time with no near-tie taken).
+    volatile uint32_t *park = reinterpret_cast<volatile uint32_t *>(slots + kPipeSlotsPark);
+    uint2 Pprev;
+    auto park_state = [&]() {
+#pragma unroll
+        for (int m = 0; m < kColsPerLane; m++) {
+            park[m * 32 + lane] = (uint32_t)E1[m];
+            park[(8 + m) * 32 + lane] = E2[m];
+        }
+        const uint32_t w[14] = {A1, (uint32_t)A2, nA.x, nA.y, nB.x, nB.y, nC.x, nC.y, nD.x, nD.y, nd1, nd2,
+                                Pprev.x, Pprev.y};
+#pragma unroll
+        for (int k = 0; k < 14; k++)
+            park[(16 + k) * 32 + lane] = w[k];
+    };
+    auto unpark_state = [&]() {
+#pragma unroll
+        for (int m = 0; m < kColsPerLane; m++) {
+            E1[m] = (int32_t)park[m * 32 + lane];
+            E2[m] = park[(8 + m) * 32 + lane];
+        }
+        uint32_t w[14];
+#pragma unroll
+        for (int k = 0; k < 14; k++)
+            w[k] = park[(16 + k) * 32 + lane];
+        A1 = w[0];
+        A2 = (S2T)w[1];
+        nA = make_uint2(w[2], w[3]);
+        nB = make_uint2(w[4], w[5]);
+        nC = make_uint2(w[6], w[7]);
+        nD = make_uint2(w[8], w[9]);
+        nd1 = w[10];
+        nd2 = w[11];
+        Pprev = make_uint2(w[12], w[13]);
+    };
+
     // prologue: row y0
     sums_to_slot(y0);
-    uint2 Pprev = centre(y0);
+    Pprev = centre(y0);
     if (y0 + 1 < y1)
         fetch(y0 + 1);
-    for (int64_t i = y0 + 1; i < y1; i++) {
-        const uint2 Pcur = centre(i);
-        slide8(nA, nB, nC, nD, E1, E2);
-        A1 += (uint32_t)__reduce_add_sync(0xFFFFFFFFu, nd1);
-        A2 += (S2T)__reduce_add_sync(0xFFFFFFFFu, nd2);
-        fetch(i + 1 < y1 ? i + 1 : i);  // the last fetch is unused (no branch)
-        sums_to_slot(i);
-        threshold_row(i - 1, Pprev);
-        Pprev = Pcur;
+    int64_t i = y0 + 1;
+    for (;;) {
+        // rows until one with a near-tie (warp-uniform exit)
+        bool tie = false;
+        uint2 Ptie = make_uint2(0u, 0u);
+        uint32_t tbyte = 0;
+        float tslack = 1.0f;
+        for (; i < y1; i++) {
+            const uint2 Pcur = centre(i);
+            slide8(nA, nB, nC, nD, E1, E2);
+            A1 += (uint32_t)__reduce_add_sync(0xFFFFFFFFu, nd1);
+            A2 += (S2T)__reduce_add_sync(0xFFFFFFFFu, nd2);
+            fetch(i + 1 < y1 ? i + 1 : i);  // the last fetch is unused (no branch)
+            sums_to_slot(i);
+            const uint2 Prow = Pprev;
+            Pprev = Pcur;
+            if (threshold_fast(i - 1, Prow, tbyte, tslack)) {
+                Ptie = Prow;
+                tie = true;
+                break;
+            }
+        }
+        if (MODE != MODE_FP64 || !tie)
+            break;
+        park_state();
+        threshold_rare(i - 1, Ptie, tbyte, tslack);
+        unpark_state();
+        i++;
     }
-    threshold_row(y1 - 1, Pprev);
+    {
+        uint32_t tbyte;
+        float tslack;
+        if (threshold_fast(y1 - 1, Pprev, tbyte, tslack))
+            threshold_rare(y1 - 1, Pprev, tbyte, tslack);
+    }
 
     if (MODE == MODE_FP64 && o.fallbacks) {
         const unsigned v = __reduce_add_sync(0xFFFFFFFFu, (unsigned)nfb);
