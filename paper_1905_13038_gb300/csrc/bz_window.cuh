@@ -1459,6 +1459,15 @@ __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &w
     uint32_t A1 = __reduce_add_sync(0xFFFFFFFFu, a1p);
     S2T A2 = (S2T)__reduce_add_sync(0xFFFFFFFFu, a2p);  // < 2^32 when h*w <= 66051
 
+    // The anchor's entering and leaving bytes are already in the B streams:
+    // byte m of lane L's B stream is column x0 + 8 L + m - l, which lies in
+    // the anchor window [x0 - l, x0 + r) exactly when 8 L + m < w (w <= 256
+    // on this path; edge tiles read columns outside [0, W) as 0, as the
+    // clipped anchor window does).  amx / amy: those bytes of the lane.
+    const int anb = win.w - kColsPerLane * lane;
+    const uint32_t amx = anb >= 4 ? 0xFFFFFFFFu : (anb <= 0 ? 0u : 0xFFFFFFFFu >> (8 * (4 - anb)));
+    const uint32_t amy = anb >= 8 ? 0xFFFFFFFFu : (anb <= 4 ? 0u : 0xFFFFFFFFu >> (8 * (8 - anb)));
+
     // branch-free slide data for row i: rows outside the image read row 0
     // and are masked to zero
     uint2 nA, nB, nC, nD;
@@ -1470,16 +1479,17 @@ __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &w
         const uint8_t *pb = g.img + (vb ? rb : 0) * g.pitch;
         uint2 A = ldA(pa), B = ldB(pa);
         uint2 C = ldA(pb), D = ldB(pb);
-        uint32_t e1 = 0, e2 = 0, x1 = 0, x2 = 0;
-        anchor_row(pa, e1, e2);
-        anchor_row(pb, x1, x2);
         const uint32_t ma = va ? 0xFFFFFFFFu : 0u, mb = vb ? 0xFFFFFFFFu : 0u;
         nA = make_uint2(A.x & ma, A.y & ma);
         nB = make_uint2(B.x & ma, B.y & ma);
         nC = make_uint2(C.x & mb, C.y & mb);
         nD = make_uint2(D.x & mb, D.y & mb);
-        nd1 = (e1 & ma) - (x1 & mb);
-        nd2 = (e2 & ma) - (x2 & mb);
+        // the anchor's row change: its bytes of the entering row minus those
+        // of the leaving row
+        const uint32_t bx = nB.x & amx, by = nB.y & amy, dx = nD.x & amx, dy = nD.y & amy;
+        nd1 = __dp4a(bx, 0x01010101u, __dp4a(by, 0x01010101u, 0u)) -
+              __dp4a(dx, 0x01010101u, __dp4a(dy, 0x01010101u, 0u));
+        nd2 = __dp4a(bx, bx, __dp4a(by, by, 0u)) - __dp4a(dx, dx, __dp4a(dy, dy, 0u));
     };
 
     // window sums of the current row -> slot (i & 1)
