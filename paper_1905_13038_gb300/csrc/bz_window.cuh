@@ -1706,7 +1706,7 @@ __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &w
     // have to keep its state alive across that path (which, kept live across
     // it, cost the loop ~3 % of its time with no near-tie taken).
     volatile uint32_t *park = reinterpret_cast<volatile uint32_t *>(slots + kPipeSlotsPark);
-    uint2 Pprev;
+    uint2 Pprev = make_uint2(0u, 0u);  // row y0's pixels, set by the prologue below
     auto park_state = [&]() {
 #pragma unroll
         for (int m = 0; m < kColsPerLane; m++) {

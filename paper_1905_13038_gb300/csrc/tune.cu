@@ -9,9 +9,11 @@
 //   batch    tile rows of the batched window and quantile kernels, as
 //            multiples of each job's window height.
 // Candidates are timed with CUDA events on the caller's stream (one
-// untimed run, then the mean of a few, each after reading a buffer larger
-// than L2 so that the input comes from HBM as it does for a stream of
-// distinct images), the fastest is stored under a key of
+// untimed run, then the median of several, each after reading a buffer
+// larger than L2 so that the input comes from HBM as it does for a stream of
+// distinct images; with three runs and their mean, run-to-run spread of the
+// window kernel (~2 %) was as large as the gap between the best candidates
+// and a slower tile schedule could win), the fastest is stored under a key of
 // GPU name and SM count, kernel, precision (or quantile class), window-size
 // buckets (next power of two of h and w) and image-size bucket (half octaves
 // of H x W), and the cache is written back to its file.
@@ -23,6 +25,7 @@
 // tune.json, else $HOME/.cache/paper_1905_13038_gb300/tune.json.  A missing
 // or unreadable file is an empty cache; it is rewritten whole (temporary file
 // and rename) after each tuning.
+#include <algorithm>
 #include <errno.h>
 #include <math.h>
 #include <stdio.h>
@@ -393,9 +396,9 @@ static void *l2_flush_buffer(size_t &bytes)
     return bufs[dev];
 }
 
-// Mean device time of `launch` (a callable returning cudaError_t) on
-// `stream`: one untimed run, then `reps` timed ones, each after an L2 flush.
-// Negative on error.
+// Median device time of `launch` (a callable returning cudaError_t) on
+// `stream`: one untimed run, then `reps` (at most 15) timed ones, each after
+// an L2 flush.  Negative on error.
 template <typename F>
 static double time_on(cudaStream_t stream, int reps, F &&launch)
 {
@@ -408,7 +411,8 @@ static double time_on(cudaStream_t stream, int reps, F &&launch)
     }
     size_t fbytes = 0;
     void *fbuf = l2_flush_buffer(fbytes);
-    double total = 0.0;
+    float ts[15];
+    reps = reps < 1 ? 1 : (reps > 15 ? 15 : reps);
     bool ok = launch() == cudaSuccess;
     int sms = 152;
     int dev = 0;
@@ -424,12 +428,15 @@ static double time_on(cudaStream_t stream, int reps, F &&launch)
         ok = ok && cudaEventRecord(a, stream) == cudaSuccess && launch() == cudaSuccess &&
              cudaEventRecord(b, stream) == cudaSuccess && cudaEventSynchronize(b) == cudaSuccess &&
              cudaEventElapsedTime(&t, a, b) == cudaSuccess;
-        total += t;
+        ts[r] = t;
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     cudaGetLastError();
-    return ok ? total / reps : -1.0;
+    if (!ok)
+        return -1.0;
+    std::sort(ts, ts + reps);
+    return reps % 2 ? ts[reps / 2] : 0.5 * ((double)ts[reps / 2 - 1] + ts[reps / 2]);
 }
 
 static void push_unique(std::vector<int64_t> &v, int64_t x, int64_t lo, int64_t hi)
@@ -469,7 +476,7 @@ bool tune_window(int mode, const Image &g, const Window &win, int64_t row0, int6
                 c.edge = st ? 1.0f : edges[e];
                 c.stripes = st;
                 TuneScope scope(&c);
-                const double ms = time_on(stream, 3, launch);
+                const double ms = time_on(stream, 9, launch);
                 if (ms > 0.0 && (best_ms < 0.0 || ms < best_ms)) {
                     best_ms = ms;
                     best = c;
@@ -498,7 +505,7 @@ bool tune_quantile(const Image &g, const Window &win, const std::function<cudaEr
         c.edge = 1.0f;
         c.stripes = -1;
         TuneScope scope(&c);
-        const double ms = time_on(stream, 3, launch);
+        const double ms = time_on(stream, 9, launch);
         if (ms > 0.0 && (best_ms < 0.0 || ms < best_ms)) {
             best_ms = ms;
             best = c;
