@@ -14,7 +14,9 @@
 // window sums of a row are then a prefix sum of E along the row: a lane-local
 // prefix plus a warp scan, offset by the anchor S(i, x0-1), which the warp
 // itself slides down with DP4A row sums over the anchor window.  There is no
-// shared memory, no halo column and no block-level synchronisation.
+// block-level synchronisation: the generic row routine uses no shared memory,
+// the pipelined one (window_rows_pipe) only the warp's own (row slots of
+// window sums, the column sums of its warm-up, tables, parked state).
 //
 // Threshold: certified FP32 evaluation of the canonical formula with a
 // rigorous absolute error bound E; pixels with |I - t32| <= E are evaluated
@@ -1326,9 +1328,10 @@ static __device__ __noinline__ uint32_t near_tie_row(const TT T, const ExtF F, u
 // narrower than a tile): streams that leave the row are clamped and shifted
 // (edge_clamp), the anchor window is clipped to the row, and the per-column
 // counts and their reciprocals come from a per-warp table.
-// smem: kPipeSlots x 16 = 7680 bytes per warp (two 2 KB row slots, the 2 KB
-// column table, 512 bytes for the FP64 near-tie list and its results, and the
-// 1 KB table of per-row constants; the warm-up uses the first 4.5 KB first).
+// smem: kPipeSlots x 16 = 11,520 bytes per warp (two 2 KB row slots, the 2 KB
+// column table, 512 bytes for the FP64 near-tie list and its results, the
+// 1 KB table of per-row constants and 3.75 KB for the parked loop state; the
+// column-sum warm-up uses the first 4.5 KB before the row loop starts).
 template <int MODE, bool WARMB = false, bool EDGE = false, int AW = 1, int EXTM = 0>
 __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &win, const Thresh &T,
                                                  const Outputs &o, int64_t x0, int64_t y0,
@@ -1371,9 +1374,11 @@ __device__ __forceinline__ void window_rows_pipe(const Image &g, const Window &w
         return EDGE ? shift8(v, shift_of(1)) : v;
     };
 
-    // anchor words: the caller guarantees (aend - a4) <= 128 AW, AW words
-    // per lane (lane + 32 q); lanes past the window read the first word and
-    // mask it to zero
+    // anchor words, read by the small-page warm-up only (the row loop takes
+    // the anchor's bytes from the B streams, the column-sum warm-up from its
+    // column sums): the caller guarantees (aend - a4) <= 128 AW, AW words per
+    // lane (lane + 32 q); lanes past the window read the first word and mask
+    // it to zero
     int64_t ac0 = x0 - l, aend = x0 + r;
     if (EDGE) {  // clip the anchor window to the row
         ac0 = ac0 > 0 ? ac0 : 0;
@@ -1831,7 +1836,8 @@ __device__ __forceinline__ void sched_tile(const TileSched &S, int64_t W, const 
 // window [x0 - l, x0 + r) that AW words per lane cover: at most 128 AW bytes
 // from the word boundary below x0 - l (x0 is a multiple of 256; an edge
 // tile's clipped window starts at column 0 or there, and it is no wider).
-// Returns AW (1 or 2), or 0 when the path does not apply.
+// AW also sets the halo of the column-sum warm-up (64 AW columns each side,
+// l, r <= 64 AW).  Returns AW (1 or 2), or 0 when the path does not apply.
 __host__ __device__ inline int pipe_words(int mode, bool vec, bool s2_32, const Image &g,
                                           const Window &win)
 {
@@ -1869,8 +1875,9 @@ __device__ __forceinline__ void tile_prefetch_l2(const Image &g, const Window &w
 // One warp computes the tile of columns [x0, x0+256) x rows [y0, y1).
 // prefetch: start with tile_prefetch_l2.
 // AW > 0: the launch takes the pipelined path with AW anchor words per lane
-// (pipe_words) and the caller provides kPipeSlots x 16 bytes of shared memory per warp
-// (`slots`); interior and edge tiles then both take it.  AW = 0: window_rows.
+// (pipe_words: the anchor and halo width) and the caller provides
+// kPipeSlots x 16 bytes of shared memory per warp (`slots`); interior and
+// edge tiles then both take it.  AW = 0: window_rows.
 template <int MODE, bool VEC, typename S2T, int AW, bool WARMB = false>
 __device__ __forceinline__ void window_tile(const Image &g, const Window &win, const Thresh &T,
                                             const Outputs &o, int64_t x0, int64_t y0, int64_t y1,
