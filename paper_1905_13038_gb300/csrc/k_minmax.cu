@@ -58,6 +58,34 @@ __device__ __forceinline__ uint32_t mm_load(const Image &g, int64_t row, int64_t
     return v;
 }
 
+// 16-bit pair minimum / maximum (one instruction; the byte-quad __vminu4 /
+// __vmaxu4 take several).  The vertical sweeps keep a word's 4 columns as two
+// pairs: columns 0, 1 (lo) and 2, 3 (hi), each byte widened to 16 bits.
+__device__ __forceinline__ uint32_t min_u16x2(uint32_t a, uint32_t b)
+{
+    uint32_t d;
+    asm("min.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+__device__ __forceinline__ uint32_t max_u16x2(uint32_t a, uint32_t b)
+{
+    uint32_t d;
+    asm("max.u16x2 %0, %1, %2;" : "=r"(d) : "r"(a), "r"(b));
+    return d;
+}
+__device__ __forceinline__ uint32_t pair_lo(uint32_t w)
+{
+    return __byte_perm(w, 0u, 0x4140u);
+}
+__device__ __forceinline__ uint32_t pair_hi(uint32_t w)
+{
+    return __byte_perm(w, 0u, 0x4342u);
+}
+__device__ __forceinline__ uint32_t pairs_pack(uint32_t lo, uint32_t hi)
+{
+    return __byte_perm(lo, hi, 0x6420u);
+}
+
 // Bytes [byte, byte+4) of a shared-memory row of words.
 __device__ __forceinline__ uint32_t mm_bytes(const uint32_t *row, int byte)
 {
@@ -116,16 +144,22 @@ __global__ void __launch_bounds__(kMmThreads)
         }
         oob[m] = mk;
     }
+    uint32_t oobl[kMmMaxWords], oobh[kMmMaxWords];  // the masks as pairs (0x00FF: outside)
+#pragma unroll
+    for (int m = 0; m < kMmMaxWords; m++) {
+        oobl[m] = pair_lo(oob[m]);
+        oobh[m] = pair_hi(oob[m]);
+    }
     for (int64_t a = y0; a < y1; a += h) {
         const int64_t b = a + h < y1 ? a + h : y1;
         const int64_t c = a + u;
         // backward sweep: suffix extrema of rows s .. c, stored for the
         // window starts s = i-o+1, i in [a, b)
-        uint32_t smin[kMmMaxWords], smax[kMmMaxWords];
+        uint32_t sminl[kMmMaxWords], sminh[kMmMaxWords], smaxl[kMmMaxWords], smaxh[kMmMaxWords];
 #pragma unroll
         for (int m = 0; m < kMmMaxWords; m++) {
-            smin[m] = 0xFFFFFFFFu;
-            smax[m] = 0u;
+            sminl[m] = sminh[m] = 0x00FF00FFu;
+            smaxl[m] = smaxh[m] = 0u;
         }
         // (rows are loaded kMmBatch at a time so that their latencies overlap)
         for (int64_t s0 = c; s0 >= a - o + 1; s0 -= kMmBatch) {
@@ -146,8 +180,11 @@ __global__ void __launch_bounds__(kMmThreads)
                 if (s >= 0 && s < g.H) {
 #pragma unroll
                     for (int m = 0; m < kMmMaxWords; m++) {
-                        smin[m] = __vminu4(smin[m], v[k][m] | oob[m]);
-                        smax[m] = __vmaxu4(smax[m], v[k][m] & ~oob[m]);
+                        const uint32_t vl = pair_lo(v[k][m]), vh = pair_hi(v[k][m]);
+                        sminl[m] = min_u16x2(sminl[m], vl | oobl[m]);
+                        sminh[m] = min_u16x2(sminh[m], vh | oobh[m]);
+                        smaxl[m] = max_u16x2(smaxl[m], vl & ~oobl[m]);
+                        smaxh[m] = max_u16x2(smaxh[m], vh & ~oobh[m]);
                     }
                 }
                 const int64_t i = s + o - 1;  // the output row whose window starts at s
@@ -156,19 +193,19 @@ __global__ void __launch_bounds__(kMmThreads)
                     for (int m = 0; m < kMmMaxWords; m++) {
                         if (act[m]) {
                             const int q = tid + m * kMmThreads;
-                            Vmin[(i - y0) * NWP + q] = smin[m];
-                            Vmax[(i - y0) * NWP + q] = smax[m];
+                            Vmin[(i - y0) * NWP + q] = pairs_pack(sminl[m], sminh[m]);
+                            Vmax[(i - y0) * NWP + q] = pairs_pack(smaxl[m], smaxh[m]);
                         }
                     }
                 }
             }
         }
         // forward sweep: prefix extrema of rows c+1 .. i+u
-        uint32_t pmin[kMmMaxWords], pmax[kMmMaxWords];
+        uint32_t pminl[kMmMaxWords], pminh[kMmMaxWords], pmaxl[kMmMaxWords], pmaxh[kMmMaxWords];
 #pragma unroll
         for (int m = 0; m < kMmMaxWords; m++) {
-            pmin[m] = 0xFFFFFFFFu;
-            pmax[m] = 0u;
+            pminl[m] = pminh[m] = 0x00FF00FFu;
+            pmaxl[m] = pmaxh[m] = 0u;
         }
         for (int64_t i0 = a + 1; i0 < b; i0 += kMmBatch) {
             uint32_t v[kMmBatch][kMmMaxWords];
@@ -189,13 +226,17 @@ __global__ void __launch_bounds__(kMmThreads)
                 for (int m = 0; m < kMmMaxWords; m++) {
                     if (act[m]) {
                         if (i + u < g.H) {
-                            pmin[m] = __vminu4(pmin[m], v[k][m] | oob[m]);
-                            pmax[m] = __vmaxu4(pmax[m], v[k][m] & ~oob[m]);
+                            const uint32_t vl = pair_lo(v[k][m]), vh = pair_hi(v[k][m]);
+                            pminl[m] = min_u16x2(pminl[m], vl | oobl[m]);
+                            pminh[m] = min_u16x2(pminh[m], vh | oobh[m]);
+                            pmaxl[m] = max_u16x2(pmaxl[m], vl & ~oobl[m]);
+                            pmaxh[m] = max_u16x2(pmaxh[m], vh & ~oobh[m]);
                         }
                         const int q = tid + m * kMmThreads;
                         const int64_t x = (i - y0) * NWP + q;
-                        Vmin[x] = __vminu4(Vmin[x], pmin[m]);
-                        Vmax[x] = __vmaxu4(Vmax[x], pmax[m]);
+                        const uint32_t a = Vmin[x], b = Vmax[x];
+                        Vmin[x] = pairs_pack(min_u16x2(pair_lo(a), pminl[m]), min_u16x2(pair_hi(a), pminh[m]));
+                        Vmax[x] = pairs_pack(max_u16x2(pair_lo(b), pmaxl[m]), max_u16x2(pair_hi(b), pmaxh[m]));
                     }
                 }
             }
